@@ -1,0 +1,524 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test checks one oracle function against something other than the
+oracle itself: a value the paper states, a closed form, an independent
+numerical route (quadrature, an ODE solve, a banded linear solve, a dense
+matrix assembled face by face), or an invariant of the scheme.  Equation
+numbers refer to Sun et al., arXiv 2303.14119.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, linalg, optimize, stats
+
+import oracle
+from oracle import EPS0, ME, QE, Oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def paper_defaults():
+    with open(os.path.join(GOLDEN, "paper_defaults.json")) as fh:
+        return json.load(fh)
+
+
+# ---------------------------------------------------------------- Eqs. 8-11
+def test_seey_peak_is_delta_max_at_A_max_for_normal_incidence():
+    """Sec. 2 after Eq. 9: delta_max is the largest yield and A_max the normal
+    incidence energy where it occurs.  Checked on the paper's defaults."""
+    d = paper_defaults()
+    dmax, amax = d["delta_max"], d["A_max_eV"]
+    res = optimize.minimize_scalar(lambda A: -oracle.seey(A, 0.0, dmax, amax),
+                                   bounds=(1.0, 10 * amax), method="bounded",
+                                   options={"xatol": 1e-9})
+    assert abs(-res.fun / dmax - 1.0) < 2e-4
+    assert abs(res.x / amax - 1.0) < 2e-3
+
+
+def test_seey_angle_scaling_identity():
+    """Eqs. 8-9: the incidence angle rescales the energy axis by
+    (1 + k alpha^2/pi) and the yield by (1 + k alpha^2/(2 pi))."""
+    dmax, amax, ks = 3.0, 400.0, 1.0
+    for alpha in (0.1, 0.5, 1.0, 1.5):
+        for A in (5.0, 60.0, 400.0, 3000.0):
+            lhs = oracle.seey(A * (1 + ks * alpha ** 2 / math.pi), alpha, dmax, amax, ks)
+            rhs = (1 + ks * alpha ** 2 / (2 * math.pi)) * oracle.seey(A, 0.0, dmax, amax, ks)
+            assert lhs == pytest.approx(rhs, rel=1e-13)
+
+
+def test_seey_limits_and_monotonicity():
+    assert oracle.seey(0.0, 0.0, 3.0, 400.0) == 0.0
+    assert oracle.seey(1e-9, 0.0, 3.0, 400.0) < 1e-8
+    A = np.linspace(1.0, 400.0, 200)
+    y = [oracle.seey(a, 0.0, 3.0, 400.0) for a in A]
+    assert np.all(np.diff(y) > 0)  # rising branch below A_max
+    A = np.linspace(420.0, 5000.0, 200)
+    y = [oracle.seey(a, 0.0, 3.0, 400.0) for a in A]
+    assert np.all(np.diff(y) < 0)  # falling branch above A_max
+
+
+def test_incident_energy_and_angle():
+    """Eq. 10 in eV and Eq. 11 measured from the surface normal."""
+    v = math.sqrt(2 * 100.0 * QE / ME)  # 100 eV electron
+    assert oracle.incident_energy_eV(-v, 0.0) == pytest.approx(100.0, rel=1e-14)
+    assert oracle.incident_energy_eV(-v / math.sqrt(2), v / math.sqrt(2)) == pytest.approx(100.0, rel=1e-14)
+    assert oracle.incidence_angle(-1.0, 0.0) == 0.0
+    assert oracle.incidence_angle(-2.0, 2.0) == pytest.approx(math.pi / 4, rel=1e-15)
+    assert oracle.incidence_angle(-1e-3, 5.0) == pytest.approx(math.pi / 2, abs=1e-3)
+
+
+def test_seey_matrix_layout():
+    """Sec. 2: delta_e(i, j) over the (v1, v2) grid, only where v1 < 0."""
+    o = Oracle(4, 6, 5, 20e-6, -6e7, 6e7, -3e7, 3e7)
+    o.set_see(3.0, 400.0, 1.0, 2.0)
+    delta, _, _ = o.tables()
+    _, v1, v2 = o.grid()
+    for i in range(6):
+        for j in range(5):
+            if v1[i] >= 0:
+                assert delta[i, j] == 0.0
+            else:
+                A = 0.5 * ME * (v1[i] ** 2 + v2[j] ** 2) / QE
+                al = math.atan(abs(v2[j] / v1[i]))
+                assert delta[i, j] == pytest.approx(oracle.seey(A, al, 3.0, 400.0), rel=1e-14)
+    # v2 -> -v2 symmetry (alpha uses |v2|) on a symmetric grid
+    assert np.allclose(delta, delta[:, ::-1], rtol=1e-13, atol=0)
+
+
+# ---------------------------------------------------------------- Eqs. 15-16
+def test_emission_prefactor_gives_unit_flux():
+    """Eq. 15's prefactor makes the flux integral of Eq. 16 equal Gamma_see."""
+    for T in (1.0, 2.0, 5.0):
+        vt = math.sqrt(T * QE / ME)
+        val, err = integrate.dblquad(lambda v2, v1: v1 * oracle.emission_continuum(v1, v2, T),
+                                     0.0, 12 * vt, -12 * vt, 12 * vt, epsabs=0, epsrel=1e-10)
+        assert val == pytest.approx(1.0, rel=1e-8)
+
+
+def test_emission_table_flux_and_temperature():
+    """R5 reading: grid-normalised Eq. 15 carries unit flux; on a fine grid its
+    flux-weighted mean of m v1^2/2 is T_se and its mean of m v2^2/2 is T_se/2
+    (half-Maxwellian flux in v1, Maxwellian in v2)."""
+    T = 2.0
+    vt = math.sqrt(T * QE / ME)
+    o = Oracle(2, 400, 300, 20e-6, -8 * vt, 8 * vt, -8 * vt, 8 * vt)
+    o.set_see(3.0, 400.0, 1.0, T)
+    _, gse, _ = o.tables()
+    _, v1, v2 = o.grid()
+    info = o.info()
+    dv = info["dv1"] * info["dv2"]
+    V1, V2 = np.meshgrid(v1, v2, indexing="ij")
+    assert np.all(gse[V1 <= 0] == 0)
+    flux = V1 * gse * dv
+    assert flux.sum() == pytest.approx(1.0, rel=1e-13)
+    e1 = (flux * 0.5 * ME * V1 ** 2).sum() / QE
+    e2 = (flux * 0.5 * ME * V2 ** 2).sum() / QE
+    assert e1 == pytest.approx(T, rel=1e-3)
+    assert e2 == pytest.approx(T / 2, rel=1e-3)
+    # ratio to the continuum form is one constant that tends to 1
+    cont = np.vectorize(lambda a, b: oracle.emission_continuum(a, b, T))(V1, V2)
+    m = V1 > 0
+    r = gse[m] / cont[m]
+    assert np.ptp(r) / r.mean() < 1e-10
+    assert r.mean() == pytest.approx(1.0, rel=1e-4)
+
+
+# ---------------------------------------------------------------- Eq. 7
+def test_source_shape_density_and_moments():
+    """R6 reading of Eq. 7: unit density, half Maxwellian on v2 > 0 (mean
+    sqrt(2T/(pi m))), full Maxwellian in v1 (mean 0, <v1^2> = T/m)."""
+    T = 4.0
+    vt = math.sqrt(T * QE / ME)
+    o = Oracle(8, 300, 400, 20e-6, -8 * vt, 8 * vt, -8 * vt, 8 * vt)
+    o.set_source(1.0, 10e-6, 15e-6, T)
+    _, _, gfe = o.tables()
+    _, v1, v2 = o.grid()
+    info = o.info()
+    dv = info["dv1"] * info["dv2"]
+    V1, V2 = np.meshgrid(v1, v2, indexing="ij")
+    assert np.all(gfe[V2 <= 0] == 0)
+    w = gfe * dv
+    assert w.sum() == pytest.approx(1.0, rel=1e-13)
+    assert (w * V1).sum() == pytest.approx(0.0, abs=1e-9 * vt)
+    assert (w * V1 ** 2).sum() == pytest.approx(vt ** 2, rel=1e-3)
+    assert (w * V2).sum() == pytest.approx(math.sqrt(2 / math.pi) * vt, rel=1e-3)
+    # band: centres in [10, 15] um on 8 cells of 2.5 um -> centres 11.25, 13.75
+    assert info["n_band"] == 2
+
+
+# ---------------------------------------------------------------- Poisson
+def _poisson_fd(ne, sigma, dx):
+    """Independent route: second-order FD Poisson for the potential at cell
+    centres, -phi'' = rho/eps0 with rho = -e n, E = sigma/(2 eps0) at the
+    dielectric (Neumann) and phi = 0 at x = h_max (Dirichlet); E at centres
+    is the mean of the two face fields -dphi/dx."""
+    nx = len(ne)
+    rho = -QE * np.asarray(ne)
+    ab = np.zeros((3, nx))
+    rhs = -rho / EPS0 * dx * dx
+    ab[0, 1:] = 1.0
+    ab[1, :] = -2.0
+    ab[2, :-1] = 1.0
+    # wall face: (phi_0 - phi_-1)/dx = -E_wall  ->  phi_-1 = phi_0 + dx E_wall
+    ab[1, 0] = -1.0
+    rhs[0] -= dx * sigma / (2 * EPS0)
+    # vacuum face value zero: phi_nx = -phi_{nx-1}
+    ab[1, -1] = -3.0
+    phi = linalg.solve_banded((1, 1), ab, rhs)
+    faces = np.empty(nx + 1)
+    faces[0] = sigma / (2 * EPS0)
+    faces[1:-1] = -(phi[1:] - phi[:-1]) / dx
+    faces[-1] = -(0.0 - phi[-1]) / (dx / 2)
+    return 0.5 * (faces[:-1] + faces[1:]), faces
+
+
+def test_ex_matches_fd_poisson_solve():
+    nx, nv1, nv2 = 40, 6, 6
+    o = Oracle(nx, nv1, nv2, 20e-6, -6e7, 6e7, -3e7, 3e7)
+    rng = np.random.default_rng(3)
+    f = rng.uniform(0.0, 1.0, (nx, nv1, nv2)) * 1e6
+    sigma = 2e-3
+    o.set_state(f, sigma)
+    ne, ex, _, _ = o.moments()
+    info = o.info()
+    assert ne == pytest.approx(f.sum(axis=(1, 2)) * info["dv1"] * info["dv2"], rel=1e-13)
+    ref, faces = _poisson_fd(ne, sigma, info["dx"])
+    scale = np.abs(ref).max()
+    assert np.abs(ex - ref).max() < 1e-10 * scale
+    assert ex[0] != pytest.approx(sigma / (2 * EPS0))  # centre, not the wall face
+    # the vacuum-side face field equals the Gauss value: total charge balance
+    assert faces[-1] == pytest.approx(sigma / (2 * EPS0) - QE / EPS0 * ne.sum() * info["dx"], rel=1e-9)
+
+
+def test_external_field_mode():
+    o = Oracle(8, 4, 4, 20e-6, -6e7, 6e7, -3e7, 3e7)
+    o.set_fields(-1e6, self_consistent=False, Ex_ext=2.5e5)
+    o.set_state(np.ones((8, 4, 4)), 1.0)
+    _, ex, _, _ = o.moments()
+    assert np.all(ex == 2.5e5)
+    assert np.all(o.accel() == pytest.approx(-QE * 2.5e5 / ME, rel=1e-15))
+    assert o.info()["a2"] == pytest.approx(QE * 1e6 / ME, rel=1e-15)
+
+
+# ---------------------------------------------------------------- advection
+def test_free_streaming_binomial_and_exact_shift():
+    """With no forces the donor-cell x-update of a delta is a binomial kernel
+    B(n, c) in the upwind direction; at c = 1 it is an exact shift."""
+    nx, nv1, nv2 = 64, 8, 3
+    h, V = 20e-6, 6e7
+    dx, dv1 = h / nx, 2 * V / nv1
+    vmax_c = V - dv1 / 2
+    dt = dx / vmax_c  # c = 1 on the two outermost v1 rows
+    o = Oracle(nx, nv1, nv2, h, -V, V, -3e7, 3e7, dt=dt)
+    o.set_fields(0.0, self_consistent=False, Ex_ext=0.0)
+    k0, n = 30, 15
+    f0 = np.zeros((nx, nv1, nv2))
+    f0[k0] = 1.0
+    o.set_state(f0, 0.0)
+    o.step(n)
+    f = o.get_f()
+    _, v1, _ = o.grid()
+    for i in range(nv1):
+        c = abs(v1[i]) * dt / dx
+        s = 1 if v1[i] > 0 else -1
+        m = np.arange(n + 1)
+        expect = stats.binom.pmf(m, n, min(c, 1.0))
+        got = f[k0 + s * m, i, :]
+        assert np.allclose(got, expect[:, None], rtol=0, atol=1e-14)
+        assert abs(f[:, i, :].sum() - nv2) < 1e-12  # nothing left the domain
+    assert f[k0 + n, nv1 - 1, 0] == pytest.approx(1.0, abs=1e-14)
+    assert f[k0 - n, 0, 0] == pytest.approx(1.0, abs=1e-14)
+
+
+def _accel_for_courant(c, dv, dt):
+    return c * dv / dt
+
+
+@pytest.mark.parametrize("sign1", [1, -1])
+def test_velocity_marginal_trinomial(sign1):
+    """Constant forces: the x-marginal of a delta evolves by the unsplit
+    donor-cell update in (v1, v2) alone, a trinomial kernel."""
+    nx, nv1, nv2 = 64, 14, 12
+    h, V1, V2 = 20e-6, 6e7, 3e7
+    o = Oracle(nx, nv1, nv2, h, -V1, V1, -V2, V2, cfl=0.4)
+    info = o.info()
+    dt = info["dt"]
+    c1, c2 = 0.2, 0.15
+    a1 = sign1 * _accel_for_courant(c1, info["dv1"], dt)
+    a2 = _accel_for_courant(c2, info["dv2"], dt)
+    o.set_fields(-a2 * ME / QE, self_consistent=False, Ex_ext=-a1 * ME / QE)
+    k0, i0, j0, n = 32, 7, 3, 6
+    f0 = np.zeros((nx, nv1, nv2))
+    f0[k0, i0, j0] = 1.0
+    o.set_state(f0, 0.0)
+    o.step(n)
+    g = o.get_f().sum(axis=0)
+    expect = np.zeros_like(g)
+    for b in range(n + 1):
+        for c in range(n + 1 - b):
+            p = stats.multinomial.pmf([b, c, n - b - c], n, [c1, c2, 1 - c1 - c2])
+            expect[i0 + sign1 * b, j0 + c] = p
+    assert np.allclose(g, expect, rtol=0, atol=1e-13)
+
+
+def test_x_v2_joint_trinomial():
+    """No v1 force: at a fixed v1 row the delta spreads in (x, v2) as the
+    trinomial of (c_x, c_2)."""
+    nx, nv1, nv2 = 64, 10, 14
+    o = Oracle(nx, nv1, nv2, 20e-6, -6e7, 6e7, -3e7, 3e7, cfl=0.4)
+    info = o.info()
+    dt, dx = info["dt"], info["dx"]
+    c2 = 0.25
+    a2 = _accel_for_courant(c2, info["dv2"], dt)
+    o.set_fields(-a2 * ME / QE, self_consistent=False, Ex_ext=0.0)
+    _, v1, _ = o.grid()
+    i, k0, j0, n = 7, 20, 2, 7
+    cx = v1[i] * dt / dx
+    assert cx > 0
+    f0 = np.zeros((nx, nv1, nv2))
+    f0[k0, i, j0] = 1.0
+    o.set_state(f0, 0.0)
+    o.step(n)
+    f = o.get_f()[:, i, :]
+    expect = np.zeros_like(f)
+    for a in range(n + 1):
+        for b in range(n + 1 - a):
+            expect[k0 + a, j0 + b] = stats.multinomial.pmf([a, b, n - a - b], n, [cx, c2, 1 - cx - c2])
+    assert np.allclose(f, expect, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- dense matrix
+def _dense_step(f, sigma, tabs, grid, p):
+    """One step assembled face by face as an affine map f' = M f + b, with
+    E_x from the FD Poisson solve above and sigma from Eq. 18."""
+    nx, nv1, nv2 = f.shape
+    x, v1, v2 = grid
+    dx, dv1, dv2, dt = p["dx"], p["dv1"], p["dv2"], p["dt"]
+    delta, gse, gfe = tabs
+    N = f.size
+    L = lambda k, i, j: (k * nv1 + i) * nv2 + j
+    ne = f.sum(axis=(1, 2)) * dv1 * dv2
+    ex, _ = _poisson_fd(ne, sigma, dx)
+    a1 = -QE * ex / ME
+    a2 = -QE * p["Ey"] / ME
+    M = np.eye(N)
+    b = np.zeros(N)
+    # Gamma_see as a row vector on the x = 0 plane (Eqs. 12-14)
+    r_see = np.zeros(N)
+    for i in range(nv1):
+        for j in range(nv2):
+            if v1[i] < 0:
+                r_see[L(0, i, j)] = delta[i, j] * (-v1[i]) * dv1 * dv2
+
+    def add_face(lo, hi, row, scale):
+        if lo is not None:
+            M[lo] -= scale * row
+        if hi is not None:
+            M[hi] += scale * row
+
+    for kf in range(nx + 1):
+        for i in range(nv1):
+            for j in range(nv2):
+                row = np.zeros(N)
+                v = v1[i]
+                if v > 0:
+                    row = v * gse[i, j] * r_see if kf == 0 else _unit(N, L(kf - 1, i, j)) * v
+                elif v < 0 and kf < nx:
+                    row = _unit(N, L(kf, i, j)) * v
+                add_face(L(kf - 1, i, j) if kf > 0 else None, L(kf, i, j) if kf < nx else None,
+                         row, dt / dx)
+    for k in range(nx):
+        for jf in range(nv2 + 1):
+            for i in range(nv1):
+                row = np.zeros(N)
+                if a2 > 0 and jf > 0:
+                    row = _unit(N, L(k, i, jf - 1)) * a2
+                elif a2 < 0 and jf < nv2:
+                    row = _unit(N, L(k, i, jf)) * a2
+                add_face(L(k, i, jf - 1) if jf > 0 else None, L(k, i, jf) if jf < nv2 else None,
+                         row, dt / dv2)
+        for iface in range(nv1 + 1):
+            for j in range(nv2):
+                row = np.zeros(N)
+                if a1[k] > 0 and iface > 0:
+                    row = _unit(N, L(k, iface - 1, j)) * a1[k]
+                elif a1[k] < 0 and iface < nv1:
+                    row = _unit(N, L(k, iface, j)) * a1[k]
+                add_face(L(k, iface - 1, j) if iface > 0 else None, L(k, iface, j) if iface < nv1 else None,
+                         row, dt / dv1)
+    band = [k for k in range(nx) if p["x_lo"] <= x[k] <= p["x_hi"]]
+    for k in band:
+        for i in range(nv1):
+            for j in range(nv2):
+                b[L(k, i, j)] += dt * p["J"] / QE / (len(band) * dx) * gfe[i, j]
+    fn = (M @ f.ravel() + b).reshape(f.shape)
+    dsig = 0.0
+    for i in range(nv1):
+        if v1[i] < 0:
+            for j in range(nv2):
+                dsig += (delta[i, j] - 1.0) * (-v1[i]) * f[0, i, j] * dv1 * dv2
+    return fn, sigma + QE * dt * dsig
+
+
+def _unit(N, idx):
+    u = np.zeros(N)
+    u[idx] = 1.0
+    return u
+
+
+def _strong_case(nx, nv1, nv2, seed=1):
+    """A tiny grid with every term of the step active and large Courant
+    numbers: self-consistent E_x that changes sign across x, large E_y, SEE
+    with a spread emission shape, and a strong source."""
+    h, V1, V2 = 20e-6, 6e7, 3e7
+    o = Oracle(nx, nv1, nv2, h, -V1, V1, -V2, V2, cfl=0.4)
+    info = o.info()
+    a2 = _accel_for_courant(0.2, info["dv2"], info["dt"])
+    p = dict(info, Ey=-a2 * ME / QE, J=1e7, x_lo=0.3 * h, x_hi=0.7 * h)
+    o.set_fields(p["Ey"], True, 0.0)
+    o.set_see(3.0, 400.0, 1.0, 400.0)
+    o.set_source(p["J"], p["x_lo"], p["x_hi"], 300.0)
+    # amplitude so the space-charge field is comparable to sigma/(2 eps0)
+    emax = 0.25 * info["dv1"] / info["dt"] * ME / QE
+    sigma = 2 * EPS0 * emax * 0.8
+    n_tot = 1.6 * emax * EPS0 / QE  # areal density giving a field drop of 1.6 emax
+    amp = 2 * n_tot / (h * 2 * V1 * 2 * V2)
+    rng = np.random.default_rng(seed)
+    f0 = rng.uniform(0.0, 1.0, (nx, nv1, nv2)) * amp
+    return o, f0, sigma, p
+
+
+def test_dense_matrix_brute_force():
+    o, f0, sigma, p = _strong_case(4, 4, 5)
+    o.set_state(f0, sigma)
+    assert o.courant_sum() <= 1.0
+    tabs = o.tables()
+    grid = o.grid()
+    a1 = o.accel()
+    assert a1.max() > 0 > a1.min()  # both v1 directions exercised
+    f, s = f0.copy(), sigma
+    for _ in range(5):
+        f, s = _dense_step(f, s, tabs, grid, p)
+    o.step(5)
+    got = o.get_f()
+    assert np.abs(got - f).sum() / np.abs(f).sum() < 1e-13
+    assert o.surface_charge() == pytest.approx(s, rel=1e-12)
+
+
+# ---------------------------------------------------------------- invariants
+def test_conservation_ledger():
+    """Electron and charge balance to round-off (Eqs. 13-18 with R5, R9)."""
+    o, f0, sigma, p = _strong_case(16, 12, 10, seed=5)
+    o.set_state(f0, sigma)
+    o.step(60)
+    L = o.ledger()
+    rhs = L["emit"] - L["pe"] - L["vac"] - L["lv"] + L["inj"]
+    scale = max(abs(L["emit"]), abs(L["pe"]), abs(L["vac"]), abs(L["lv"]), abs(L["inj"]), L["N"])
+    assert abs((L["N"] - L["N0"]) - rhs) < 1e-12 * scale
+    assert L["emit"] == pytest.approx(L["see"], rel=1e-13)  # R5
+    dsig = o.surface_charge() - L["sigma0"]
+    assert dsig / QE == pytest.approx(L["see"] - L["pe"], rel=1e-12)  # Eq. 18
+    assert L["inj"] == pytest.approx(60 * p["dt"] * p["J"] / QE, rel=1e-12)
+    for key in ("emit", "pe", "vac", "lv"):
+        assert L[key] > 0
+
+
+def test_positivity_under_cfl():
+    o, f0, sigma, p = _strong_case(12, 10, 8, seed=7)
+    o.set_state(f0, sigma)
+    for _ in range(20):
+        assert o.courant_sum() <= 1.0
+        o.step(1)
+        f = o.get_f()
+        assert f.min() >= -1e-14 * f.max()
+
+
+def test_cfl_violation_is_reported():
+    o = Oracle(8, 6, 6, 20e-6, -6e7, 6e7, -3e7, 3e7, dt=1e-12)
+    assert o.step_status(1) == oracle.ECFL
+
+
+def test_default_dt_from_cfl():
+    o = Oracle(64, 48, 48, 20e-6, -6e7, 6e7, -3e7, 3e7, cfl=0.4)
+    assert o.info()["dt"] == pytest.approx(0.4 * (20e-6 / 64) / 6e7, rel=1e-15)
+
+
+def test_convergence_rule_degenerate_and_active():
+    """End of Sec. 2: converged when sigma and both fluxes change by at most
+    0.1 % over the window.  An empty domain is converged once the window has
+    passed; a domain with a source switched on is not."""
+    o = Oracle(8, 6, 6, 20e-6, -6e7, 6e7, -3e7, 3e7)
+    o.set_convergence(5, 1e-3)
+    o.step(4)
+    assert o.info()["sat_step"] == -1
+    o.step(1)
+    assert o.info()["sat_step"] == 5
+    o2 = Oracle(8, 6, 6, 20e-6, -6e7, 6e7, -3e7, 3e7)
+    o2.set_see(3.0, 400.0, 1.0, 2.0)
+    o2.set_source(1.0, 5e-6, 15e-6, 4.0)
+    o2.set_convergence(5, 1e-3)
+    o2.step(12)
+    assert o2.info()["sat_step"] == -1
+    h = o2.history()
+    assert h.shape == (13, oracle.HIST_COLS)
+    assert np.all(h[:, 0] == np.arange(13))
+
+
+def test_see_disabled_means_no_secondaries():
+    o, f0, sigma, p = _strong_case(6, 6, 6, seed=2)
+    o.set_see(3.0, 400.0, 1.0, 400.0, enabled=False)
+    o.set_state(f0, sigma)
+    _, _, gpe, gsee = o.moments()
+    assert gsee == 0.0 and gpe > 0
+    o.step(1)
+    # Eq. 18 with no SEE: every primary is deposited
+    assert o.surface_charge() == pytest.approx(sigma - QE * p["dt"] * gpe, rel=1e-13)
+
+
+# ---------------------------------------------------------------- Eqs. 19-20
+def test_first_crossover_is_unit_yield():
+    for dmax, amax in ((3.0, 400.0), (6.5, 650.0), (2.0, 250.0)):
+        a1 = oracle.first_crossover(dmax, amax)
+        ref = optimize.brentq(lambda A: oracle.seey(A, 0.0, dmax, amax) - 1.0, 1e-6, amax, xtol=1e-14)
+        assert a1 == pytest.approx(ref, rel=1e-10)
+        assert oracle.seey(a1, 0.0, dmax, amax) == pytest.approx(1.0, abs=1e-12)
+    assert oracle.first_crossover(0.9, 400.0) < 0  # no crossover below unit yield
+
+
+def test_time_of_flight_by_kinematics():
+    """Sec. 3: a secondary leaving normally with energy A0 against a constant
+    restoring acceleration returns after 2 v0/|a_x| (ODE with landing event)."""
+    A0, ax = 2.0, 3e16
+    v0 = math.sqrt(2 * A0 * QE / ME)
+    ev = lambda t, y: y[0]
+    ev.terminal, ev.direction = True, -1
+    sol = integrate.solve_ivp(lambda t, y: [y[1], -ax], (0, 1e-6), [0.0, v0], events=ev,
+                              rtol=1e-12, atol=1e-30, max_step=1e-12, first_step=1e-15)
+    t_land = sol.t_events[0][0]
+    assert oracle.time_of_flight(A0, ax) == pytest.approx(t_land, rel=1e-6)
+
+
+def test_sigma_eq20_from_cosine_averaged_kinematics():
+    """Eq. 20 is Eq. 19 with the squared normal emission speed averaged over
+    the cosine law (<cos^2> = 1/2 by quadrature), E_x = sigma/(2 eps0) and
+    a_x/a_y = E_x/E_y.  Solve Eq. 19 for sigma by root finding."""
+    num, _ = integrate.quad(lambda t: math.cos(t) ** 2 * math.cos(t) * math.sin(t), 0, math.pi / 2)
+    den, _ = integrate.quad(lambda t: math.cos(t) * math.sin(t), 0, math.pi / 2)
+    c2 = num / den
+    A0 = 2.0
+    A1 = oracle.first_crossover(3.0, 400.0)
+    for Ey in (-5e5, -1e6, -3e6):
+        ay = QE * abs(Ey) / ME
+
+        def residual(sig):
+            ax = QE * sig / (2 * EPS0) / ME
+            vn2 = 2 * A0 * QE / ME * c2  # averaged squared normal speed
+            t = 2 * math.sqrt(vn2) / ax
+            l_ef = 0.5 * ay * t * t
+            return 2 / ME * (A1 - A0) * QE - 2 * ay * l_ef  # Eq. 19 in SI
+
+        sig = optimize.brentq(residual, 1e-9, 1.0, xtol=1e-20, rtol=1e-14)
+        assert oracle.sigma_eq20(Ey, A0, A1) == pytest.approx(sig, rel=1e-9)
