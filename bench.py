@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Throughput of the 1D2V flashover step on GB300: phase-space cell-updates/s
+and the step kernel's fraction of the HBM roofline.
+
+Workload (default): 1024 x 256 x 256 cells (67.1 M), velocity spans
+v1 in +-6e7 m/s and v2 in +-3e7 m/s, h_max = 20 um, dt at CFL 0.4,
+delta_max 3, A_max 400 eV, T_se 2 eV, J = 1 A/m^2 on [10, 15] um at
+T_fe = 4 eV, f0 = 1e-6 relative seeded noise; the applied field is swept
+over E_y in {-5e5, -1e6, -3e6} V/m, so one benchmark step advances the
+three field instances by one solver step each (201 M cell-updates).
+The headline precision (f stored and advected in FP32, moments, fluxes,
+surface charge and ledger in FP64) is timed first; the FP64 path on the
+same workload is reported side by side.
+
+Launch: ``python bench.py [--gpus N] [--steps K] [--warmup W]``; for N > 1
+one process per GPU under torchrun, each rank running its own independent
+instances (replicas: the workload has no data exchange between instances).
+``--impl reference`` times the CPU oracle instead (see DESIGN).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2303_14119_gb300 import synth  # noqa: E402
+
+WORKLOAD = "full_1024x256x256"
+METRIC = "phase-space cell-updates/s"
+UNIT = "cell-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--no-side", action="store_true", help="skip the side-by-side precision")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(precision):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu
+    summary, if its source hash matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    from paper_2303_14119_gb300 import _build
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != _build.source_hash():
+        return None
+    key = "bytes_per_launch_%s" % precision
+    return float(vals[key]) if key in vals else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[4 + q] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------- our arm
+def make_grids(fk, w, precision, stream):
+    grids = []
+    for Ey in w.get("Ey_sweep", (w["Ey"],)):
+        g = fk.Grid(w["nx"], w["nv1"], w["nv2"], w["h_max"], -w["v1_span"], w["v1_span"],
+                    -w["v2_span"], w["v2_span"], cfl=w["cfl"], precision=precision,
+                    stream=stream)
+        g.set_fields(Ey)
+        g.set_see(w["delta_max"], w["A_max"], w["k_s"], w["T_se"])
+        g.set_source(w["J"], w["x_lo"], w["x_hi"], w["T_fe"])
+        grids.append(g)
+    return grids
+
+
+def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device):
+    stream = torch.cuda.current_stream().cuda_stream
+    grids = make_grids(fk, w, precision, stream)
+    for g in grids:
+        g.set_f(f0)
+    for _ in range(warmup):
+        for g in grids:
+            g.step(1)
+    for g in grids:
+        g.sync()
+        g.set_kernel_timing(True)
+    clocks = ClockSampler(device)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        for g in grids:
+            g.step(1)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    launches, kms = 0, 0.0
+    for g in grids:
+        n, t = g.kernel_timing()
+        launches += n
+        kms += t
+        g.set_kernel_timing(False)
+        g.sync()
+    cells = w["nx"] * w["nv1"] * w["nv2"]
+    res = dict(ms=ms, launches=launches, kernel_ms=kms, cells=cells, n_inst=len(grids),
+               clocks=ck, grids=grids)
+    return res
+
+
+def e2e_arm(fk, torch, w, precision, f0_pinned, steps):
+    """The user's loop through the C ABI with host buffers: upload f0 from
+    pinned host memory, then per step advance and read sigma and the wall
+    fluxes back, finally read f back; all inside the timed region."""
+    stream = torch.cuda.current_stream().cuda_stream
+    grids = make_grids(fk, w, precision, stream)
+    nx = w["nx"]
+    out_f = torch.empty(f0_pinned.shape, dtype=torch.float64, pin_memory=True).numpy()
+    ne = np.empty(nx)
+    ex = np.empty(nx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in grids:
+        g.set_f(f0_pinned)
+    for _ in range(steps):
+        for g in grids:
+            g.step(1)
+            fk.fk_moments(g.h, nx, ne, ex)
+            g.surface_charge()
+    for g in grids:
+        g.get_f(out_f)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for g in grids:
+        g.close()
+    cells = w["nx"] * w["nv1"] * w["nv2"]
+    n = len(grids)
+    h2d = n * f0_pinned.nbytes / steps
+    d2h = n * (2 * nx * 8 + 2 * 8 + 8) + n * out_f.nbytes / steps
+    return dict(value=n * cells * steps / dt, unit=UNIT, h2d_bytes_per_step=int(h2d),
+                d2h_bytes_per_step=int(d2h), steps=steps)
+
+
+def cpu_baseline(w, seconds=15.0):
+    """The FP64 oracle as it stands, single thread, on a bounded sample: as
+    many whole steps of one field instance of the workload as fit in about
+    `seconds` (at least one)."""
+    import oracle
+    shape = (w["nx"], w["nv1"], w["nv2"])
+    o = oracle.Oracle(*shape, w["h_max"], -w["v1_span"], w["v1_span"], -w["v2_span"],
+                      w["v2_span"], cfl=w["cfl"])
+    o.set_fields(w["Ey"])
+    o.set_see(w["delta_max"], w["A_max"], w["k_s"], w["T_se"])
+    o.set_source(w["J"], w["x_lo"], w["x_hi"], w["T_fe"])
+    o.set_state(synth.initial_f(shape, w["seed"], w["noise_rel"], w["J"], w["T_fe"]), 0.0)
+    cells = int(np.prod(shape))
+    n, t = 0, 0.0
+    while t < seconds or n == 0:
+        t0 = time.perf_counter()
+        o.step(1)
+        t += time.perf_counter() - t0
+        n += 1
+        if n * cells > 2e9:
+            break
+    o.close()
+    return {"value": n * cells / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d step(s) of one %dx%dx%d field instance (E_y=%g V/m), FP64, 1 thread"
+                      % (n, *shape, w["Ey"])}
+
+
+def roofline(res, precision, peak, peak_kind):
+    bpc = 4 if precision == "f32" else 8
+    if res["launches"] == 0:
+        return None
+    avg_s = res["kernel_ms"] / res["launches"] / 1e3
+    alg_bytes = 2 * bpc * res["cells"]  # one read of f^n, one write of f^{n+1}
+    achieved = alg_bytes / avg_s / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": kernel_traffic(precision),
+            "peak_kind": "%s (copy bandwidth)" % peak_kind,
+            "kernel": "fused upwind step", "avg_launch_us": round(avg_s * 1e6, 2),
+            "alg_bytes_per_launch": alg_bytes}
+
+
+def run_ours(args):
+    rank, world, local = dist_env()
+    import torch
+    from paper_2303_14119_gb300 import fk
+    fk.load()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("gloo")
+        dist = td
+    w = synth.WORKLOADS[args.workload]
+    shape = (w["nx"], w["nv1"], w["nv2"])
+    f0 = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    f0[...] = synth.initial_f(shape, w["seed"], w["noise_rel"], w["J"], w["T_fe"])
+    peak, peak_kind = measured_peaks()
+    prec = fk.FK_F32 if args.precision == "f32" else fk.FK_F64
+    res = time_arm(fk, torch, w, prec, f0, args.steps, args.warmup, dist, local)
+    for g in res.pop("grids"):
+        g.close()
+    ms = res["ms"]
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t[0])
+    total_updates = world * res["n_inst"] * res["cells"] * args.steps
+    value = total_updates / (ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": "%s, E_y sweep %s V/m (%d instances per step)"
+                               % (args.workload, list(w.get("Ey_sweep", (w["Ey"],))), res["n_inst"]),
+                   "cells_per_instance": res["cells"], "precision_storage": args.precision,
+                   "accumulators": "f64", "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline(res, args.precision, peak, peak_kind),
+        "gpu_launches": args.steps * res["n_inst"] * 2,
+        "clocks": res["clocks"],
+    }
+    if not args.no_side:
+        other = "f64" if args.precision == "f32" else "f32"
+        oprec = fk.FK_F64 if other == "f64" else fk.FK_F32
+        osteps = max(1, args.steps // (2 if other == "f64" else 1))
+        r2 = time_arm(fk, torch, w, oprec, f0, osteps, args.warmup, dist, local)
+        for g in r2.pop("grids"):
+            g.close()
+        line["side_by_side"] = {other: {
+            "value": world * r2["n_inst"] * r2["cells"] * osteps / (r2["ms"] / 1e3),
+            "ms_per_step": r2["ms"] / osteps, "steps": osteps,
+            "roofline": roofline(r2, other, peak, peak_kind), "clocks": r2["clocks"]}}
+    if not args.no_e2e:
+        e2e = e2e_arm(fk, torch, w, prec, f0, args.e2e_steps)
+        if dist is not None:
+            t = torch.tensor([e2e["value"]], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            e2e["value"] = float(t[0])
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle arm: each step is one FP64 oracle step of one field
+    instance of the workload (a bounded sample), on one host thread."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    w = synth.WORKLOADS[args.workload]
+    shape = (w["nx"], w["nv1"], w["nv2"])
+    o = oracle.Oracle(*shape, w["h_max"], -w["v1_span"], w["v1_span"], -w["v2_span"],
+                      w["v2_span"], cfl=w["cfl"])
+    o.set_fields(w["Ey"])
+    o.set_see(w["delta_max"], w["A_max"], w["k_s"], w["T_se"])
+    o.set_source(w["J"], w["x_lo"], w["x_hi"], w["T_fe"])
+    o.set_state(synth.initial_f(shape, w["seed"], w["noise_rel"], w["J"], w["T_fe"]), 0.0)
+    steps = max(1, min(args.steps, 20))
+    warm = max(0, min(args.warmup, 1))
+    o.step(warm)
+    t0 = time.perf_counter()
+    o.step(steps)
+    t = time.perf_counter() - t0
+    cells = int(np.prod(shape))
+    value = cells * steps / t
+    sample = "%d FP64 oracle step(s) of one %dx%dx%d field instance, 1 thread" % (steps, *shape)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warm, "ms_per_step": t / steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "cells_per_instance": cells},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

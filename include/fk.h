@@ -1,0 +1,202 @@
+/*
+ * fk.h -- C ABI of the GB300 library that advances the electron velocity
+ * distribution f(x, v1, v2) of the 1D2V continuum-kinetic model of vacuum
+ * surface flashover (Sun et al., arXiv 2303.14119).
+ *
+ * Model (Sec. 2): x is the coordinate normal to the insulator, x = 0 the
+ * dielectric surface and x = h_max the vacuum side; v1 = v_x is the normal
+ * velocity and v2 = v_y the tangential velocity along the applied field E_y.
+ * One time step is an explicit, first-order upwind, finite-volume update of
+ * Eq. 2 (advection in x, v1 and v2 plus the field-emission source of Eq. 7),
+ * with the secondary-electron wall boundary of Eqs. 12-16, the absorbing
+ * vacuum boundary of Eq. 17, the surface-charge update of Eq. 18 and the
+ * normal field E_x from the 1D Poisson problem stated after Eq. 2.
+ *
+ * Conventions shared by every call:
+ *  - Grids are uniform and cell-centred: x_k = (k + 1/2) dx, v1_i = v1_min +
+ *    (i + 1/2) dv1, v2_j likewise.  Host arrays of f are FP64, C order
+ *    [k][i][j] (v2 fastest), nx * nv1 * nv2 elements.
+ *  - SI units throughout, except energies and temperatures in eV.
+ *  - Every call returns an fk_status.  Nothing aborts and no C++ exception
+ *    crosses the boundary.  After a failure, fk_last_error() describes it.
+ *  - The library owns all device memory of a grid; it allocates it in
+ *    fk_create_grid and frees it in fk_destroy_grid.  Host buffers passed in
+ *    are owned by the caller and are only read or written during the call
+ *    (copies complete before the call returns).
+ *  - Work is ordered on the grid's CUDA stream.  fk_step only enqueues;
+ *    the getters synchronise that stream.  Errors detected on the device
+ *    (CFL violation, non-finite sums, a pipeline wait that ran out) are
+ *    sticky: the step that meets one leaves f at the last valid state, later
+ *    steps do nothing, and the next getter or fk_sync returns the status.
+ *  - Calls on one grid must not run concurrently from several threads.
+ *    Distinct grids are independent.
+ */
+#ifndef FK_H
+#define FK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fk_grid fk_grid; /* opaque, library-owned */
+
+typedef enum {
+  FK_OK = 0,
+  FK_EINVAL = 1,   /* an argument is out of range or NULL */
+  FK_ENOMEM = 2,   /* device or host allocation failed */
+  FK_ECUDA = 3,    /* a CUDA runtime call failed (message in fk_last_error) */
+  FK_ECFL = 4,     /* |c_x| + |c_1| + |c_2| > 1 somewhere: the explicit
+                      upwind step would not keep f >= 0 */
+  FK_ENUMERIC = 5, /* a moment or flux became NaN or infinite */
+  FK_ETIMEOUT = 6, /* a bounded wait inside a kernel ran out */
+  FK_ESTATE = 7    /* call not valid in the grid's current state */
+} fk_status;
+
+typedef enum {
+  FK_F64 = 0, /* f stored and advected in FP64 */
+  FK_F32 = 1  /* f stored and advected in FP32; moments, fluxes, surface
+                 charge, field and ledger stay FP64 */
+} fk_precision;
+
+/* Grid description.
+ * nx, nv1, nv2 >= 2 cells; h_max > 0 (m); v1_min < v1_max, v2_min < v2_max
+ * (m/s); dt > 0 (s), or dt <= 0 to take dt = cfl * dx / max(|v1_min|,
+ * |v1_max|) with cfl > 0; history_capacity = rows kept in the device history
+ * ring (0 selects 65536).  Sec. 2, paragraph on default parameters: "grid
+ * and time resolutions are prescribed by the CFL conditions". */
+typedef struct {
+  int32_t nx, nv1, nv2;
+  int32_t precision; /* fk_precision */
+  double h_max;
+  double v1_min, v1_max, v2_min, v2_max;
+  double dt;
+  double cfl;
+  int64_t history_capacity;
+  int32_t device; /* CUDA device ordinal */
+  int32_t reserved;
+} fk_grid_desc;
+
+/* Create a grid with f = 0 and sigma = 0 everywhere (Sec. 2: the simulation
+ * starts with no space or surface charge), no applied field, E_x
+ * self-consistent, secondary emission and source switched off.
+ * cuda_stream: a cudaStream_t to order the grid's work on, or NULL for a
+ * stream the grid creates and owns.  On success *out receives the grid.
+ * Returns FK_EINVAL for a bad description, FK_ECFL if the x-Courant number
+ * max|v1| dt/dx exceeds 1, FK_ENOMEM / FK_ECUDA on device failures. */
+fk_status fk_create_grid(const fk_grid_desc *desc, void *cuda_stream, fk_grid **out);
+
+/* Release the grid and all its device memory.  NULL is accepted. */
+fk_status fk_destroy_grid(fk_grid *grid);
+
+/* Fields of Sec. 2 (text after Eq. 2).  Ey (V/m) is the applied tangential
+ * field, constant and <= 0 (cathode on the left).  self_consistent != 0:
+ * E_x(x) from the 1D Poisson problem with E_x = sigma/(2 eps0) at the
+ * dielectric and V = 0 at the vacuum side, i.e. Gauss's law integrated from
+ * the wall over the electron space charge -e n_e; otherwise E_x = Ex_external
+ * everywhere.  Acceleration of electrons: a = -e E / m_e. */
+fk_status fk_set_fields(fk_grid *grid, double Ey, int self_consistent, double Ex_external);
+
+/* Secondary electron emission, Sec. 2, Eqs. 8-16.  The yield matrix
+ * delta(i, j) of Eqs. 8-11 (delta_max, A_max in eV, smoothness k_s >= 0) is
+ * built once over the grid cells with v1 < 0.  Each step the primary flux
+ * dGamma_pe = -v1 f(x=0) dv1 dv2 (Eq. 13) and Gamma_see = sum delta dGamma_pe
+ * (Eqs. 12, 14) are re-emitted at x = 0 into v1 > 0 as the half-Maxwellian
+ * of Eq. 15 at temperature T_se (eV), normalised on the grid so that the
+ * emitted flux equals Gamma_see.  enabled = 0 switches re-emission off
+ * (delta treated as 0; every primary is then deposited on the surface). */
+fk_status fk_set_see(fk_grid *grid, double delta_max, double A_max_eV, double k_s,
+                     double T_se_eV, int enabled);
+
+/* Field-emission source of Eq. 7: J (A/m^2, >= 0, 0 switches it off)
+ * injected uniformly on the cells whose centres lie in [x_lo, x_hi] (m),
+ * with a velocity shape that is Maxwellian in v1 and half-Maxwellian on
+ * v2 > 0 at temperature T_fe (eV), normalised on the grid so that exactly
+ * J/e electrons per m^2 per s are injected.  FK_EINVAL if J > 0 and no cell
+ * centre lies in the band. */
+fk_status fk_set_source(fk_grid *grid, double J, double x_lo, double x_hi, double T_fe_eV);
+
+/* Convergence test of Sec. 2 (paragraph after Eq. 18): the run is saturated
+ * at the first step n >= window with |q_n - q_{n-window}| <= rel_tol |q_n|
+ * for q = sigma, Gamma_pe and Gamma_see.  Defaults: window 10000, rel_tol
+ * 1e-3.  FK_EINVAL unless 1 <= window < history_capacity and rel_tol >= 0. */
+fk_status fk_set_convergence(fk_grid *grid, int64_t window, double rel_tol);
+
+/* Advance n >= 0 time steps (forward Euler, all fluxes from f^n; Eq. 18
+ * updates sigma for the next step's E_x).  Stream-ordered and asynchronous:
+ * it returns once the work is enqueued.  Returns a sticky device error seen
+ * by an earlier synchronising call (FK_ECFL, FK_ENUMERIC, FK_ETIMEOUT). */
+fk_status fk_step(fk_grid *grid, int64_t n);
+
+/* Wait for the grid's stream and report any sticky device error. */
+fk_status fk_sync(fk_grid *grid);
+
+/* Moments of the current state (synchronises).  n_e[nx] (m^-3) and Ex[nx]
+ * (V/m) at cell centres; *gamma_pe and *gamma_see (m^-2 s^-1) of Eqs. 13-14
+ * evaluated on the x = 0 plane.  Any pointer may be NULL. */
+fk_status fk_moments(fk_grid *grid, double *n_e, double *Ex, double *gamma_pe,
+                     double *gamma_see);
+
+/* Surface charge density sigma_e (C/m^2) of the current state, Eq. 18. */
+fk_status fk_surface_charge(fk_grid *grid, double *sigma);
+
+/* Per-step history (Fig. 3 quantities), one row of FK_HISTORY_COLS doubles
+ * per state: step, time (s), sigma (C/m^2), Gamma_pe, Gamma_see, Gamma_vac
+ * (m^-2 s^-1), areal electron count N = sum n_e dx (m^-2), E_x at the first
+ * cell centre (V/m).  Copies the most recent min(max_rows, stored) rows,
+ * oldest first, into out[rows][FK_HISTORY_COLS]; *rows receives the count. */
+#define FK_HISTORY_COLS 8
+fk_status fk_history(fk_grid *grid, double *out, int64_t max_rows, int64_t *rows);
+
+/* Conservation ledger since the last reset (fk_set_f, fk_set_surface_charge
+ * or creation), FK_LEDGER_LEN doubles: N, N0, emitted, primary (wall),
+ * vacuum, velocity-edge loss, injected, sigma0, secondary -- the six
+ * cumulative terms are time integrals (m^-2) of the fluxes of each step's
+ * starting state, so that N - N0 = emitted - primary - vacuum - loss +
+ * injected and (sigma - sigma0)/e = secondary - primary up to rounding. */
+#define FK_LEDGER_LEN 9
+fk_status fk_ledger(fk_grid *grid, double *out);
+
+/* Step index of the current state and the first saturated step (-1 if the
+ * convergence test has not passed). */
+fk_status fk_step_count(fk_grid *grid, int64_t *step, int64_t *saturated_step);
+
+/* Copy f of the current state to host FP64 [nx][nv1][nv2] (synchronises). */
+fk_status fk_get_f(fk_grid *grid, double *host_f);
+
+/* Replace f (host FP64 [nx][nv1][nv2], values finite) and restart the run at
+ * step 0: history cleared, ledger baseline taken from the new state.  An FP32
+ * grid rounds each value to nearest. */
+fk_status fk_set_f(fk_grid *grid, const double *host_f);
+
+/* Replace sigma (C/m^2) and restart the run at step 0 like fk_set_f. */
+fk_status fk_set_surface_charge(fk_grid *grid, double sigma);
+
+/* Grid facts: out[0..5] = dx, dv1, dv2, dt (s), c2 (signed v2-Courant number
+ * a2 dt/dv2), max |c_x|.  Host-side, no synchronisation. */
+fk_status fk_grid_info(const fk_grid *grid, double *out);
+
+/* Kernel timing (tracing).  enabled != 0: later fk_step calls launch each
+ * step directly (no graph replay) and record a CUDA event pair around every
+ * launch of the fused step kernel on the grid's stream; enabled = 0 returns
+ * to graph replay.  Switching discards pending records. */
+fk_status fk_set_kernel_timing(fk_grid *grid, int enabled);
+
+/* Synchronise and report the step-kernel launches recorded since the last
+ * call (at most 8192 are kept; later ones are counted but not timed):
+ * *launches = launches timed, *total_ms = sum of their durations (ms).
+ * The records are consumed. */
+fk_status fk_kernel_timing(fk_grid *grid, int64_t *launches, double *total_ms);
+
+/* Text of the last error on this grid ("" if none).  grid may be NULL for
+ * errors of fk_create_grid on the calling thread.  Valid until the next call
+ * on the same grid. */
+const char *fk_last_error(const fk_grid *grid);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FK_H */

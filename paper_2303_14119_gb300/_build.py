@@ -1,0 +1,88 @@
+"""Build the CUDA library ``libflashkin.so`` in-tree for sm_103a.
+
+Each ``csrc/*.cu`` file compiles to an object in ``_build/`` in parallel;
+the objects link into one shared library with the CUDA runtime linked
+statically.  Sources newer than the library trigger a rebuild.
+"""
+from __future__ import annotations
+
+import glob
+import os
+import subprocess
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+OUT = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libflashkin.so")
+INCLUDE = os.path.join(ROOT, "include")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         "-Xcompiler", "-ffp-contract=off",
+         "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+_lock = threading.Lock()
+
+
+def _sources():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def _deps():
+    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "fk.h"),
+                                                                  os.path.abspath(__file__)]
+
+
+def stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(p) > t for p in _deps())
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    with _lock:
+        if not force and not stale():
+            return LIB
+        os.makedirs(OUT, exist_ok=True)
+        procs, objs = [], []
+        for src in _sources():
+            obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+            cmd = [NVCC, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj]
+            if verbose:
+                print(" ".join(cmd))
+            procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+            objs.append(obj)
+        errors = []
+        for src, p in procs:
+            out, _ = p.communicate()
+            if verbose or p.returncode != 0:
+                print(out.decode(errors="replace"))
+            if p.returncode != 0:
+                errors.append(src)
+        if errors:
+            raise RuntimeError("nvcc failed for: " + ", ".join(errors))
+        tmp = LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call([NVCC, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+
+def source_hash() -> str:
+    """Short hash of the CUDA sources (identifies the kernels a profile was
+    taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh"))):
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    import sys
+    build(force="--force" in sys.argv, verbose=True)
+    print(LIB)

@@ -1,0 +1,649 @@
+// Host side of the C ABI declared in include/fk.h: the grid object, its
+// device buffers, parameter tables, CUDA-graph replay of the step loop and
+// the synchronising getters.
+//
+// Paper: Sun et al., arXiv 2303.14119, Sec. 2 (model, boundary conditions,
+// surface charge, convergence test).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fk_internal.cuh"
+
+using namespace fk;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kGraphSteps = 32;  // steps per captured graph (even)
+constexpr int kMaxTimed = 8192;  // step-kernel launches timed between reads
+constexpr size_t kStageElems = size_t(1) << 23;  // FP64 staging chunk, 64 MB
+
+}  // namespace
+
+struct fk_grid {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;
+  fk_grid_desc desc{};
+  int prec = FK_F64;
+  int nx = 0, nv1 = 0, nv2 = 0, pitch = 0;
+  size_t esize = 8;
+  double dx = 0, dv1 = 0, dv2 = 0, dt = 0;
+  Params prm{};
+  Params* d_prm = nullptr;
+  DevState* d_st = nullptr;
+  void* d_f[2] = {nullptr, nullptr};
+  int enq_cur = 0;            // buffer the next enqueued step reads
+  int base_cur = 0;           // buffer that held state base_step
+  long long base_step = 0;
+  Tables tab{};
+  Partials part{};
+  double *d_ne = nullptr, *d_Ex = nullptr, *d_c1 = nullptr, *d_hist = nullptr;
+  void* d_stage = nullptr;
+  // physics parameters as last set
+  double Ey = 0, Ex_ext = 0;
+  int self_consistent = 1;
+  double delta_max = 0, A_max = 1, k_s = 1, T_se = 1;
+  int see_enabled = 0;
+  double J = 0, x_lo = 0, x_hi = 0, T_fe = 1;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  unsigned known_flags = 0;
+  // kernel timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;  // pairs: 2*r = start, 2*r+1 = stop
+  int ev_used = 0;              // pairs recorded since the last read
+  std::string err;
+};
+
+namespace {
+
+fk_status fail(fk_grid* g, fk_status s, const std::string& msg) {
+  if (g)
+    g->err = msg;
+  else
+    g_create_error = msg;
+  return s;
+}
+
+fk_status cuda_fail(fk_grid* g, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(g, e == cudaErrorMemoryAllocation ? FK_ENOMEM : FK_ECUDA, m);
+}
+
+#define FK_CUDA(g, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((g), e_, #call); \
+  } while (0)
+
+fk_status flags_status(fk_grid* g, unsigned flags) {
+  if (flags & kFlagTimeout) return fail(g, FK_ETIMEOUT, "a bounded wait inside the step kernel ran out");
+  if (flags & kFlagNumeric) return fail(g, FK_ENUMERIC, "a moment or flux became non-finite");
+  if (flags & kFlagCfl)
+    return fail(g, FK_ECFL, "|c_x| + |c_1| + |c_2| exceeds 1: the explicit upwind step is unstable");
+  return FK_OK;
+}
+
+StepArgs make_args(fk_grid* g, int cur) {
+  StepArgs a{};
+  a.f_in = g->d_f[cur];
+  a.f_out = g->d_f[cur ^ 1];
+  a.nx = g->nx;
+  a.nv1 = g->nv1;
+  a.nv2 = g->nv2;
+  a.pitch = g->pitch;
+  a.c1 = g->d_c1;
+  a.prm = g->d_prm;
+  a.st = g->d_st;
+  a.tab = g->tab;
+  a.part = g->part;
+  return a;
+}
+
+fk_status upload_params(fk_grid* g) {
+  FK_CUDA(g, cudaMemcpyAsync(g->d_prm, &g->prm, sizeof(Params), cudaMemcpyHostToDevice, g->stream));
+  return FK_OK;
+}
+
+// Synchronise, read the device scalars, and re-base the buffer bookkeeping
+// on the last valid state.
+fk_status sync_state(fk_grid* g, DevState* out) {
+  FK_CUDA(g, cudaSetDevice(g->dev));
+  FK_CUDA(g, cudaMemcpyAsync(out, g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
+  FK_CUDA(g, cudaStreamSynchronize(g->stream));
+  const long long adv = out->step - g->base_step;
+  g->base_cur = (int)((g->base_cur + (adv & 1)) & 1);
+  g->base_step = out->step;
+  g->enq_cur = g->base_cur;
+  g->known_flags = out->flags;
+  return FK_OK;
+}
+
+// Evaluate the current state: moments of f, then finalize in `mode`.
+fk_status evaluate(fk_grid* g, int mode) {
+  StepArgs a = make_args(g, g->enq_cur);
+  FK_CUDA(g, launch_step(a, g->prec, 1, g->stream));
+  FK_CUDA(g, launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_hist, mode, g->stream));
+  return FK_OK;
+}
+
+fk_status clear_flags(fk_grid* g, unsigned mask) {
+  // flags live in DevState; clear with a read-modify-write through the host
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  st.flags &= ~mask;
+  FK_CUDA(g, cudaMemcpyAsync(&g->d_st->flags, &st.flags, sizeof(unsigned), cudaMemcpyHostToDevice,
+                             g->stream));
+  g->known_flags = st.flags;
+  return FK_OK;
+}
+
+fk_status rebuild_tables(fk_grid* g) {
+  const double W = (g->prm.band_hi - g->prm.band_lo) * g->dx;
+  const double j_over_ew = (g->J > 0.0 && W > 0.0) ? g->J / kQe / W : 0.0;
+  FK_CUDA(g, launch_tables(g->tab, g->d_prm, g->nv1, g->nv2, g->desc.v1_min, g->desc.v2_min,
+                           g->dv1, g->dv2, g->dt, g->dx, g->delta_max, g->A_max, g->k_s,
+                           g->T_se, g->T_fe, j_over_ew, g->stream));
+  return FK_OK;
+}
+
+// Parameters changed: rebuild tables, re-evaluate the current state and
+// rewrite its history row.  Clears a CFL flag (the new fields may fix it).
+fk_status refresh(fk_grid* g) {
+  fk_status s = clear_flags(g, kFlagCfl);
+  if (s != FK_OK) return s;
+  if ((s = upload_params(g)) != FK_OK) return s;
+  if ((s = rebuild_tables(g)) != FK_OK) return s;
+  return evaluate(g, kModeRefresh);
+}
+
+void free_grid(fk_grid* g) {
+  if (!g) return;
+  cudaSetDevice(g->dev);
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  for (int p = 0; p < 2; p++)
+    if (g->graph[p]) cudaGraphExecDestroy(g->graph[p]);
+  void* ptrs[] = {g->d_prm, g->d_st, g->d_f[0], g->d_f[1], g->tab.v1, g->tab.cx,
+                  g->tab.delta, g->tab.gse, g->tab.src, g->tab.src32, g->tab.gfe_raw,
+                  g->part.n, g->part.lv, g->part.pe, g->part.see, g->part.vac,
+                  g->d_ne, g->d_Ex, g->d_c1, g->d_hist, g->d_stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+}
+
+template <typename P>
+cudaError_t dalloc(P** p, size_t bytes) {
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16);
+}
+
+fk_status build_graph(fk_grid* g, int parity) {
+  cudaStream_t cs = g->cap_stream;
+  FK_CUDA(g, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  int cur = parity;
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < kGraphSteps && e == cudaSuccess; s++) {
+    StepArgs a = make_args(g, cur);
+    e = launch_step(a, g->prec, 0, cs);
+    if (e == cudaSuccess)
+      e = launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_hist, kModeStep, cs);
+    cur ^= 1;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(g, e, "capturing the step graph");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(g, e2, "cudaStreamEndCapture");
+  cudaError_t e3 = cudaGraphInstantiate(&g->graph[parity], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e3 != cudaSuccess) return cuda_fail(g, e3, "cudaGraphInstantiate");
+  return FK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** out) {
+  g_create_error.clear();
+  if (!desc || !out) return fail(nullptr, FK_EINVAL, "desc and out must not be NULL");
+  *out = nullptr;
+  const fk_grid_desc& d = *desc;
+  if (d.nx < 2 || d.nv1 < 2 || d.nv2 < 2)
+    return fail(nullptr, FK_EINVAL, "nx, nv1, nv2 must be >= 2");
+  if (d.nv1 > (1 << 16) || d.nv2 > (1 << 16) || d.nx > (1 << 20))
+    return fail(nullptr, FK_EINVAL, "grid dimension too large");
+  if (!(d.h_max > 0) || !(d.v1_min < d.v1_max) || !(d.v2_min < d.v2_max) ||
+      !isfinite(d.h_max) || !isfinite(d.v1_min) || !isfinite(d.v1_max) ||
+      !isfinite(d.v2_min) || !isfinite(d.v2_max))
+    return fail(nullptr, FK_EINVAL, "need h_max > 0, v1_min < v1_max, v2_min < v2_max, finite");
+  if (!(d.dt > 0) && !(d.cfl > 0))
+    return fail(nullptr, FK_EINVAL, "need dt > 0 or cfl > 0");
+  if (d.precision != FK_F64 && d.precision != FK_F32)
+    return fail(nullptr, FK_EINVAL, "precision must be FK_F64 or FK_F32");
+  if (d.history_capacity < 0) return fail(nullptr, FK_EINVAL, "history_capacity must be >= 0");
+
+  fk_grid* g = new (std::nothrow) fk_grid();
+  if (!g) return fail(nullptr, FK_ENOMEM, "host allocation failed");
+  g->desc = d;
+  g->dev = d.device;
+  g->prec = d.precision;
+  g->nx = d.nx;
+  g->nv1 = d.nv1;
+  g->nv2 = d.nv2;
+  g->esize = d.precision == FK_F32 ? 4 : 8;
+  const int align = (int)(16 / g->esize);  // 16-byte rows
+  g->pitch = (d.nv2 + align - 1) / align * align;
+  g->dx = d.h_max / d.nx;
+  g->dv1 = (d.v1_max - d.v1_min) / d.nv1;
+  g->dv2 = (d.v2_max - d.v2_min) / d.nv2;
+  const double vmax = fmax(fabs(d.v1_min), fabs(d.v1_max));
+  g->dt = d.dt > 0 ? d.dt : d.cfl * g->dx / vmax;
+  double cx_max = 0.0;
+  for (int i = 0; i < d.nv1; i++)
+    cx_max = fmax(cx_max, fabs(d.v1_min + (i + 0.5) * g->dv1) * g->dt / g->dx);
+
+  Params& p = g->prm;
+  p.dx = g->dx;
+  p.dv1 = g->dv1;
+  p.dv2 = g->dv2;
+  p.dt = g->dt;
+  p.Ey = 0;
+  p.Ex_ext = 0;
+  p.c2 = 0;
+  p.cx_max = cx_max;
+  p.inj = 0;
+  p.sat_tol = 1e-3;
+  p.sat_window = 10000;
+  p.hist_cap = d.history_capacity > 0 ? d.history_capacity : 65536;
+  p.self_consistent = 1;
+  p.see_enabled = 0;
+  p.band_lo = p.band_hi = 0;
+  if (p.sat_window >= p.hist_cap) p.sat_window = p.hist_cap - 1;
+  if (cx_max > 1.0 + 1e-12) {
+    delete g;
+    return fail(nullptr, FK_ECFL, "max |v1| dt / dx exceeds 1");
+  }
+
+#define CREATE_CUDA(call)                                     \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) {                                  \
+      fk_status s_ = cuda_fail(nullptr, e_, #call);           \
+      free_grid(g);                                           \
+      return s_;                                              \
+    }                                                         \
+  } while (0)
+
+  CREATE_CUDA(cudaSetDevice(g->dev));
+  if (cuda_stream) {
+    g->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    CREATE_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    g->own_stream = true;
+  }
+  CREATE_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+  const size_t nv = (size_t)d.nv1 * d.nv2;
+  const size_t fbytes = (size_t)d.nx * d.nv1 * g->pitch * g->esize;
+  g->part.nu = step_units_per_plane(d.nv1, d.nv2);
+  const size_t nparts = (size_t)d.nx * g->part.nu;
+  CREATE_CUDA(dalloc(&g->d_prm, sizeof(Params)));
+  CREATE_CUDA(dalloc(&g->d_st, sizeof(DevState)));
+  CREATE_CUDA(dalloc(&g->d_f[0], fbytes));
+  CREATE_CUDA(dalloc(&g->d_f[1], fbytes));
+  CREATE_CUDA(dalloc(&g->tab.v1, d.nv1 * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->tab.cx, d.nv1 * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->tab.delta, nv * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->tab.gse, nv * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->tab.src, nv * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->tab.src32, nv * sizeof(float)));
+  CREATE_CUDA(dalloc(&g->tab.gfe_raw, nv * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->part.n, nparts * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->part.lv, nparts * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->part.pe, g->part.nu * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->part.see, g->part.nu * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->part.vac, g->part.nu * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->d_ne, d.nx * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->d_Ex, d.nx * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->d_c1, d.nx * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->d_hist, (size_t)p.hist_cap * FK_HISTORY_COLS * sizeof(double)));
+  CREATE_CUDA(cudaMemsetAsync(g->d_f[0], 0, fbytes, g->stream));
+  CREATE_CUDA(cudaMemsetAsync(g->d_f[1], 0, fbytes, g->stream));
+  CREATE_CUDA(cudaMemsetAsync(g->d_st, 0, sizeof(DevState), g->stream));
+  CREATE_CUDA(cudaMemsetAsync(g->part.pe, 0, g->part.nu * sizeof(double), g->stream));
+  CREATE_CUDA(cudaMemsetAsync(g->part.see, 0, g->part.nu * sizeof(double), g->stream));
+  CREATE_CUDA(cudaMemsetAsync(g->part.vac, 0, g->part.nu * sizeof(double), g->stream));
+  CREATE_CUDA(cudaMemsetAsync(g->part.lv, 0, nparts * sizeof(double), g->stream));
+#undef CREATE_CUDA
+  fk_status s = upload_params(g);
+  if (s == FK_OK) s = rebuild_tables(g);
+  if (s == FK_OK) s = evaluate(g, kModeReset);
+  if (s == FK_OK) {
+    DevState st;
+    s = sync_state(g, &st);
+  }
+  if (s != FK_OK) {
+    g_create_error = g->err;
+    free_grid(g);
+    return s;
+  }
+  *out = g;
+  return FK_OK;
+}
+
+fk_status fk_destroy_grid(fk_grid* g) {
+  free_grid(g);
+  return FK_OK;
+}
+
+fk_status fk_set_fields(fk_grid* g, double Ey, int self_consistent, double Ex_external) {
+  if (!g) return FK_EINVAL;
+  if (!(Ey <= 0.0) || !isfinite(Ey) || !isfinite(Ex_external))
+    return fail(g, FK_EINVAL, "E_y must be finite and <= 0 (cathode on the left); E_x finite");
+  g->Ey = Ey;
+  g->Ex_ext = Ex_external;
+  g->self_consistent = self_consistent ? 1 : 0;
+  g->prm.Ey = Ey;
+  g->prm.Ex_ext = Ex_external;
+  g->prm.self_consistent = g->self_consistent;
+  g->prm.c2 = (-kQe * Ey / kMe) * g->dt / g->dv2;
+  return refresh(g);
+}
+
+fk_status fk_set_see(fk_grid* g, double delta_max, double A_max_eV, double k_s, double T_se_eV,
+                     int enabled) {
+  if (!g) return FK_EINVAL;
+  if (!(delta_max >= 0.0) || !(A_max_eV > 0.0) || !(k_s >= 0.0) || !(T_se_eV > 0.0) ||
+      !isfinite(delta_max) || !isfinite(A_max_eV) || !isfinite(k_s) || !isfinite(T_se_eV))
+    return fail(g, FK_EINVAL, "need delta_max >= 0, A_max > 0, k_s >= 0, T_se > 0");
+  g->delta_max = delta_max;
+  g->A_max = A_max_eV;
+  g->k_s = k_s;
+  g->T_se = T_se_eV;
+  g->see_enabled = enabled ? 1 : 0;
+  g->prm.see_enabled = g->see_enabled;
+  return refresh(g);
+}
+
+fk_status fk_set_source(fk_grid* g, double J, double x_lo, double x_hi, double T_fe_eV) {
+  if (!g) return FK_EINVAL;
+  if (!(J >= 0.0) || !(x_lo <= x_hi) || !(T_fe_eV > 0.0) || !isfinite(J) || !isfinite(T_fe_eV))
+    return fail(g, FK_EINVAL, "need J >= 0, x_lo <= x_hi, T_fe > 0");
+  int lo = -1, hi = -1;
+  for (int k = 0; k < g->nx; k++) {
+    const double x = (k + 0.5) * g->dx;
+    if (x >= x_lo && x <= x_hi) {
+      if (lo < 0) lo = k;
+      hi = k + 1;
+    }
+  }
+  if (J > 0.0 && lo < 0) return fail(g, FK_EINVAL, "no cell centre lies in [x_lo, x_hi]");
+  g->J = J;
+  g->x_lo = x_lo;
+  g->x_hi = x_hi;
+  g->T_fe = T_fe_eV;
+  if (J > 0.0) {
+    g->prm.band_lo = lo;
+    g->prm.band_hi = hi;
+    g->prm.inj = J / kQe;
+  } else {
+    g->prm.band_lo = g->prm.band_hi = 0;
+    g->prm.inj = 0.0;
+  }
+  return refresh(g);
+}
+
+fk_status fk_set_convergence(fk_grid* g, int64_t window, double rel_tol) {
+  if (!g) return FK_EINVAL;
+  if (window < 1 || window >= g->prm.hist_cap || !(rel_tol >= 0.0))
+    return fail(g, FK_EINVAL, "need 1 <= window < history_capacity and rel_tol >= 0");
+  g->prm.sat_window = window;
+  g->prm.sat_tol = rel_tol;
+  return upload_params(g);
+}
+
+fk_status fk_step(fk_grid* g, int64_t n) {
+  if (!g) return FK_EINVAL;
+  if (n < 0) return fail(g, FK_EINVAL, "n must be >= 0");
+  if (g->known_flags) return flags_status(g, g->known_flags);
+  FK_CUDA(g, cudaSetDevice(g->dev));
+  while (n > 0) {
+    if (g->timing) {
+      StepArgs a = make_args(g, g->enq_cur);
+      const bool rec = g->ev_used < kMaxTimed;
+      if (rec) FK_CUDA(g, cudaEventRecord(g->ev[2 * g->ev_used], g->stream));
+      FK_CUDA(g, launch_step(a, g->prec, 0, g->stream));
+      if (rec) FK_CUDA(g, cudaEventRecord(g->ev[2 * g->ev_used + 1], g->stream));
+      if (rec) g->ev_used++;
+      FK_CUDA(g, launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_hist, kModeStep, g->stream));
+      g->enq_cur ^= 1;
+      n -= 1;
+    } else if (n >= kGraphSteps) {
+      if (!g->graph[g->enq_cur]) {
+        fk_status s = build_graph(g, g->enq_cur);
+        if (s != FK_OK) return s;
+      }
+      FK_CUDA(g, cudaGraphLaunch(g->graph[g->enq_cur], g->stream));
+      n -= kGraphSteps;  // even: the current buffer is unchanged
+    } else {
+      StepArgs a = make_args(g, g->enq_cur);
+      FK_CUDA(g, launch_step(a, g->prec, 0, g->stream));
+      FK_CUDA(g, launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_hist, kModeStep, g->stream));
+      g->enq_cur ^= 1;
+      n -= 1;
+    }
+  }
+  return FK_OK;
+}
+
+fk_status fk_sync(fk_grid* g) {
+  if (!g) return FK_EINVAL;
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  return flags_status(g, st.flags);
+}
+
+fk_status fk_moments(fk_grid* g, double* n_e, double* Ex, double* gamma_pe, double* gamma_see) {
+  if (!g) return FK_EINVAL;
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  if (n_e) FK_CUDA(g, cudaMemcpy(n_e, g->d_ne, g->nx * sizeof(double), cudaMemcpyDeviceToHost));
+  if (Ex) FK_CUDA(g, cudaMemcpy(Ex, g->d_Ex, g->nx * sizeof(double), cudaMemcpyDeviceToHost));
+  if (gamma_pe) *gamma_pe = st.g_pe;
+  if (gamma_see) *gamma_see = st.g_see;
+  return flags_status(g, st.flags);
+}
+
+fk_status fk_surface_charge(fk_grid* g, double* sigma) {
+  if (!g || !sigma) return FK_EINVAL;
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  *sigma = st.sigma;
+  return flags_status(g, st.flags);
+}
+
+fk_status fk_history(fk_grid* g, double* out, int64_t max_rows, int64_t* rows) {
+  if (!g || !rows || (max_rows > 0 && !out)) return FK_EINVAL;
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  const long long cap = g->prm.hist_cap;
+  // rows 0..step are stored (the ring keeps the last cap of them)
+  const long long total = st.step + 1;
+  long long n = std::min<long long>(std::min<long long>(max_rows, total), cap);
+  if (n < 0) n = 0;
+  const long long first = total - n;
+  for (long long r = 0; r < n;) {
+    const long long slot = (first + r) % cap;
+    const long long run = std::min<long long>(n - r, cap - slot);
+    FK_CUDA(g, cudaMemcpy(out + r * FK_HISTORY_COLS, g->d_hist + slot * FK_HISTORY_COLS,
+                          run * FK_HISTORY_COLS * sizeof(double), cudaMemcpyDeviceToHost));
+    r += run;
+  }
+  *rows = n;
+  return flags_status(g, st.flags);
+}
+
+fk_status fk_ledger(fk_grid* g, double* out) {
+  if (!g || !out) return FK_EINVAL;
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  out[0] = st.n_tot;
+  out[1] = st.n0;
+  out[2] = st.cum_emit;
+  out[3] = st.cum_pe;
+  out[4] = st.cum_vac;
+  out[5] = st.cum_lv;
+  out[6] = st.cum_inj;
+  out[7] = st.sigma0;
+  out[8] = st.cum_see;
+  return flags_status(g, st.flags);
+}
+
+fk_status fk_step_count(fk_grid* g, int64_t* step, int64_t* saturated_step) {
+  if (!g) return FK_EINVAL;
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  if (step) *step = st.step;
+  if (saturated_step) *saturated_step = st.sat_step;
+  return flags_status(g, st.flags);
+}
+
+fk_status fk_get_f(fk_grid* g, double* host_f) {
+  if (!g || !host_f) return FK_EINVAL;
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  const void* src = g->d_f[g->base_cur];
+  const size_t rows = (size_t)g->nx * g->nv1;
+  if (g->prec == FK_F64) {
+    FK_CUDA(g, cudaMemcpy2D(host_f, g->nv2 * sizeof(double), src, g->pitch * sizeof(double),
+                            g->nv2 * sizeof(double), rows, cudaMemcpyDeviceToHost));
+  } else {
+    if (!g->d_stage) FK_CUDA(g, cudaMalloc(&g->d_stage, kStageElems * sizeof(double)));
+    const size_t rows_per = std::max<size_t>(1, kStageElems / g->nv2);
+    for (size_t r0 = 0; r0 < rows; r0 += rows_per) {
+      const size_t nr = std::min(rows_per, rows - r0);
+      FK_CUDA(g, launch_convert(static_cast<const float*>(src) + r0 * g->pitch, g->d_stage, nr,
+                                g->nv2, g->pitch, 0, g->stream));
+      FK_CUDA(g, cudaMemcpyAsync(host_f + r0 * g->nv2, g->d_stage, nr * g->nv2 * sizeof(double),
+                                 cudaMemcpyDeviceToHost, g->stream));
+      FK_CUDA(g, cudaStreamSynchronize(g->stream));
+    }
+  }
+  return flags_status(g, st.flags);
+}
+
+fk_status fk_set_f(fk_grid* g, const double* host_f) {
+  if (!g || !host_f) return FK_EINVAL;
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  void* dst = g->d_f[0];
+  const size_t rows = (size_t)g->nx * g->nv1;
+  if (g->prec == FK_F64) {
+    FK_CUDA(g, cudaMemcpy2DAsync(dst, g->pitch * sizeof(double), host_f, g->nv2 * sizeof(double),
+                                 g->nv2 * sizeof(double), rows, cudaMemcpyHostToDevice, g->stream));
+  } else {
+    if (!g->d_stage) FK_CUDA(g, cudaMalloc(&g->d_stage, kStageElems * sizeof(double)));
+    const size_t rows_per = std::max<size_t>(1, kStageElems / g->nv2);
+    for (size_t r0 = 0; r0 < rows; r0 += rows_per) {
+      const size_t nr = std::min(rows_per, rows - r0);
+      FK_CUDA(g, cudaMemcpyAsync(g->d_stage, host_f + r0 * g->nv2, nr * g->nv2 * sizeof(double),
+                                 cudaMemcpyHostToDevice, g->stream));
+      FK_CUDA(g, launch_convert(g->d_stage, static_cast<float*>(dst) + r0 * g->pitch, nr, g->nv2,
+                                g->pitch, 1, g->stream));
+      FK_CUDA(g, cudaStreamSynchronize(g->stream));  // staging buffer reuse
+    }
+  }
+  g->base_cur = g->enq_cur = 0;
+  g->base_step = 0;
+  // every sticky flag belongs to the replaced state
+  FK_CUDA(g, cudaMemsetAsync(&g->d_st->flags, 0, sizeof(unsigned), g->stream));
+  g->known_flags = 0;
+  s = evaluate(g, kModeReset);
+  if (s != FK_OK) return s;
+  if ((s = sync_state(g, &st)) != FK_OK) return s;
+  return flags_status(g, st.flags);
+}
+
+fk_status fk_set_surface_charge(fk_grid* g, double sigma) {
+  if (!g || !isfinite(sigma)) return g ? fail(g, FK_EINVAL, "sigma must be finite") : FK_EINVAL;
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  FK_CUDA(g, cudaMemcpyAsync(&g->d_st->sigma, &sigma, sizeof(double), cudaMemcpyHostToDevice,
+                             g->stream));
+  FK_CUDA(g, cudaMemsetAsync(&g->d_st->flags, 0, sizeof(unsigned), g->stream));
+  g->known_flags = 0;
+  g->base_step = 0;  // the reset below restarts the step count
+  s = evaluate(g, kModeReset);
+  if (s != FK_OK) return s;
+  if ((s = sync_state(g, &st)) != FK_OK) return s;
+  return flags_status(g, st.flags);
+}
+
+fk_status fk_grid_info(const fk_grid* g, double* out) {
+  if (!g || !out) return FK_EINVAL;
+  out[0] = g->dx;
+  out[1] = g->dv1;
+  out[2] = g->dv2;
+  out[3] = g->dt;
+  out[4] = g->prm.c2;
+  out[5] = g->prm.cx_max;
+  return FK_OK;
+}
+
+fk_status fk_set_kernel_timing(fk_grid* g, int enabled) {
+  if (!g) return FK_EINVAL;
+  FK_CUDA(g, cudaSetDevice(g->dev));
+  if (enabled && g->ev.empty()) {
+    g->ev.resize(2 * kMaxTimed, nullptr);
+    for (auto& e : g->ev) FK_CUDA(g, cudaEventCreate(&e));
+  }
+  FK_CUDA(g, cudaStreamSynchronize(g->stream));
+  g->timing = enabled != 0;
+  g->ev_used = 0;
+  return FK_OK;
+}
+
+fk_status fk_kernel_timing(fk_grid* g, int64_t* launches, double* total_ms) {
+  if (!g || !launches || !total_ms) return FK_EINVAL;
+  FK_CUDA(g, cudaSetDevice(g->dev));
+  FK_CUDA(g, cudaStreamSynchronize(g->stream));
+  double tot = 0.0;
+  for (int r = 0; r < g->ev_used; r++) {
+    float ms = 0.f;
+    FK_CUDA(g, cudaEventElapsedTime(&ms, g->ev[2 * r], g->ev[2 * r + 1]));
+    tot += ms;
+  }
+  *launches = g->ev_used;
+  *total_ms = tot;
+  g->ev_used = 0;
+  return FK_OK;
+}
+
+const char* fk_last_error(const fk_grid* g) {
+  return g ? g->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

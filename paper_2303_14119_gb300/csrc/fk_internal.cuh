@@ -1,0 +1,102 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Not part of the public ABI (include/fk.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "fk.h"
+
+namespace fk {
+
+// CODATA 2018 values (SI).
+constexpr double kQe = 1.602176634e-19;    // elementary charge, C
+constexpr double kMe = 9.1093837015e-31;   // electron mass, kg
+constexpr double kEps0 = 8.8541878128e-12; // vacuum permittivity, F/m
+constexpr double kPi = 3.14159265358979323846;
+
+// Sticky device error bits (fk_dev_state::flags).
+enum : unsigned {
+  kFlagCfl = 1u,
+  kFlagNumeric = 2u,
+  kFlagTimeout = 4u,
+};
+
+// Run parameters read by the kernels from device memory, so that captured
+// CUDA graphs stay valid when a setter changes them.
+struct Params {
+  double dx, dv1, dv2, dt;
+  double Ey, Ex_ext;
+  double c2;      // signed v2-Courant number a2 dt / dv2
+  double cx_max;  // max_i |v1_i| dt / dx
+  double inj;     // injected electrons per m^2 per s (J/e, 0 if off)
+  double sat_tol;
+  long long sat_window;
+  long long hist_cap;
+  int self_consistent;
+  int see_enabled;
+  int band_lo, band_hi; // source planes [band_lo, band_hi)
+};
+
+// Mutable per-run scalars, device resident.
+struct DevState {
+  double sigma, sigma0;
+  // fluxes and totals of the current state
+  double g_pe, g_see, g_vac, n_tot, n0;
+  // cumulative ledger terms
+  double cum_emit, cum_see, cum_pe, cum_vac, cum_lv, cum_inj;
+  long long step, sat_step, hist_count;
+  unsigned flags;
+  unsigned pad;
+};
+
+// Per work-unit partial sums written by the step kernel's epilogue; the
+// finalize kernel reduces them in a fixed order.
+struct Partials {
+  double* n;    // [nx][nu] sum of f^{n+1} over the unit's cells
+  double* lv;   // [nx][nu] sum over downwind velocity-edge cells of |c| f^n
+  double* pe;   // [nu]     sum over x = 0 cells with v1 < 0 of -v1 f^{n+1}
+  double* see;  // [nu]     same weighted by delta
+  double* vac;  // [nu]     sum over x = nx-1 cells with v1 > 0 of v1 f^{n+1}
+  int nu;       // units per plane
+};
+
+struct Tables {
+  double* v1;     // [nv1] cell-centre normal velocities
+  double* cx;     // [nv1] signed x-Courant numbers v1 dt / dx
+  double* delta;  // [nv1][nv2] SEE yield, zero where v1 >= 0
+  double* gse;    // [nv1][nv2] emission shape, unit flux
+  double* src;    // [nv1][nv2] dt * S / (band plane) = dt (J/e)/W g_fe
+  float* src32;   // same rounded to FP32
+  double* gfe_raw;// [nv1][nv2] scratch for the source shape
+};
+
+struct StepArgs {
+  const void* f_in;
+  void* f_out;
+  int nx, nv1, nv2, pitch;  // pitch = row stride of f in elements (>= nv2)
+  const double* c1;         // [nx] signed v1-Courant numbers of f^n
+  const Params* prm;
+  DevState* st;
+  Tables tab;
+  Partials part;
+};
+
+// Launchers (return the launch error).
+cudaError_t launch_tables(const Tables& t, const Params* prm_dev, int nv1, int nv2,
+                          double v1_min, double v2_min, double dv1, double dv2,
+                          double dt, double dx, double delta_max, double A_max,
+                          double k_s, double T_se, double T_fe, double J_over_eW,
+                          cudaStream_t s);
+cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cudaStream_t s);
+int step_units_per_plane(int nv1, int nv2);
+cudaError_t launch_finalize(const StepArgs& a, double* ne, double* Ex, double* c1,
+                            double* hist, int mode, cudaStream_t s);
+cudaError_t launch_convert(const void* src, void* dst, size_t rows, int nv2, int pitch,
+                           int to_f32, cudaStream_t s);
+
+enum FinalizeMode { kModeStep = 0, kModeRefresh = 1, kModeReset = 2 };
+
+}  // namespace fk

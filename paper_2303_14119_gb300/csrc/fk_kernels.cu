@@ -1,0 +1,429 @@
+// Set-up tables, the fused upwind step (direct-load variant), the finalize
+// kernel (moments -> surface charge, field, Courant numbers, ledger,
+// history) and the precision conversion used by fk_set_f / fk_get_f.
+//
+// Paper: Sun et al., arXiv 2303.14119, Sec. 2.
+#include <math.h>
+
+#include "fk_internal.cuh"
+
+namespace fk {
+
+// ---------------------------------------------------------------------------
+// Deterministic block reductions: fixed shuffle tree, fixed warp order.
+template <int NT>
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = l < NT / 32 ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+template <int NT>
+__device__ double block_max(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = l < NT / 32 ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Tables (one block, deterministic sums).
+//  delta: SEE yield of Eqs. 8-11 where v1 < 0.
+//  gse:   Eq. 15 shape on v1 > 0, normalised to unit flux sum v1 g dv1 dv2.
+//  src:   dt (J/e)/W times the Eq. 7 shape (Maxwellian in v1, half
+//         Maxwellian on v2 > 0), normalised to unit density.
+constexpr int kTabThreads = 1024;
+
+// Cell centre lo + (i + 1/2) h with separate roundings (no fused multiply-
+// add), so the velocity grid is bit-identical to a host computation.
+__device__ __forceinline__ double cell_centre(double lo, int i, double h) {
+  return __dadd_rn(lo, __dmul_rn((double)i + 0.5, h));
+}
+
+__global__ void __launch_bounds__(kTabThreads)
+tables_kernel(Tables t, int nv1, int nv2, double v1_min, double v2_min, double dv1,
+              double dv2, double dt, double dx, double dmax, double amax, double ks,
+              double Tse, double Tfe, double j_over_ew) {
+  __shared__ double sh[32];
+  __shared__ double norms[2];
+  double s_se = 0.0, s_fe = 0.0;
+  const int ncell = nv1 * nv2;
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int i = c / nv2, j = c - (c / nv2) * nv2;
+    const double v1 = cell_centre(v1_min, i, dv1);
+    const double v2 = cell_centre(v2_min, j, dv2);
+    const double vv = v1 * v1 + v2 * v2;
+    double d = 0.0;
+    if (v1 < 0.0) {
+      const double A = 0.5 * kMe * vv / kQe;         // Eq. 10, eV
+      const double al = atan(fabs(v2 / v1));         // Eq. 11
+      const double z = 1.284 * A / (amax * (1.0 + ks * al * al / kPi));  // Eq. 9
+      if (z > 0.0)
+        d = 1.526 * dmax * (1.0 + ks * al * al / (2.0 * kPi)) *
+            (1.0 - exp(-pow(z, 1.725))) / pow(z, 0.725);  // Eq. 8
+    }
+    t.delta[c] = d;
+    const double gs = v1 > 0.0 ? exp(-kMe * vv / (2.0 * Tse * kQe)) : 0.0;
+    t.gse[c] = gs;
+    s_se += v1 * gs;
+    const double gf = v2 > 0.0 ? exp(-kMe * vv / (2.0 * Tfe * kQe)) : 0.0;
+    t.gfe_raw[c] = gf;
+    s_fe += gf;
+  }
+  s_se = block_sum<kTabThreads>(s_se, sh);
+  s_fe = block_sum<kTabThreads>(s_fe, sh);
+  if (threadIdx.x == 0) {
+    norms[0] = s_se * dv1 * dv2;
+    norms[1] = s_fe * dv1 * dv2;
+  }
+  __syncthreads();
+  const double nse = norms[0], nfe = norms[1];
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    t.gse[c] = nse > 0.0 ? t.gse[c] / nse : 0.0;
+    const double s = nfe > 0.0 ? dt * j_over_ew * (t.gfe_raw[c] / nfe) : 0.0;
+    t.src[c] = s;
+    t.src32[c] = (float)s;
+  }
+  for (int i = threadIdx.x; i < nv1; i += blockDim.x) {
+    const double v1 = cell_centre(v1_min, i, dv1);
+    t.v1[i] = v1;
+    t.cx[i] = __ddiv_rn(__dmul_rn(v1, dt), dx);
+  }
+}
+
+cudaError_t launch_tables(const Tables& t, const Params*, int nv1, int nv2, double v1_min,
+                          double v2_min, double dv1, double dv2, double dt, double dx,
+                          double delta_max, double A_max, double k_s, double T_se,
+                          double T_fe, double j_over_ew, cudaStream_t s) {
+  tables_kernel<<<1, kTabThreads, 0, s>>>(t, nv1, nv2, v1_min, v2_min, dv1, dv2, dt, dx,
+                                          delta_max, A_max, k_s, T_se, T_fe, j_over_ew);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Direct-load step kernel.  One block per work unit = (plane k, band of R
+// rows of v1).  Each thread updates cells of the unit; every neighbour is a
+// plain load (the L1/L2 caches catch the re-reads).
+//
+// Per cell, with c_x = v1 dt/dx, c_1 = a1(x) dt/dv1, c_2 = a2 dt/dv2 and the
+// upwind neighbour f_u in each direction (zero beyond a velocity edge or the
+// vacuum side, Gamma_see g_se at the wall for v1 > 0):
+//   f' = f - |c_x|(f - f_ux) - |c_1|(f - f_u1) - |c_2|(f - f_u2) + dt S
+// which is the donor-cell flux difference of Eq. 2 written per cell.
+constexpr int kStepThreads = 256;
+constexpr int kCellsPerUnit = 4096;
+
+int step_rows_per_unit(int nv1, int nv2) {
+  int r = kCellsPerUnit / nv2;
+  if (r < 1) r = 1;
+  if (r > nv1) r = nv1;
+  return r;
+}
+int step_units_per_plane(int nv1, int nv2) {
+  const int r = step_rows_per_unit(nv1, nv2);
+  return (nv1 + r - 1) / r;
+}
+
+template <typename T>
+__device__ __forceinline__ T update_cell(T f, T fx, T fv, T fw, T ax, T a1, T a2, T s);
+
+template <>
+__device__ __forceinline__ double update_cell<double>(double f, double fx, double fv,
+                                                      double fw, double ax, double a1,
+                                                      double a2, double s) {
+  // convex form: (1 - ax - a1 - a2) f + ax fx + a1 fv + a2 fw + s
+  const double d = 1.0 - ax - a1 - a2;
+  return fma(a2, fw, fma(a1, fv, fma(ax, fx, fma(d, f, s))));
+}
+
+template <>
+__device__ __forceinline__ float update_cell<float>(float f, float fx, float fv, float fw,
+                                                    float ax, float a1, float a2, float s) {
+  // increment form keeps one rounding of f per step dominant
+  const float inc = fmaf(a2, fw - f, fmaf(a1, fv - f, fmaf(ax, fx - f, s)));
+  return f + inc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kStepThreads)
+step_direct_kernel(StepArgs a, int rows, int moments_only) {
+  __shared__ double sh[32];
+  const int nu = a.part.nu;
+  const int k = blockIdx.x / nu;
+  const int u = blockIdx.x - k * nu;
+  const Params& p = *a.prm;
+  if (!moments_only && a.st->flags) return;  // sticky error: freeze the state
+  const T* __restrict__ fin = static_cast<const T*>(a.f_in);
+  T* __restrict__ fout = static_cast<T*>(a.f_out);
+  const int nx = a.nx, nv1 = a.nv1, nv2 = a.nv2, pitch = a.pitch;
+  const size_t plane = (size_t)nv1 * pitch;
+  const double c1d = a.c1[k];
+  const double c2d = p.c2;
+  const double gsee = a.st->g_see;
+  const bool band = k >= p.band_lo && k < p.band_hi;
+  const int i0 = u * rows;
+  const int i1 = min(nv1, i0 + rows);
+  const int ncell = (i1 - i0) * nv2;
+  double s_n = 0.0, s_lv = 0.0, s_pe = 0.0, s_see = 0.0, s_vac = 0.0;
+  const T a1 = (T)fabs(c1d), a2 = (T)fabs(c2d);
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int i = i0 + c / nv2;
+    const int j = c - (c / nv2) * nv2;
+    const size_t idx = (size_t)k * plane + (size_t)i * pitch + j;
+    const T f = fin[idx];
+    const double cxd = a.tab.cx[i];
+    T fx = (T)0;
+    if (cxd > 0.0)
+      fx = k > 0 ? fin[idx - plane] : (T)(gsee * a.tab.gse[i * nv2 + j]);
+    else if (cxd < 0.0)
+      fx = k < nx - 1 ? fin[idx + plane] : (T)0;
+    T fv = (T)0;
+    if (c1d > 0.0)
+      fv = i > 0 ? fin[idx - pitch] : (T)0;
+    else if (c1d < 0.0)
+      fv = i < nv1 - 1 ? fin[idx + pitch] : (T)0;
+    T fw = (T)0;
+    if (c2d > 0.0)
+      fw = j > 0 ? fin[idx - 1] : (T)0;
+    else if (c2d < 0.0)
+      fw = j < nv2 - 1 ? fin[idx + 1] : (T)0;
+    T s = (T)0;
+    if (band) {
+      if (sizeof(T) == 8)
+        s = (T)a.tab.src[i * nv2 + j];
+      else
+        s = (T)a.tab.src32[i * nv2 + j];
+    }
+    T fn = f;
+    if (!moments_only) {
+      fn = update_cell<T>(f, fx, fv, fw, (T)fabs(cxd), a1, a2, s);
+      fout[idx] = fn;
+      // loss through the downwind velocity edges, from f^n (ledger)
+      if ((c1d > 0.0 && i == nv1 - 1) || (c1d < 0.0 && i == 0)) s_lv += fabs(c1d) * (double)f;
+      if ((c2d > 0.0 && j == nv2 - 1) || (c2d < 0.0 && j == 0)) s_lv += fabs(c2d) * (double)f;
+    }
+    const double fnd = (double)fn;
+    s_n += fnd;
+    const double v1 = a.tab.v1[i];
+    if (k == 0 && v1 < 0.0) {
+      const double g = -v1 * fnd;  // Eq. 13 without dv1 dv2
+      s_pe += g;
+      s_see += a.tab.delta[i * nv2 + j] * g;  // Eq. 12
+    }
+    if (k == nx - 1 && v1 > 0.0) s_vac += v1 * fnd;
+  }
+  s_n = block_sum<kStepThreads>(s_n, sh);
+  s_lv = block_sum<kStepThreads>(s_lv, sh);
+  if (k == 0) {
+    s_pe = block_sum<kStepThreads>(s_pe, sh);
+    s_see = block_sum<kStepThreads>(s_see, sh);
+  }
+  if (k == nx - 1) s_vac = block_sum<kStepThreads>(s_vac, sh);
+  if (threadIdx.x == 0) {
+    a.part.n[(size_t)k * nu + u] = s_n;
+    a.part.lv[(size_t)k * nu + u] = s_lv;
+    if (k == 0) {
+      a.part.pe[u] = s_pe;
+      a.part.see[u] = s_see;
+    }
+    if (k == nx - 1) a.part.vac[u] = s_vac;
+  }
+}
+
+cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cudaStream_t s) {
+  const int rows = step_rows_per_unit(a.nv1, a.nv2);
+  const int nblk = a.nx * a.part.nu;
+  if (precision == FK_F32)
+    step_direct_kernel<float><<<nblk, kStepThreads, 0, s>>>(a, rows, moments_only);
+  else
+    step_direct_kernel<double><<<nblk, kStepThreads, 0, s>>>(a, rows, moments_only);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Finalize: one block.  Reduces the partials in a fixed order, then
+//  - step mode: ledger += dt * (fluxes of f^n), sigma^{n+1} = sigma^n +
+//    e dt (Gamma_see^n - Gamma_pe^n)  (Eq. 18 summed with Eq. 14), step++;
+//  - stores the fluxes of the new state, N, n_e;
+//  - E_x from Gauss's law integrated from the wall, E_x(0) = sigma/(2 eps0)
+//    (the Poisson problem of Sec. 2), and c_1 = -e E_x dt / (m_e dv1);
+//  - CFL and finiteness checks (sticky flags), history row, convergence
+//    test (Sec. 2, paragraph after Eq. 18).
+constexpr int kFinThreads = 1024;
+
+__global__ void __launch_bounds__(kFinThreads)
+finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, double* hist, int mode) {
+  __shared__ double sh[32];
+  __shared__ double wsum[32];
+  __shared__ double bc[8];
+  const Params& p = *a.prm;
+  DevState* st = a.st;
+  if (mode == kModeStep && st->flags) return;
+  const int nx = a.nx, nu = a.part.nu;
+  const int t = threadIdx.x;
+  const int per = (nx + kFinThreads - 1) / kFinThreads;
+  const int k0 = min(nx, t * per), k1 = min(nx, k0 + per);
+  const double dvv = p.dv1 * p.dv2;
+  // per-plane sums over units, fixed order
+  double loc_n = 0.0, loc_lv = 0.0;
+  for (int k = k0; k < k1; k++) {
+    double sn = 0.0, sl = 0.0;
+    for (int u = 0; u < nu; u++) {
+      sn += a.part.n[(size_t)k * nu + u];
+      sl += a.part.lv[(size_t)k * nu + u];
+    }
+    ne[k] = sn * dvv;
+    loc_n += sn * dvv;
+    loc_lv += sl;
+  }
+  // exclusive scan of the per-thread chunk totals (fixed order)
+  const int lane = t & 31, w = t >> 5;
+  double incl = loc_n;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+  if (lane == 0) excl = 0.0;
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    double x = wsum[lane];
+    double xi = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += y;
+    }
+    wsum[lane] = xi - x;  // exclusive over warps
+  }
+  __syncthreads();
+  const double before = wsum[w] + excl;  // sum of n over planes < k0
+  const double ntot = block_sum<kFinThreads>(loc_n, sh) * p.dx;
+  const double lvtot = block_sum<kFinThreads>(loc_lv, sh);
+  if (t == 0) {
+    double pe = 0.0, see = 0.0, vac = 0.0;
+    for (int u = 0; u < nu; u++) {
+      pe += a.part.pe[u];
+      see += a.part.see[u];
+      vac += a.part.vac[u];
+    }
+    pe *= dvv;
+    see = p.see_enabled ? see * dvv : 0.0;
+    vac *= dvv;
+    if (mode == kModeStep) {
+      const double lv = lvtot * p.dx * dvv / p.dt;
+      st->cum_emit += p.dt * st->g_see;
+      st->cum_see += p.dt * st->g_see;
+      st->cum_pe += p.dt * st->g_pe;
+      st->cum_vac += p.dt * st->g_vac;
+      st->cum_lv += p.dt * lv;
+      st->cum_inj += p.dt * p.inj;
+      st->sigma += kQe * p.dt * (st->g_see - st->g_pe);
+      st->step += 1;
+    }
+    if (mode == kModeReset) {
+      st->step = 0;
+      st->hist_count = 0;
+      st->sat_step = -1;
+      st->cum_emit = st->cum_see = st->cum_pe = st->cum_vac = st->cum_lv = st->cum_inj = 0.0;
+      st->sigma0 = st->sigma;
+      st->n0 = ntot;
+    }
+    st->g_pe = pe;
+    st->g_see = see;
+    st->g_vac = vac;
+    st->n_tot = ntot;
+    if (!isfinite(pe) || !isfinite(see) || !isfinite(vac) || !isfinite(ntot) ||
+        !isfinite(st->sigma))
+      st->flags |= kFlagNumeric;
+    bc[0] = st->sigma;
+  }
+  __syncthreads();
+  const double sigma = bc[0];
+  // E_x at cell centres and the v1-Courant numbers
+  double run = before;
+  double cmax = 0.0;
+  for (int k = k0; k < k1; k++) {
+    const double nk = ne[k];
+    const double e = p.self_consistent
+                         ? sigma / (2.0 * kEps0) - kQe / kEps0 * p.dx * (run + 0.5 * nk)
+                         : p.Ex_ext;
+    run += nk;
+    Ex[k] = e;
+    const double c = -kQe * e / kMe * p.dt / p.dv1;
+    c1[k] = c;
+    cmax = fmax(cmax, fabs(c));
+  }
+  cmax = block_max<kFinThreads>(cmax, sh);
+  __syncthreads();
+  if (t == 0) {
+    if (cmax + p.cx_max + fabs(p.c2) > 1.0 + 1e-12) st->flags |= kFlagCfl;
+    const long long row = st->step;
+    const long long cap = p.hist_cap;
+    double* r = hist + (size_t)(row % cap) * FK_HISTORY_COLS;
+    r[0] = (double)row;
+    r[1] = (double)row * p.dt;
+    r[2] = st->sigma;
+    r[3] = st->g_pe;
+    r[4] = st->g_see;
+    r[5] = st->g_vac;
+    r[6] = st->n_tot;
+    r[7] = Ex[0];
+    if (row + 1 > st->hist_count) st->hist_count = row + 1;
+    if (mode == kModeStep && st->sat_step < 0 && row >= p.sat_window && p.sat_window < cap) {
+      const double* o = hist + (size_t)((row - p.sat_window) % cap) * FK_HISTORY_COLS;
+      bool ok = true;
+      for (int q = 2; q <= 4; q++)
+        if (!(fabs(r[q] - o[q]) <= p.sat_tol * fabs(r[q]))) ok = false;
+      if (ok) st->sat_step = row;
+    }
+  }
+}
+
+cudaError_t launch_finalize(const StepArgs& a, double* ne, double* Ex, double* c1,
+                            double* hist, int mode, cudaStream_t s) {
+  finalize_kernel<<<1, kFinThreads, 0, s>>>(a, ne, Ex, c1, hist, mode);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 rows <-> FP32 rows with a row pitch (host arrays are dense FP64).
+__global__ void convert_kernel(const void* src, void* dst, size_t rows, int nv2, int pitch,
+                               int to_f32) {
+  const size_t n = rows * (size_t)nv2;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = e / nv2, j = e - (e / nv2) * nv2;
+    if (to_f32)
+      static_cast<float*>(dst)[r * pitch + j] = (float)static_cast<const double*>(src)[e];
+    else
+      static_cast<double*>(dst)[e] = (double)static_cast<const float*>(src)[r * pitch + j];
+  }
+}
+
+cudaError_t launch_convert(const void* src, void* dst, size_t rows, int nv2, int pitch,
+                           int to_f32, cudaStream_t s) {
+  const size_t n = rows * (size_t)nv2;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  convert_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, dst, rows, nv2, pitch, to_f32);
+  return cudaGetLastError();
+}
+
+}  // namespace fk

@@ -1,0 +1,316 @@
+"""Python binding of the C ABI in ``include/fk.h`` (ctypes, marshalling only).
+
+Every function here has the name of the C entry point it calls and does
+nothing but convert arguments and results; every step of the solver runs in
+the CUDA kernels of ``libflashkin.so``.  There is no CPU path: if the library
+is missing or cannot load, importing the binding's functions raises.
+
+Host arrays are numpy FP64 arrays (any contiguous buffer works; a pinned
+torch CPU tensor viewed with ``.numpy()`` makes the copies asynchronous-
+capable).  Streams are passed as raw ``cudaStream_t`` integers, e.g.
+``torch.cuda.current_stream().cuda_stream``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+FK_OK, FK_EINVAL, FK_ENOMEM, FK_ECUDA, FK_ECFL, FK_ENUMERIC, FK_ETIMEOUT, FK_ESTATE = range(8)
+FK_F64, FK_F32 = 0, 1
+FK_HISTORY_COLS = 8
+FK_LEDGER_LEN = 9
+STATUS_NAMES = {0: "FK_OK", 1: "FK_EINVAL", 2: "FK_ENOMEM", 3: "FK_ECUDA", 4: "FK_ECFL",
+                5: "FK_ENUMERIC", 6: "FK_ETIMEOUT", 7: "FK_ESTATE"}
+
+
+class fk_grid_desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("nv1", C.c_int32), ("nv2", C.c_int32),
+                ("precision", C.c_int32), ("h_max", C.c_double), ("v1_min", C.c_double),
+                ("v1_max", C.c_double), ("v2_min", C.c_double), ("v2_max", C.c_double),
+                ("dt", C.c_double), ("cfl", C.c_double), ("history_capacity", C.c_int64),
+                ("device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class FkError(RuntimeError):
+    def __init__(self, status, what, message):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (what, STATUS_NAMES.get(status, status), message))
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load ``libflashkin.so`` (building it first if it is missing or stale
+    and nvcc is available).  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and (not os.path.exists(_build.LIB) or _build.stale()):
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError("libflashkin.so is not built; run paper_2303_14119_gb300._build.build()")
+    lib = C.CDLL(_build.LIB)
+    P, D, I, I64 = C.c_void_p, C.c_double, C.c_int, C.c_int64
+    dp = C.POINTER(C.c_double)
+    i64p = C.POINTER(C.c_int64)
+    sig = {
+        "fk_create_grid": [C.POINTER(fk_grid_desc), P, C.POINTER(P)],
+        "fk_destroy_grid": [P],
+        "fk_set_fields": [P, D, I, D],
+        "fk_set_see": [P, D, D, D, D, I],
+        "fk_set_source": [P, D, D, D, D],
+        "fk_set_convergence": [P, I64, D],
+        "fk_step": [P, I64],
+        "fk_sync": [P],
+        "fk_moments": [P, dp, dp, dp, dp],
+        "fk_surface_charge": [P, dp],
+        "fk_history": [P, dp, I64, i64p],
+        "fk_ledger": [P, dp],
+        "fk_step_count": [P, i64p, i64p],
+        "fk_get_f": [P, dp],
+        "fk_set_f": [P, dp],
+        "fk_set_surface_charge": [P, D],
+        "fk_grid_info": [P, dp],
+        "fk_set_kernel_timing": [P, I],
+        "fk_kernel_timing": [P, i64p, dp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = C.c_int
+        fn.argtypes = args
+    lib.fk_last_error.restype = C.c_char_p
+    lib.fk_last_error.argtypes = [P]
+    _lib = lib
+    return lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(status, what, handle=None):
+    if status != FK_OK:
+        msg = load().fk_last_error(handle).decode(errors="replace")
+        raise FkError(status, what, msg)
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError("expected %d elements, got %d" % (n, a.size))
+    return a
+
+
+# --- the C entry points, one Python function each --------------------------
+def fk_create_grid(nx, nv1, nv2, h_max, v1_min, v1_max, v2_min, v2_max, dt=0.0, cfl=0.4,
+                   precision=FK_F64, history_capacity=0, device=0, stream=None):
+    d = fk_grid_desc(int(nx), int(nv1), int(nv2), int(precision), float(h_max), float(v1_min),
+                     float(v1_max), float(v2_min), float(v2_max), float(dt), float(cfl),
+                     int(history_capacity), int(device), 0)
+    h = C.c_void_p()
+    st = load().fk_create_grid(C.byref(d), C.c_void_p(stream) if stream else None, C.byref(h))
+    _check(st, "fk_create_grid")
+    return h.value
+
+
+def fk_destroy_grid(g):
+    _check(load().fk_destroy_grid(g), "fk_destroy_grid", g)
+
+
+def fk_set_fields(g, Ey, self_consistent=True, Ex_external=0.0):
+    _check(load().fk_set_fields(g, float(Ey), int(bool(self_consistent)), float(Ex_external)),
+           "fk_set_fields", g)
+
+
+def fk_set_see(g, delta_max, A_max_eV, k_s=1.0, T_se_eV=2.0, enabled=True):
+    _check(load().fk_set_see(g, float(delta_max), float(A_max_eV), float(k_s), float(T_se_eV),
+                             int(bool(enabled))), "fk_set_see", g)
+
+
+def fk_set_source(g, J, x_lo, x_hi, T_fe_eV):
+    _check(load().fk_set_source(g, float(J), float(x_lo), float(x_hi), float(T_fe_eV)),
+           "fk_set_source", g)
+
+
+def fk_set_convergence(g, window, rel_tol):
+    _check(load().fk_set_convergence(g, int(window), float(rel_tol)), "fk_set_convergence", g)
+
+
+def fk_step(g, n=1):
+    _check(load().fk_step(g, int(n)), "fk_step", g)
+
+
+def fk_step_status(g, n=1):
+    """fk_step returning the raw status instead of raising."""
+    return load().fk_step(g, int(n))
+
+
+def fk_sync(g):
+    _check(load().fk_sync(g), "fk_sync", g)
+
+
+def fk_sync_status(g):
+    return load().fk_sync(g)
+
+
+def fk_moments(g, nx, n_e=None, Ex=None):
+    n_e = np.empty(nx) if n_e is None else n_e
+    Ex = np.empty(nx) if Ex is None else Ex
+    gpe = np.empty(1)
+    gsee = np.empty(1)
+    _check(load().fk_moments(g, _dp(n_e), _dp(Ex), _dp(gpe), _dp(gsee)), "fk_moments", g)
+    return n_e, Ex, float(gpe[0]), float(gsee[0])
+
+
+def fk_surface_charge(g):
+    s = np.empty(1)
+    _check(load().fk_surface_charge(g, _dp(s)), "fk_surface_charge", g)
+    return float(s[0])
+
+
+def fk_history(g, max_rows):
+    out = np.empty((int(max_rows), FK_HISTORY_COLS))
+    rows = C.c_int64()
+    _check(load().fk_history(g, _dp(out), int(max_rows), C.byref(rows)), "fk_history", g)
+    return out[: rows.value]
+
+
+def fk_ledger(g):
+    out = np.empty(FK_LEDGER_LEN)
+    _check(load().fk_ledger(g, _dp(out)), "fk_ledger", g)
+    keys = ["N", "N0", "emit", "pe", "vac", "lv", "inj", "sigma0", "see"]
+    return dict(zip(keys, out.tolist()))
+
+
+def fk_step_count(g):
+    s, sat = C.c_int64(), C.c_int64()
+    _check(load().fk_step_count(g, C.byref(s), C.byref(sat)), "fk_step_count", g)
+    return s.value, sat.value
+
+
+def fk_get_f(g, shape, out=None):
+    n = int(np.prod(shape))
+    out = np.empty(shape, dtype=np.float64) if out is None else out
+    if out.dtype != np.float64 or out.size != n or not out.flags.c_contiguous:
+        raise ValueError("out must be a contiguous FP64 array of %d elements" % n)
+    _check(load().fk_get_f(g, _dp(out)), "fk_get_f", g)
+    return out
+
+
+def fk_set_f(g, f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _check(load().fk_set_f(g, _dp(f)), "fk_set_f", g)
+
+
+def fk_set_surface_charge(g, sigma):
+    _check(load().fk_set_surface_charge(g, float(sigma)), "fk_set_surface_charge", g)
+
+
+def fk_grid_info(g):
+    out = np.empty(6)
+    _check(load().fk_grid_info(g, _dp(out)), "fk_grid_info", g)
+    return dict(dx=out[0], dv1=out[1], dv2=out[2], dt=out[3], c2=out[4], cx_max=out[5])
+
+
+def fk_set_kernel_timing(g, enabled):
+    _check(load().fk_set_kernel_timing(g, int(bool(enabled))), "fk_set_kernel_timing", g)
+
+
+def fk_kernel_timing(g):
+    n = C.c_int64()
+    ms = np.empty(1)
+    _check(load().fk_kernel_timing(g, C.byref(n), _dp(ms)), "fk_kernel_timing", g)
+    return n.value, float(ms[0])
+
+
+def fk_last_error(g=None):
+    return load().fk_last_error(g).decode(errors="replace")
+
+
+class Grid:
+    """Owning handle around one ``fk_grid``; methods call the entry points
+    above with the grid's shape filled in."""
+
+    def __init__(self, nx, nv1, nv2, h_max, v1_min, v1_max, v2_min, v2_max, dt=0.0, cfl=0.4,
+                 precision=FK_F64, history_capacity=0, device=0, stream=None):
+        self.h = fk_create_grid(nx, nv1, nv2, h_max, v1_min, v1_max, v2_min, v2_max, dt, cfl,
+                                precision, history_capacity, device, stream)
+        self.shape = (int(nx), int(nv1), int(nv2))
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "h", None):
+            fk_destroy_grid(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_fields(self, Ey, self_consistent=True, Ex_external=0.0):
+        fk_set_fields(self.h, Ey, self_consistent, Ex_external)
+
+    def set_see(self, delta_max, A_max_eV, k_s=1.0, T_se_eV=2.0, enabled=True):
+        fk_set_see(self.h, delta_max, A_max_eV, k_s, T_se_eV, enabled)
+
+    def set_source(self, J, x_lo, x_hi, T_fe_eV):
+        fk_set_source(self.h, J, x_lo, x_hi, T_fe_eV)
+
+    def set_convergence(self, window, rel_tol):
+        fk_set_convergence(self.h, window, rel_tol)
+
+    def step(self, n=1):
+        fk_step(self.h, n)
+
+    def sync(self):
+        fk_sync(self.h)
+
+    def moments(self):
+        return fk_moments(self.h, self.shape[0])
+
+    def surface_charge(self):
+        return fk_surface_charge(self.h)
+
+    def history(self, max_rows):
+        return fk_history(self.h, max_rows)
+
+    def ledger(self):
+        return fk_ledger(self.h)
+
+    def step_count(self):
+        return fk_step_count(self.h)
+
+    def get_f(self, out=None):
+        return fk_get_f(self.h, self.shape, out)
+
+    def set_f(self, f):
+        fk_set_f(self.h, f)
+
+    def set_state(self, f, sigma):
+        fk_set_f(self.h, f)
+        fk_set_surface_charge(self.h, sigma)
+
+    def set_surface_charge(self, sigma):
+        fk_set_surface_charge(self.h, sigma)
+
+    def info(self):
+        return fk_grid_info(self.h)
+
+    def set_kernel_timing(self, enabled):
+        fk_set_kernel_timing(self.h, enabled)
+
+    def kernel_timing(self):
+        return fk_kernel_timing(self.h)

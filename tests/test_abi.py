@@ -1,0 +1,70 @@
+"""The C-ABI library loads, exports every entry point include/fk.h declares,
+and rejects invalid grids on the host before touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2303_14119_gb300 import fk
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(fk_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_entry_points()
+    for required in ("fk_create_grid", "fk_destroy_grid", "fk_set_fields", "fk_set_see",
+                     "fk_set_source", "fk_step", "fk_moments", "fk_surface_charge",
+                     "fk_history", "fk_ledger", "fk_get_f", "fk_set_f", "fk_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = fk.load()
+    missing = [n for n in declared_entry_points() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def _desc(**kw):
+    d = dict(nx=8, nv1=6, nv2=6, precision=0, h_max=20e-6, v1_min=-6e7, v1_max=6e7,
+             v2_min=-3e7, v2_max=3e7, dt=0.0, cfl=0.4, history_capacity=0, device=0, reserved=0)
+    d.update(kw)
+    return fk.fk_grid_desc(**d)
+
+
+@pytest.mark.parametrize("bad", [dict(nx=1), dict(nv1=1), dict(nv2=0), dict(h_max=0.0),
+                                 dict(v1_min=1.0, v1_max=1.0), dict(v2_min=2.0, v2_max=1.0),
+                                 dict(dt=0.0, cfl=0.0), dict(precision=7),
+                                 dict(history_capacity=-1), dict(h_max=float("nan"))])
+def test_invalid_descriptions_rejected_on_host(bad):
+    lib = fk.load()
+    h = C.c_void_p()
+    st = lib.fk_create_grid(C.byref(_desc(**bad)), None, C.byref(h))
+    assert st == fk.FK_EINVAL
+    assert h.value is None
+    assert lib.fk_last_error(None)
+
+
+def test_x_courant_above_one_rejected_on_host():
+    lib = fk.load()
+    h = C.c_void_p()
+    st = lib.fk_create_grid(C.byref(_desc(dt=1e-12)), None, C.byref(h))
+    assert st == fk.FK_ECFL
+
+
+def test_null_arguments():
+    lib = fk.load()
+    assert lib.fk_create_grid(None, None, None) == fk.FK_EINVAL
+    assert lib.fk_destroy_grid(None) == fk.FK_OK
+    assert lib.fk_step(None, 1) == fk.FK_EINVAL
+    assert lib.fk_sync(None) == fk.FK_EINVAL
