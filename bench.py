@@ -155,7 +155,10 @@ def make_grids(fk, w, precision, stream):
 
 
 def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device):
+    # every grid runs on torch's current stream (a created stream, not the
+    # legacy default), so the events below bracket exactly the grids' work
     stream = torch.cuda.current_stream().cuda_stream
+    assert stream, "time_arm needs a non-default current stream"
     grids = make_grids(fk, w, precision, stream)
     for g in grids:
         g.set_f(f0)
@@ -190,8 +193,10 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device):
         g.set_kernel_timing(False)
         g.sync()
     cells = w["nx"] * w["nv1"] * w["nv2"]
+    info = grids[0].info()
     res = dict(ms=ms, launches=launches, kernel_ms=kms, cells=cells, n_inst=len(grids),
-               clocks=ck, grids=grids)
+               clocks=ck, grids=grids,
+               kernel={k: info[k] for k in ("kernel", "n_tiles", "n_chunks", "chunk_len")})
     return res
 
 
@@ -200,6 +205,7 @@ def e2e_arm(fk, torch, w, precision, f0_pinned, steps):
     pinned host memory, then per step advance and read sigma and the wall
     fluxes back, finally read f back; all inside the timed region."""
     stream = torch.cuda.current_stream().cuda_stream
+    assert stream, "e2e_arm needs a non-default current stream"
     grids = make_grids(fk, w, precision, stream)
     nx = w["nx"]
     out_f = torch.empty(f0_pinned.shape, dtype=torch.float64, pin_memory=True).numpy()
@@ -275,6 +281,7 @@ def run_ours(args):
     from paper_2303_14119_gb300 import fk
     fk.load()
     torch.cuda.set_device(local)
+    torch.cuda.set_stream(torch.cuda.Stream())
     dist = None
     if world > 1:
         import torch.distributed as td
@@ -306,6 +313,7 @@ def run_ours(args):
                    "accumulators": "f64", "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline(res, args.precision, peak, peak_kind),
+        "kernel_plan": res["kernel"],
         "gpu_launches": args.steps * res["n_inst"] * 2,
         "clocks": res["clocks"],
     }

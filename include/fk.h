@@ -174,8 +174,11 @@ fk_status fk_set_f(fk_grid *grid, const double *host_f);
 /* Replace sigma (C/m^2) and restart the run at step 0 like fk_set_f. */
 fk_status fk_set_surface_charge(fk_grid *grid, double sigma);
 
-/* Grid facts: out[0..5] = dx, dv1, dv2, dt (s), c2 (signed v2-Courant number
- * a2 dt/dv2), max |c_x|.  Host-side, no synchronisation. */
+/* Grid facts, FK_INFO_LEN doubles: dx, dv1, dv2, dt (s), c2 (signed
+ * v2-Courant number a2 dt/dv2), max |c_x|, step kernel (1 streaming,
+ * 0 direct-load), v1-row tiles per plane, x-chunks, planes per chunk.
+ * Host-side, no synchronisation. */
+#define FK_INFO_LEN 10
 fk_status fk_grid_info(const fk_grid *grid, double *out);
 
 /* Kernel timing (tracing).  enabled != 0: later fk_step calls launch each

@@ -6,6 +6,7 @@
 // surface charge, convergence test).
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -46,7 +47,10 @@ struct fk_grid {
   long long base_step = 0;
   Tables tab{};
   Partials part{};
+  Geom geom{};
+  bool use_stream = true;  // streaming kernel (else the direct-load kernel)
   double *d_ne = nullptr, *d_Ex = nullptr, *d_c1 = nullptr, *d_hist = nullptr;
+  float* d_c1_32 = nullptr;
   void* d_stage = nullptr;
   // physics parameters as last set
   double Ey = 0, Ex_ext = 0;
@@ -101,6 +105,8 @@ StepArgs make_args(fk_grid* g, int cur) {
   a.nv2 = g->nv2;
   a.pitch = g->pitch;
   a.c1 = g->d_c1;
+  a.c1_32 = g->d_c1_32;
+  a.geom = g->geom;
   a.prm = g->d_prm;
   a.st = g->d_st;
   a.tab = g->tab;
@@ -131,8 +137,22 @@ fk_status sync_state(fk_grid* g, DevState* out) {
 fk_status evaluate(fk_grid* g, int mode) {
   StepArgs a = make_args(g, g->enq_cur);
   FK_CUDA(g, launch_step(a, g->prec, 1, g->stream));
-  FK_CUDA(g, launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_hist, mode, g->stream));
+  FK_CUDA(g, launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, mode,
+                             g->stream));
   return FK_OK;
+}
+
+// One step: the step kernel then the finalize kernel on stream s.
+cudaError_t enqueue_step(fk_grid* g, int cur, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+  StepArgs a = make_args(g, cur);
+  cudaError_t e = cudaSuccess;
+  if (ev0) e = cudaEventRecord(ev0, s);
+  if (e == cudaSuccess)
+    e = g->use_stream ? launch_step_stream(a, g->prec, s) : launch_step(a, g->prec, 0, s);
+  if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
+  if (e == cudaSuccess)
+    e = launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, kModeStep, s);
+  return e;
 }
 
 fk_status clear_flags(fk_grid* g, unsigned mask) {
@@ -150,7 +170,7 @@ fk_status clear_flags(fk_grid* g, unsigned mask) {
 fk_status rebuild_tables(fk_grid* g) {
   const double W = (g->prm.band_hi - g->prm.band_lo) * g->dx;
   const double j_over_ew = (g->J > 0.0 && W > 0.0) ? g->J / kQe / W : 0.0;
-  FK_CUDA(g, launch_tables(g->tab, g->d_prm, g->nv1, g->nv2, g->desc.v1_min, g->desc.v2_min,
+  FK_CUDA(g, launch_tables(g->tab, g->nv1, g->nv2, g->pitch, g->desc.v1_min, g->desc.v2_min,
                            g->dv1, g->dv2, g->dt, g->dx, g->delta_max, g->A_max, g->k_s,
                            g->T_se, g->T_fe, j_over_ew, g->stream));
   return FK_OK;
@@ -173,9 +193,10 @@ void free_grid(fk_grid* g) {
   for (int p = 0; p < 2; p++)
     if (g->graph[p]) cudaGraphExecDestroy(g->graph[p]);
   void* ptrs[] = {g->d_prm, g->d_st, g->d_f[0], g->d_f[1], g->tab.v1, g->tab.cx,
-                  g->tab.delta, g->tab.gse, g->tab.src, g->tab.src32, g->tab.gfe_raw,
-                  g->part.n, g->part.lv, g->part.pe, g->part.see, g->part.vac,
-                  g->d_ne, g->d_Ex, g->d_c1, g->d_hist, g->d_stage};
+                  g->tab.cx32, g->tab.delta, g->tab.gse, g->tab.src, g->tab.src32,
+                  g->tab.gfe_raw, g->part.n, g->part.lv, g->part.pe, g->part.see,
+                  g->part.vac, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist,
+                  g->d_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
@@ -195,10 +216,7 @@ fk_status build_graph(fk_grid* g, int parity) {
   int cur = parity;
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < kGraphSteps && e == cudaSuccess; s++) {
-    StepArgs a = make_args(g, cur);
-    e = launch_step(a, g->prec, 0, cs);
-    if (e == cudaSuccess)
-      e = launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_hist, kModeStep, cs);
+    e = enqueue_step(g, cur, cs, nullptr, nullptr);
     cur ^= 1;
   }
   cudaGraph_t graph = nullptr;
@@ -211,6 +229,54 @@ fk_status build_graph(fk_grid* g, int parity) {
   cudaError_t e3 = cudaGraphInstantiate(&g->graph[parity], graph, 0);
   cudaGraphDestroy(graph);
   if (e3 != cudaSuccess) return cuda_fail(g, e3, "cudaGraphInstantiate");
+  return FK_OK;
+}
+
+// Tiles of v1 rows (never straddling the sign change of v1) and chunks of
+// x-planes: one streaming CTA per (tile, chunk), about one wave of CTAs.
+fk_status plan_geometry(fk_grid* g) {
+  const char* env = getenv("FK_STEP_KERNEL");
+  FK_CUDA(g, cudaSetDevice(g->dev));
+  int sms = 0, smem_sm = 0, reserved = 0;
+  FK_CUDA(g, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->dev));
+  FK_CUDA(g, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, g->dev));
+  FK_CUDA(g, cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, g->dev));
+  int ti_max = stream_tile_rows(g->prec, g->pitch, smem_sm, reserved);
+  g->use_stream = ti_max > 0 && !(env && strcmp(env, "direct") == 0);
+  if (!g->use_stream) ti_max = std::max(1, 4096 / g->pitch);
+  int i_neg = 0;
+  for (int i = 0; i < g->nv1; i++)
+    if (g->desc.v1_min + ((double)i + 0.5) * g->dv1 <= 0.0) i_neg++;
+  Geom& m = g->geom;
+  m.i_neg = i_neg;
+  auto split = [&](int rows, int* nt, int* ti) {
+    if (rows <= 0) {
+      *nt = 0;
+      *ti = 1;
+      return;
+    }
+    *nt = (rows + ti_max - 1) / ti_max;
+    *ti = (rows + *nt - 1) / *nt;
+  };
+  int t_pos = 0;
+  split(i_neg, &m.t_neg, &m.ti_neg);
+  split(g->nv1 - i_neg, &t_pos, &m.ti_pos);
+  m.n_tiles = m.t_neg + t_pos;
+  m.stage_elems = (std::max(m.ti_neg, m.ti_pos) + 2) * g->pitch;
+  m.n_chunks = 1;
+  m.chunk_len = g->nx;
+  if (g->use_stream) {
+    const int per_sm = stream_ctas_per_sm(g->prec, stream_smem_bytes(g->prec, m.stage_elems));
+    if (per_sm <= 0) {
+      g->use_stream = false;
+    } else {
+      // about one wave: (tiles x chunks) CTAs for the resident slots, and at
+      // least 4 planes per chunk (the upwind plane is loaded once per chunk)
+      const int nc = std::max(1, std::min(sms * per_sm / m.n_tiles, (g->nx + 3) / 4));
+      m.chunk_len = (g->nx + nc - 1) / nc;
+      m.n_chunks = (g->nx + m.chunk_len - 1) / m.chunk_len;
+    }
+  }
   return FK_OK;
 }
 
@@ -297,9 +363,17 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
     g->own_stream = true;
   }
   CREATE_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
-  const size_t nv = (size_t)d.nv1 * d.nv2;
+  const size_t nv = (size_t)d.nv1 * g->pitch;  // 2D tables use the row pitch
   const size_t fbytes = (size_t)d.nx * d.nv1 * g->pitch * g->esize;
-  g->part.nu = step_units_per_plane(d.nv1, d.nv2);
+  {
+    fk_status gs = plan_geometry(g);
+    if (gs != FK_OK) {
+      g_create_error = g->err;
+      free_grid(g);
+      return gs;
+    }
+  }
+  g->part.nu = g->geom.n_tiles;
   const size_t nparts = (size_t)d.nx * g->part.nu;
   CREATE_CUDA(dalloc(&g->d_prm, sizeof(Params)));
   CREATE_CUDA(dalloc(&g->d_st, sizeof(DevState)));
@@ -307,6 +381,7 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   CREATE_CUDA(dalloc(&g->d_f[1], fbytes));
   CREATE_CUDA(dalloc(&g->tab.v1, d.nv1 * sizeof(double)));
   CREATE_CUDA(dalloc(&g->tab.cx, d.nv1 * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->tab.cx32, d.nv1 * sizeof(float)));
   CREATE_CUDA(dalloc(&g->tab.delta, nv * sizeof(double)));
   CREATE_CUDA(dalloc(&g->tab.gse, nv * sizeof(double)));
   CREATE_CUDA(dalloc(&g->tab.src, nv * sizeof(double)));
@@ -320,6 +395,7 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   CREATE_CUDA(dalloc(&g->d_ne, d.nx * sizeof(double)));
   CREATE_CUDA(dalloc(&g->d_Ex, d.nx * sizeof(double)));
   CREATE_CUDA(dalloc(&g->d_c1, d.nx * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->d_c1_32, d.nx * sizeof(float)));
   CREATE_CUDA(dalloc(&g->d_hist, (size_t)p.hist_cap * FK_HISTORY_COLS * sizeof(double)));
   CREATE_CUDA(cudaMemsetAsync(g->d_f[0], 0, fbytes, g->stream));
   CREATE_CUDA(cudaMemsetAsync(g->d_f[1], 0, fbytes, g->stream));
@@ -423,13 +499,10 @@ fk_status fk_step(fk_grid* g, int64_t n) {
   FK_CUDA(g, cudaSetDevice(g->dev));
   while (n > 0) {
     if (g->timing) {
-      StepArgs a = make_args(g, g->enq_cur);
       const bool rec = g->ev_used < kMaxTimed;
-      if (rec) FK_CUDA(g, cudaEventRecord(g->ev[2 * g->ev_used], g->stream));
-      FK_CUDA(g, launch_step(a, g->prec, 0, g->stream));
-      if (rec) FK_CUDA(g, cudaEventRecord(g->ev[2 * g->ev_used + 1], g->stream));
+      FK_CUDA(g, enqueue_step(g, g->enq_cur, g->stream, rec ? g->ev[2 * g->ev_used] : nullptr,
+                              rec ? g->ev[2 * g->ev_used + 1] : nullptr));
       if (rec) g->ev_used++;
-      FK_CUDA(g, launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_hist, kModeStep, g->stream));
       g->enq_cur ^= 1;
       n -= 1;
     } else if (n >= kGraphSteps) {
@@ -440,9 +513,7 @@ fk_status fk_step(fk_grid* g, int64_t n) {
       FK_CUDA(g, cudaGraphLaunch(g->graph[g->enq_cur], g->stream));
       n -= kGraphSteps;  // even: the current buffer is unchanged
     } else {
-      StepArgs a = make_args(g, g->enq_cur);
-      FK_CUDA(g, launch_step(a, g->prec, 0, g->stream));
-      FK_CUDA(g, launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_hist, kModeStep, g->stream));
+      FK_CUDA(g, enqueue_step(g, g->enq_cur, g->stream, nullptr, nullptr));
       g->enq_cur ^= 1;
       n -= 1;
     }
@@ -610,6 +681,10 @@ fk_status fk_grid_info(const fk_grid* g, double* out) {
   out[3] = g->dt;
   out[4] = g->prm.c2;
   out[5] = g->prm.cx_max;
+  out[6] = g->use_stream ? 1.0 : 0.0;
+  out[7] = g->geom.n_tiles;
+  out[8] = g->geom.n_chunks;
+  out[9] = g->geom.chunk_len;
   return FK_OK;
 }
 

@@ -60,40 +60,81 @@ struct Partials {
   double* pe;   // [nu]     sum over x = 0 cells with v1 < 0 of -v1 f^{n+1}
   double* see;  // [nu]     same weighted by delta
   double* vac;  // [nu]     sum over x = nx-1 cells with v1 > 0 of v1 f^{n+1}
-  int nu;       // units per plane
+  int nu;       // units (tiles) per plane
 };
 
+// Velocity-space tables.  2D tables use the row pitch of f (zero padding).
 struct Tables {
   double* v1;     // [nv1] cell-centre normal velocities
   double* cx;     // [nv1] signed x-Courant numbers v1 dt / dx
-  double* delta;  // [nv1][nv2] SEE yield, zero where v1 >= 0
-  double* gse;    // [nv1][nv2] emission shape, unit flux
-  double* src;    // [nv1][nv2] dt * S / (band plane) = dt (J/e)/W g_fe
+  float* cx32;    // [nv1] the same rounded to FP32
+  double* delta;  // [nv1][pitch] SEE yield, zero where v1 >= 0
+  double* gse;    // [nv1][pitch] emission shape, unit flux
+  double* src;    // [nv1][pitch] dt (J/e)/W g_fe, added on source planes
   float* src32;   // same rounded to FP32
-  double* gfe_raw;// [nv1][nv2] scratch for the source shape
+  double* gfe_raw;// [nv1][pitch] scratch for the source shape
 };
+
+// Work decomposition shared by the step kernels and the finalize kernel.
+// v1 rows split at i_neg: rows [0, i_neg) have v1 <= 0 (upwind in x is
+// k+1, march toward -x), rows [i_neg, nv1) have v1 > 0 (upwind k-1, march
+// toward +x).  Each half is cut into tiles of at most ti rows; a tile never
+// straddles the split, so one x-upwind direction holds for the whole tile.
+// The march along x is cut into chunks; one CTA of the streaming kernel
+// owns one (tile, chunk) unit.
+struct Geom {
+  int ti_neg, ti_pos;  // rows per tile in each half (last tile may be short)
+  int i_neg;           // first row with v1 > 0
+  int t_neg, n_tiles;  // tiles in the lower half, tiles in total
+  int chunk_len, n_chunks;
+  int stage_elems;     // elements of one shared-memory stage
+};
+
+__host__ __device__ inline void tile_rows(const Geom& g, int nv1, int t, int* i0, int* i1,
+                                          int* dir) {
+  if (t < g.t_neg) {
+    *i0 = t * g.ti_neg;
+    *i1 = (*i0 + g.ti_neg < g.i_neg) ? *i0 + g.ti_neg : g.i_neg;
+    *dir = -1;
+  } else {
+    const int u = t - g.t_neg;
+    *i0 = g.i_neg + u * g.ti_pos;
+    *i1 = (*i0 + g.ti_pos < nv1) ? *i0 + g.ti_pos : nv1;
+    *dir = 1;
+  }
+}
 
 struct StepArgs {
   const void* f_in;
   void* f_out;
   int nx, nv1, nv2, pitch;  // pitch = row stride of f in elements (>= nv2)
   const double* c1;         // [nx] signed v1-Courant numbers of f^n
+  const float* c1_32;       // [nx] the same rounded to FP32
   const Params* prm;
   DevState* st;
   Tables tab;
   Partials part;
+  Geom geom;
 };
 
 // Launchers (return the launch error).
-cudaError_t launch_tables(const Tables& t, const Params* prm_dev, int nv1, int nv2,
+cudaError_t launch_tables(const Tables& t, int nv1, int nv2, int pitch,
                           double v1_min, double v2_min, double dv1, double dv2,
                           double dt, double dx, double delta_max, double A_max,
                           double k_s, double T_se, double T_fe, double J_over_eW,
                           cudaStream_t s);
+// Direct-load step (and moments-only evaluation): one block per (plane, tile).
 cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cudaStream_t s);
-int step_units_per_plane(int nv1, int nv2);
+// Streaming step: one CTA per (tile, chunk), bulk-async staged planes.
+cudaError_t launch_step_stream(const StepArgs& a, int precision, cudaStream_t s);
+// Rows per tile of the streaming kernel for this precision and row pitch
+// so that two CTAs fit on an SM (0 if a row does not fit), its shared
+// memory per CTA, resident CTAs per SM.
+int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per_block);
+size_t stream_smem_bytes(int precision, int stage_elems);
+int stream_ctas_per_sm(int precision, size_t smem_bytes);
 cudaError_t launch_finalize(const StepArgs& a, double* ne, double* Ex, double* c1,
-                            double* hist, int mode, cudaStream_t s);
+                            float* c1_32, double* hist, int mode, cudaStream_t s);
 cudaError_t launch_convert(const void* src, void* dst, size_t rows, int nv2, int pitch,
                            int to_f32, cudaStream_t s);
 

@@ -56,34 +56,36 @@ __device__ __forceinline__ double cell_centre(double lo, int i, double h) {
 }
 
 __global__ void __launch_bounds__(kTabThreads)
-tables_kernel(Tables t, int nv1, int nv2, double v1_min, double v2_min, double dv1,
+tables_kernel(Tables t, int nv1, int nv2, int pitch, double v1_min, double v2_min, double dv1,
               double dv2, double dt, double dx, double dmax, double amax, double ks,
               double Tse, double Tfe, double j_over_ew) {
   __shared__ double sh[32];
   __shared__ double norms[2];
   double s_se = 0.0, s_fe = 0.0;
-  const int ncell = nv1 * nv2;
+  const int ncell = nv1 * pitch;
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-    const int i = c / nv2, j = c - (c / nv2) * nv2;
-    const double v1 = cell_centre(v1_min, i, dv1);
-    const double v2 = cell_centre(v2_min, j, dv2);
-    const double vv = v1 * v1 + v2 * v2;
-    double d = 0.0;
-    if (v1 < 0.0) {
-      const double A = 0.5 * kMe * vv / kQe;         // Eq. 10, eV
-      const double al = atan(fabs(v2 / v1));         // Eq. 11
-      const double z = 1.284 * A / (amax * (1.0 + ks * al * al / kPi));  // Eq. 9
-      if (z > 0.0)
-        d = 1.526 * dmax * (1.0 + ks * al * al / (2.0 * kPi)) *
-            (1.0 - exp(-pow(z, 1.725))) / pow(z, 0.725);  // Eq. 8
+    const int i = c / pitch, j = c - (c / pitch) * pitch;
+    double d = 0.0, gs = 0.0, gf = 0.0;
+    if (j < nv2) {
+      const double v1 = cell_centre(v1_min, i, dv1);
+      const double v2 = cell_centre(v2_min, j, dv2);
+      const double vv = v1 * v1 + v2 * v2;
+      if (v1 < 0.0) {
+        const double A = 0.5 * kMe * vv / kQe;                             // Eq. 10, eV
+        const double al = atan(fabs(v2 / v1));                             // Eq. 11
+        const double z = 1.284 * A / (amax * (1.0 + ks * al * al / kPi));  // Eq. 9
+        if (z > 0.0)
+          d = 1.526 * dmax * (1.0 + ks * al * al / (2.0 * kPi)) *
+              (1.0 - exp(-pow(z, 1.725))) / pow(z, 0.725);  // Eq. 8
+      }
+      gs = v1 > 0.0 ? exp(-kMe * vv / (2.0 * Tse * kQe)) : 0.0;  // Eq. 15 shape
+      s_se += v1 * gs;
+      gf = v2 > 0.0 ? exp(-kMe * vv / (2.0 * Tfe * kQe)) : 0.0;  // Eq. 7 shape
+      s_fe += gf;
     }
     t.delta[c] = d;
-    const double gs = v1 > 0.0 ? exp(-kMe * vv / (2.0 * Tse * kQe)) : 0.0;
     t.gse[c] = gs;
-    s_se += v1 * gs;
-    const double gf = v2 > 0.0 ? exp(-kMe * vv / (2.0 * Tfe * kQe)) : 0.0;
     t.gfe_raw[c] = gf;
-    s_fe += gf;
   }
   s_se = block_sum<kTabThreads>(s_se, sh);
   s_fe = block_sum<kTabThreads>(s_fe, sh);
@@ -103,22 +105,24 @@ tables_kernel(Tables t, int nv1, int nv2, double v1_min, double v2_min, double d
     const double v1 = cell_centre(v1_min, i, dv1);
     t.v1[i] = v1;
     t.cx[i] = __ddiv_rn(__dmul_rn(v1, dt), dx);
+    t.cx32[i] = (float)t.cx[i];
   }
 }
 
-cudaError_t launch_tables(const Tables& t, const Params*, int nv1, int nv2, double v1_min,
+cudaError_t launch_tables(const Tables& t, int nv1, int nv2, int pitch, double v1_min,
                           double v2_min, double dv1, double dv2, double dt, double dx,
                           double delta_max, double A_max, double k_s, double T_se,
                           double T_fe, double j_over_ew, cudaStream_t s) {
-  tables_kernel<<<1, kTabThreads, 0, s>>>(t, nv1, nv2, v1_min, v2_min, dv1, dv2, dt, dx,
+  tables_kernel<<<1, kTabThreads, 0, s>>>(t, nv1, nv2, pitch, v1_min, v2_min, dv1, dv2, dt, dx,
                                           delta_max, A_max, k_s, T_se, T_fe, j_over_ew);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Direct-load step kernel.  One block per work unit = (plane k, band of R
-// rows of v1).  Each thread updates cells of the unit; every neighbour is a
-// plain load (the L1/L2 caches catch the re-reads).
+// Direct-load step kernel.  One block per (plane k, tile t): the tile's rows
+// [i0, i1) times all v2 cells.  Every neighbour is a plain load (L1/L2 catch
+// the re-reads).  Used for the moments-only evaluation of a state and as the
+// step for grids whose rows do not fit the streaming kernel's tiles.
 //
 // Per cell, with c_x = v1 dt/dx, c_1 = a1(x) dt/dv1, c_2 = a2 dt/dv2 and the
 // upwind neighbour f_u in each direction (zero beyond a velocity edge or the
@@ -126,18 +130,6 @@ cudaError_t launch_tables(const Tables& t, const Params*, int nv1, int nv2, doub
 //   f' = f - |c_x|(f - f_ux) - |c_1|(f - f_u1) - |c_2|(f - f_u2) + dt S
 // which is the donor-cell flux difference of Eq. 2 written per cell.
 constexpr int kStepThreads = 256;
-constexpr int kCellsPerUnit = 4096;
-
-int step_rows_per_unit(int nv1, int nv2) {
-  int r = kCellsPerUnit / nv2;
-  if (r < 1) r = 1;
-  if (r > nv1) r = nv1;
-  return r;
-}
-int step_units_per_plane(int nv1, int nv2) {
-  const int r = step_rows_per_unit(nv1, nv2);
-  return (nv1 + r - 1) / r;
-}
 
 template <typename T>
 __device__ __forceinline__ T update_cell(T f, T fx, T fv, T fw, T ax, T a1, T a2, T s);
@@ -146,7 +138,8 @@ template <>
 __device__ __forceinline__ double update_cell<double>(double f, double fx, double fv,
                                                       double fw, double ax, double a1,
                                                       double a2, double s) {
-  // convex form: (1 - ax - a1 - a2) f + ax fx + a1 fv + a2 fw + s
+  // convex form: (1 - ax - a1 - a2) f + ax fx + a1 fv + a2 fw + s; every
+  // weight is >= 0 under the CFL condition, so nothing cancels
   const double d = 1.0 - ax - a1 - a2;
   return fma(a2, fw, fma(a1, fv, fma(ax, fx, fma(d, f, s))));
 }
@@ -154,80 +147,87 @@ __device__ __forceinline__ double update_cell<double>(double f, double fx, doubl
 template <>
 __device__ __forceinline__ float update_cell<float>(float f, float fx, float fv, float fw,
                                                     float ax, float a1, float a2, float s) {
-  // increment form keeps one rounding of f per step dominant
+  // increment form: one rounding of f per step dominates the error
   const float inc = fmaf(a2, fw - f, fmaf(a1, fv - f, fmaf(ax, fx - f, s)));
   return f + inc;
 }
 
 template <typename T>
+struct Acc;  // per-thread accumulator type of the density moment
+template <>
+struct Acc<double> { using type = double; };
+template <>
+struct Acc<float> { using type = float; };
+
+template <typename T>
 __global__ void __launch_bounds__(kStepThreads)
-step_direct_kernel(StepArgs a, int rows, int moments_only) {
+step_direct_kernel(StepArgs a, int moments_only) {
   __shared__ double sh[32];
-  const int nu = a.part.nu;
-  const int k = blockIdx.x / nu;
-  const int u = blockIdx.x - k * nu;
+  __shared__ unsigned s_flags;
+  const int nt = a.part.nu;
+  const int k = blockIdx.x / nt;
+  const int t = blockIdx.x - k * nt;
   const Params& p = *a.prm;
-  if (!moments_only && a.st->flags) return;  // sticky error: freeze the state
+  if (threadIdx.x == 0) s_flags = a.st->flags;
+  __syncthreads();
+  if (!moments_only && s_flags) return;  // sticky error: freeze the state
   const T* __restrict__ fin = static_cast<const T*>(a.f_in);
   T* __restrict__ fout = static_cast<T*>(a.f_out);
   const int nx = a.nx, nv1 = a.nv1, nv2 = a.nv2, pitch = a.pitch;
   const size_t plane = (size_t)nv1 * pitch;
-  const double c1d = a.c1[k];
-  const double c2d = p.c2;
+  int i0, i1, dir;
+  tile_rows(a.geom, nv1, t, &i0, &i1, &dir);
+  // per-plane coefficients in the arithmetic type (no FP64 work per cell
+  // on the FP32 path)
+  const T c1 = sizeof(T) == 8 ? (T)a.c1[k] : (T)a.c1_32[k];
+  const T c2 = (T)p.c2;
+  const T a1 = c1 < (T)0 ? -c1 : c1, a2 = c2 < (T)0 ? -c2 : c2;
   const double gsee = a.st->g_see;
   const bool band = k >= p.band_lo && k < p.band_hi;
-  const int i0 = u * rows;
-  const int i1 = min(nv1, i0 + rows);
   const int ncell = (i1 - i0) * nv2;
-  double s_n = 0.0, s_lv = 0.0, s_pe = 0.0, s_see = 0.0, s_vac = 0.0;
-  const T a1 = (T)fabs(c1d), a2 = (T)fabs(c2d);
+  typename Acc<T>::type s_n = 0;
+  double s_lv = 0.0, s_pe = 0.0, s_see = 0.0, s_vac = 0.0;
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
     const int i = i0 + c / nv2;
     const int j = c - (c / nv2) * nv2;
     const size_t idx = (size_t)k * plane + (size_t)i * pitch + j;
+    const size_t tix = (size_t)i * pitch + j;
     const T f = fin[idx];
-    const double cxd = a.tab.cx[i];
-    T fx = (T)0;
-    if (cxd > 0.0)
-      fx = k > 0 ? fin[idx - plane] : (T)(gsee * a.tab.gse[i * nv2 + j]);
-    else if (cxd < 0.0)
-      fx = k < nx - 1 ? fin[idx + plane] : (T)0;
-    T fv = (T)0;
-    if (c1d > 0.0)
-      fv = i > 0 ? fin[idx - pitch] : (T)0;
-    else if (c1d < 0.0)
-      fv = i < nv1 - 1 ? fin[idx + pitch] : (T)0;
-    T fw = (T)0;
-    if (c2d > 0.0)
-      fw = j > 0 ? fin[idx - 1] : (T)0;
-    else if (c2d < 0.0)
-      fw = j < nv2 - 1 ? fin[idx + 1] : (T)0;
-    T s = (T)0;
-    if (band) {
-      if (sizeof(T) == 8)
-        s = (T)a.tab.src[i * nv2 + j];
-      else
-        s = (T)a.tab.src32[i * nv2 + j];
-    }
     T fn = f;
     if (!moments_only) {
-      fn = update_cell<T>(f, fx, fv, fw, (T)fabs(cxd), a1, a2, s);
+      const T cx = sizeof(T) == 8 ? (T)a.tab.cx[i] : (T)a.tab.cx32[i];
+      T fx = (T)0;
+      if (cx > (T)0)
+        fx = k > 0 ? fin[idx - plane] : (T)(gsee * a.tab.gse[tix]);
+      else if (cx < (T)0)
+        fx = k < nx - 1 ? fin[idx + plane] : (T)0;
+      T fv = (T)0;
+      if (c1 > (T)0)
+        fv = i > 0 ? fin[idx - pitch] : (T)0;
+      else if (c1 < (T)0)
+        fv = i < nv1 - 1 ? fin[idx + pitch] : (T)0;
+      T fw = (T)0;
+      if (c2 > (T)0)
+        fw = j > 0 ? fin[idx - 1] : (T)0;
+      else if (c2 < (T)0)
+        fw = j < nv2 - 1 ? fin[idx + 1] : (T)0;
+      T s = (T)0;
+      if (band) s = sizeof(T) == 8 ? (T)a.tab.src[tix] : (T)a.tab.src32[tix];
+      fn = update_cell<T>(f, fx, fv, fw, cx < (T)0 ? -cx : cx, a1, a2, s);
       fout[idx] = fn;
       // loss through the downwind velocity edges, from f^n (ledger)
-      if ((c1d > 0.0 && i == nv1 - 1) || (c1d < 0.0 && i == 0)) s_lv += fabs(c1d) * (double)f;
-      if ((c2d > 0.0 && j == nv2 - 1) || (c2d < 0.0 && j == 0)) s_lv += fabs(c2d) * (double)f;
+      if ((c1 > (T)0 && i == nv1 - 1) || (c1 < (T)0 && i == 0)) s_lv += (double)a1 * (double)f;
+      if ((c2 > (T)0 && j == nv2 - 1) || (c2 < (T)0 && j == 0)) s_lv += (double)a2 * (double)f;
     }
-    const double fnd = (double)fn;
-    s_n += fnd;
-    const double v1 = a.tab.v1[i];
-    if (k == 0 && v1 < 0.0) {
-      const double g = -v1 * fnd;  // Eq. 13 without dv1 dv2
+    s_n += fn;
+    if (k == 0 && dir < 0) {
+      const double g = -a.tab.v1[i] * (double)fn;  // Eq. 13 without dv1 dv2
       s_pe += g;
-      s_see += a.tab.delta[i * nv2 + j] * g;  // Eq. 12
+      s_see += a.tab.delta[tix] * g;  // Eq. 12
     }
-    if (k == nx - 1 && v1 > 0.0) s_vac += v1 * fnd;
+    if (k == nx - 1 && dir > 0) s_vac += a.tab.v1[i] * (double)fn;
   }
-  s_n = block_sum<kStepThreads>(s_n, sh);
+  const double n_tot = block_sum<kStepThreads>((double)s_n, sh);
   s_lv = block_sum<kStepThreads>(s_lv, sh);
   if (k == 0) {
     s_pe = block_sum<kStepThreads>(s_pe, sh);
@@ -235,23 +235,22 @@ step_direct_kernel(StepArgs a, int rows, int moments_only) {
   }
   if (k == nx - 1) s_vac = block_sum<kStepThreads>(s_vac, sh);
   if (threadIdx.x == 0) {
-    a.part.n[(size_t)k * nu + u] = s_n;
-    a.part.lv[(size_t)k * nu + u] = s_lv;
+    a.part.n[(size_t)k * nt + t] = n_tot;
+    a.part.lv[(size_t)k * nt + t] = s_lv;
     if (k == 0) {
-      a.part.pe[u] = s_pe;
-      a.part.see[u] = s_see;
+      a.part.pe[t] = s_pe;
+      a.part.see[t] = s_see;
     }
-    if (k == nx - 1) a.part.vac[u] = s_vac;
+    if (k == nx - 1) a.part.vac[t] = s_vac;
   }
 }
 
 cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cudaStream_t s) {
-  const int rows = step_rows_per_unit(a.nv1, a.nv2);
   const int nblk = a.nx * a.part.nu;
   if (precision == FK_F32)
-    step_direct_kernel<float><<<nblk, kStepThreads, 0, s>>>(a, rows, moments_only);
+    step_direct_kernel<float><<<nblk, kStepThreads, 0, s>>>(a, moments_only);
   else
-    step_direct_kernel<double><<<nblk, kStepThreads, 0, s>>>(a, rows, moments_only);
+    step_direct_kernel<double><<<nblk, kStepThreads, 0, s>>>(a, moments_only);
   return cudaGetLastError();
 }
 
@@ -267,7 +266,8 @@ cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cuda
 constexpr int kFinThreads = 1024;
 
 __global__ void __launch_bounds__(kFinThreads)
-finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, double* hist, int mode) {
+finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, double* hist,
+                int mode) {
   __shared__ double sh[32];
   __shared__ double wsum[32];
   __shared__ double bc[8];
@@ -367,6 +367,7 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, double* hist, in
     Ex[k] = e;
     const double c = -kQe * e / kMe * p.dt / p.dv1;
     c1[k] = c;
+    c1_32[k] = (float)c;
     cmax = fmax(cmax, fabs(c));
   }
   cmax = block_max<kFinThreads>(cmax, sh);
@@ -396,8 +397,8 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, double* hist, in
 }
 
 cudaError_t launch_finalize(const StepArgs& a, double* ne, double* Ex, double* c1,
-                            double* hist, int mode, cudaStream_t s) {
-  finalize_kernel<<<1, kFinThreads, 0, s>>>(a, ne, Ex, c1, hist, mode);
+                            float* c1_32, double* hist, int mode, cudaStream_t s) {
+  finalize_kernel<<<1, kFinThreads, 0, s>>>(a, ne, Ex, c1, c1_32, hist, mode);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,468 @@
+// Streaming step kernel: one explicit upwind step of Eq. 2 (Sun et al.,
+// arXiv 2303.14119, Sec. 2) over the whole phase-space grid, one read of
+// f^n and one write of f^{n+1} per cell.
+//
+// Decomposition.  A CTA owns one unit = (tile of v1 rows [i0, i1) times all
+// v2 cells, chunk of consecutive x-planes).  All rows of a tile have the
+// same sign of v1, so the x-upwind neighbour of plane k is plane k - dir
+// for the whole tile; the CTA marches through its chunk in the direction
+// dir, and every consumer thread keeps the previous plane's input values of
+// its own cells in registers: the x-neighbour never comes from memory twice.
+//
+// Pipeline.  Planes arrive in shared memory through cp.async.bulk copies
+// (the TMA engine) into a ring of kStages stages.  Each stage holds the
+// tile's rows plus the one v1 halo row on the upwind side of that plane's
+// c_1.  Warp roles:
+//  - consumer warps (kWarps): wait until a stage is full, update their cells
+//    (FP32/INT work only on the FP32 path), store f^{n+1}, sum it per warp,
+//    and release the stage;
+//  - the producer warp: when a stage is released, fold the warp sums of its
+//    plane into the per-(plane, tile) partial sums, add the boundary terms
+//    of that plane (outflow through the downwind velocity edges from f^n,
+//    still in the stage; on x = 0 and x = h_max the wall fluxes of
+//    Eqs. 12-14 and the vacuum outflow of f^{n+1}), then refill the stage.
+// There is no block-wide barrier inside the march.
+//
+// Per cell: f' = f + |c_x|(f_ux - f) + |c_1|(f_u1 - f) + |c_2|(f_u2 - f) + dt S
+// (FP32: increment form) or the convex form of the same sum (FP64).
+#include <stdint.h>
+
+#include "fk_internal.cuh"
+
+namespace fk {
+
+namespace {
+
+constexpr int kThreads = 224;            // consumer threads (7 warps)
+constexpr int kWarps = kThreads / 32;    // consumer warps; one producer warp follows
+constexpr int kBlock = kThreads + 32;
+constexpr int kStages = 4;
+constexpr int kVecPerThread = 8;         // 16-byte vectors per consumer thread and plane
+constexpr long long kWaitLimit = 4000000000LL;  // cycles (~2 s) before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity; false if it did not complete
+// within kWaitLimit cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitLimit) return false;
+  return true;
+}
+
+template <typename T>
+struct alignas(16) Vec {
+  static constexpr int N = 16 / sizeof(T);
+  T e[N];
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T upd(T f, T fx, T fv, T fw, T ax, T a1, T a2, T s, T d);
+template <>
+__device__ __forceinline__ float upd<float>(float f, float fx, float fv, float fw, float ax,
+                                            float a1, float a2, float s, float) {
+  const float inc = fmaf(a2, fw - f, fmaf(a1, fv - f, fmaf(ax, fx - f, s)));
+  return f + inc;
+}
+template <>
+__device__ __forceinline__ double upd<double>(double f, double fx, double fv, double fw,
+                                              double ax, double a1, double a2, double s,
+                                              double d) {
+  // every weight is >= 0 under the CFL condition: nothing cancels
+  return fma(a2, fw, fma(a1, fv, fma(ax, fx, fma(d, f, s))));
+}
+
+template <typename T>
+__host__ __device__ constexpr size_t stage_bytes(int stage_elems) {
+  return ((size_t)stage_elems * sizeof(T) + 127) / 128 * 128;
+}
+// mbarriers full[kStages], empty[kStages]; warp sums [kStages][kWarps];
+// two control ints
+constexpr size_t kTailBytes =
+    2 * kStages * sizeof(uint64_t) + kStages * kWarps * sizeof(double) + 16;
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
+  constexpr int VEC = Vec<T>::N;
+  constexpr int M = kVecPerThread;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Geom& gm = a.geom;
+  const size_t sbytes = stage_bytes<T>(gm.stage_elems);
+  unsigned char* stage_base = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * sbytes);
+  uint64_t* empty = full + kStages;
+  double* wsum = reinterpret_cast<double*>(empty + kStages);  // [kStages][kWarps]
+  int* ctl = reinterpret_cast<int*>(wsum + kStages * kWarps);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nt = gm.n_tiles;
+  const int t = blockIdx.x % nt, chunk = blockIdx.x / nt;
+  const int nx = a.nx, nv1 = a.nv1, nv2 = a.nv2, pitch = a.pitch;
+  int i0, i1, dir;
+  tile_rows(gm, nv1, t, &i0, &i1, &dir);
+  const int s0 = chunk * gm.chunk_len;
+  const int s1 = min(nx, s0 + gm.chunk_len);
+  if (s0 >= s1 || i0 >= i1) return;  // uniform over the block
+
+  // march: step s visits plane k(s); the upwind plane of the first one is
+  // loaded first ("prime" item) unless it lies outside the domain
+  const int k_first = dir > 0 ? s0 : nx - 1 - s0;
+  const int k_up = k_first - dir;
+  const bool prime = k_up >= 0 && k_up < nx;
+  const int n_items = (s1 - s0) + (prime ? 1 : 0);
+  auto item_plane = [&](int q) -> int {
+    const int s = s0 + q - (prime ? 1 : 0);
+    if (s < s0) return k_up;
+    return dir > 0 ? s : nx - 1 - s;
+  };
+
+  if (tid == 0) {
+    ctl[0] = (int)a.st->flags;
+    for (int s = 0; s < kStages; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kThreads);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (ctl[0]) return;  // sticky error: freeze the state (uniform)
+
+  const Params& p = *a.prm;
+  const T* __restrict__ fin = static_cast<const T*>(a.f_in);
+  T* __restrict__ fout = static_cast<T*>(a.f_out);
+  const size_t plane = (size_t)nv1 * pitch;
+  const int QV = pitch / VEC;  // vectors per row
+  const int rows = i1 - i0;
+
+  if (warp == kWarps) {
+    // ============================ producer warp ============================
+    auto issue = [&](int q) {  // lane 0 only
+      const int k = item_plane(q);
+      const float c1 = a.c1_32[k];
+      int lo = i0, hi = i1;
+      if (c1 > 0.f && i0 > 0) lo = i0 - 1;  // v1 halo row on the upwind side
+      if (c1 < 0.f && i1 < nv1) hi = i1 + 1;
+      const int st = q % kStages;
+      T* dst = reinterpret_cast<T*>(stage_base + st * sbytes) + (size_t)(lo - (i0 - 1)) * pitch;
+      const T* src = fin + (size_t)k * plane + (size_t)lo * pitch;
+      const uint32_t bytes = (uint32_t)((hi - lo) * pitch * sizeof(T));
+      mbar_expect_tx(&full[st], bytes);
+      bulk_g2s(dst, src, bytes, &full[st]);
+    };
+    // a consumed compute item: partial sums of its plane (all 32 lanes)
+    auto retire = [&](int q) {
+      if (prime && q == 0) return;
+      const int k = item_plane(q);
+      const int st = q % kStages;
+      const T* sb = reinterpret_cast<const T*>(stage_base + st * sbytes);
+      const float c1f = a.c1_32[k];
+      const double a1 = c1f == 0.f ? 0.0 : fabs(a.c1[k]);
+      const double a2 = fabs(p.c2);
+      // ledger: outflow of f^n through the downwind velocity edges
+      double lv = 0.0;
+      const int erow = (c1f > 0.f && i1 == nv1) ? nv1 - 1 : ((c1f < 0.f && i0 == 0) ? 0 : -1);
+      if (erow >= 0) {
+        const T* r = sb + (size_t)(erow - i0 + 1) * pitch;
+        for (int j = lane; j < nv2; j += 32) lv += a1 * (double)r[j];
+      }
+      if (a2 > 0.0)
+        for (int r = lane; r < rows; r += 32)
+          lv += a2 * (double)sb[(size_t)(r + 1) * pitch + nv2 - 1];
+      // wall fluxes of f^{n+1} (Eqs. 12-14) and vacuum outflow; the
+      // consumers' stores are visible after the acquire on empty
+      double pe = 0.0, see = 0.0, vac = 0.0;
+      const bool wall = k == 0 && dir < 0, vout = k == nx - 1 && dir > 0;
+      if (wall || vout) {
+        const T* orow = fout + (size_t)k * plane;
+        for (int c = lane; c < rows * nv2; c += 32) {
+          const int r = c / nv2, j = c - (c / nv2) * nv2;
+          const int i = i0 + r;
+          const double fn = (double)orow[(size_t)i * pitch + j];
+          const double v1 = a.tab.v1[i];
+          if (wall) {
+            const double g = -v1 * fn;  // Eq. 13 without dv1 dv2
+            pe += g;
+            see += a.tab.delta[(size_t)i * pitch + j] * g;  // Eq. 12
+          } else {
+            vac += v1 * fn;
+          }
+        }
+      }
+      lv = warp_sum(lv);
+      if (wall || vout) {
+        pe = warp_sum(pe);
+        see = warp_sum(see);
+        vac = warp_sum(vac);
+      }
+      if (lane == 0) {
+        double sn = 0.0;
+        for (int w = 0; w < kWarps; w++) sn += wsum[st * kWarps + w];  // fixed order
+        a.part.n[(size_t)k * nt + t] = sn;
+        a.part.lv[(size_t)k * nt + t] = lv;
+        if (k == 0) {
+          a.part.pe[t] = pe;
+          a.part.see[t] = see;
+        }
+        if (k == nx - 1) a.part.vac[t] = vac;
+      }
+    };
+    int issued = 0;
+    bool ok = true;
+    for (int q = 0; q < n_items; q++) {
+      if (q >= kStages) {
+        // stage reuse: wait until every consumer thread released item q - kStages
+        ok = __all_sync(0xffffffffu,
+                        mbar_wait(&empty[q % kStages], (uint32_t)(((q / kStages) - 1) & 1)));
+        if (!ok) break;
+        retire(q - kStages);
+        __syncwarp();  // the stage is read by every lane before it is refilled
+      }
+      if (lane == 0) issue(q);
+      issued = q + 1;
+    }
+    for (int q = max(0, issued - kStages); q < issued && ok; q++) {
+      ok = __all_sync(0xffffffffu, mbar_wait(&empty[q % kStages], (uint32_t)((q / kStages) & 1)));
+      if (ok) retire(q);
+    }
+    if (!ok && lane == 0) {
+      atomicOr(&a.st->flags, kFlagTimeout);
+      // copies still in flight land before the CTA leaves
+      for (int q = max(0, issued - kStages); q < issued; q++)
+        mbar_wait(&full[q % kStages], (uint32_t)((q / kStages) & 1));
+    }
+    return;
+  }
+
+  // ============================ consumer warps =============================
+  // this thread's cells: vectors v = tid + kThreads*m of the tile
+  int vi[M], vq[M];
+  T ax[M];
+  T xr[M][VEC];
+#pragma unroll
+  for (int m = 0; m < M; m++) {
+    const int v = tid + kThreads * m;
+    vi[m] = -1;
+    vq[m] = 0;
+    ax[m] = (T)0;
+    if (v < rows * QV) {
+      const int r = v / QV;
+      vi[m] = i0 + r;
+      vq[m] = v - r * QV;
+      const T cx = sizeof(T) == 8 ? (T)a.tab.cx[vi[m]] : (T)a.tab.cx32[vi[m]];
+      ax[m] = cx < (T)0 ? -cx : cx;
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; e++) xr[m][e] = (T)0;
+  }
+  if (!prime && dir > 0) {
+    // first plane is x = 0 with v1 > 0: the upwind value is the re-emitted
+    // distribution Gamma_see g_se of Eq. 15 (zero for the vacuum side)
+    const double gsee = a.st->g_see;
+#pragma unroll
+    for (int m = 0; m < M; m++) {
+      if (vi[m] < 0) continue;
+#pragma unroll
+      for (int e = 0; e < VEC; e++)
+        xr[m][e] = (T)(gsee * a.tab.gse[(size_t)vi[m] * pitch + vq[m] * VEC + e]);
+    }
+  }
+  const T c2 = (T)p.c2;
+  const T a2 = c2 < (T)0 ? -c2 : c2;
+  T dxm[M];  // 1 - |c_x| - |c_2|; the plane's |c_1| is subtracted per item
+#pragma unroll
+  for (int m = 0; m < M; m++) dxm[m] = (T)1 - ax[m] - a2;
+
+  for (int q = 0; q < n_items; q++) {
+    const int st = q % kStages;
+    const bool compute = !(prime && q == 0);
+    const int k = item_plane(q);
+    // per-plane values and the source row (L2-resident table) are fetched
+    // before waiting for the stage, so their latency overlaps the wait
+    const float c1f = a.c1_32[k];
+    const T a1 = c1f == 0.f ? (T)0 : (sizeof(T) == 8 ? (T)fabs(a.c1[k]) : (T)fabsf(c1f));
+    const bool band = compute && k >= p.band_lo && k < p.band_hi;
+    Vec<T> srcv[M];
+#pragma unroll
+    for (int m = 0; m < M; m++) {
+      if (band && vi[m] >= 0) {
+        const T* sp = (sizeof(T) == 8 ? (const T*)a.tab.src : (const T*)a.tab.src32) +
+                      (size_t)vi[m] * pitch + vq[m] * VEC;
+        srcv[m] = *reinterpret_cast<const Vec<T>*>(sp);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VEC; e++) srcv[m].e[e] = (T)0;
+      }
+    }
+    const bool ok = mbar_wait(&full[st], (uint32_t)((q / kStages) & 1));
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (lane == 0) atomicOr(&a.st->flags, kFlagTimeout);
+      return;
+    }
+    const T* sb = reinterpret_cast<const T*>(stage_base + st * sbytes);
+    if (!compute) {
+#pragma unroll
+      for (int m = 0; m < M; m++) {
+        if (vi[m] < 0) continue;
+        const Vec<T> own = *reinterpret_cast<const Vec<T>*>(
+            sb + (size_t)(vi[m] - i0 + 1) * pitch + vq[m] * VEC);
+#pragma unroll
+        for (int e = 0; e < VEC; e++) xr[m][e] = own.e[e];
+      }
+    } else {
+      // the direction comes from the FP32 copy, as in the producer, so the
+      // halo row read below is always the one that was copied
+      const bool up1 = c1f > 0.f, dn1 = c1f < 0.f;
+      T sum_n = (T)0;
+      T* orow = fout + (size_t)k * plane;
+#pragma unroll
+      for (int m = 0; m < M; m++) {
+        const int i = vi[m];
+        const int r = i - i0;  // garbage if invalid, unused then
+        const T* srow = sb + (size_t)(r + 1) * pitch;
+        Vec<T> own;
+        if (i >= 0)
+          own = *reinterpret_cast<const Vec<T>*>(srow + vq[m] * VEC);
+        else
+#pragma unroll
+          for (int e = 0; e < VEC; e++) own.e[e] = (T)0;
+        // v2 upwind (c_2 >= 0 since E_y <= 0): element j-1
+        T left = __shfl_up_sync(0xffffffffu, own.e[VEC - 1], 1);
+        if (i < 0) continue;
+        if (vq[m] == 0)
+          left = (T)0;
+        else if (lane == 0)
+          left = srow[vq[m] * VEC - 1];
+        // v1 upwind row
+        Vec<T> nb;
+        if (up1 && i > 0)
+          nb = *reinterpret_cast<const Vec<T>*>(srow - pitch + vq[m] * VEC);
+        else if (dn1 && i < nv1 - 1)
+          nb = *reinterpret_cast<const Vec<T>*>(srow + pitch + vq[m] * VEC);
+        else
+#pragma unroll
+          for (int e = 0; e < VEC; e++) nb.e[e] = (T)0;
+        const T d = dxm[m] - a1;
+        Vec<T> out;
+        const int j0 = vq[m] * VEC;
+#pragma unroll
+        for (int e = 0; e < VEC; e++) {
+          const T f = own.e[e];
+          const T fw = e == 0 ? left : own.e[e - 1];
+          T fn = upd<T>(f, xr[m][e], nb.e[e], fw, ax[m], a1, a2, srcv[m].e[e], d);
+          if (j0 + e >= nv2) fn = (T)0;  // row padding stays zero
+          out.e[e] = fn;
+          xr[m][e] = f;  // x-upwind value for the next plane is f^n here
+          sum_n += fn;
+        }
+        __stcs(reinterpret_cast<float4*>(orow + (size_t)i * pitch + j0),
+               *reinterpret_cast<const float4*>(&out));
+      }
+      // warp sum of this plane's f^{n+1} (an FP32 grid sums its 32 lanes in
+      // FP32; everything above a warp is FP64)
+      const T ws = warp_sum(sum_n);
+      if (lane == 0) wsum[st * kWarps + warp] = (double)ws;
+    }
+    mbar_arrive(&empty[st]);  // this thread is done with stage st
+  }
+}
+
+}  // namespace
+
+int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per_block) {
+  const int esize = precision == FK_F32 ? 4 : 8;
+  const int vec = 16 / esize;
+  const int cells = kThreads * kVecPerThread * vec;
+  if (pitch > cells) return 0;
+  int rows = cells / pitch;
+  // two CTAs per SM: each holds kStages stages of (rows + 2) * pitch elements
+  const long budget = (long)smem_per_sm / 2 - reserved_per_block - (long)kTailBytes;
+  const long stage = budget / kStages / 128 * 128;
+  const long fit = stage / ((long)pitch * esize) - 2;
+  if (fit < rows) rows = (int)fit;
+  return rows > 0 ? rows : 0;
+}
+
+size_t stream_smem_bytes(int precision, int stage_elems) {
+  const size_t sb = precision == FK_F32 ? stage_bytes<float>(stage_elems)
+                                        : stage_bytes<double>(stage_elems);
+  return kStages * sb + kTailBytes;
+}
+
+int stream_ctas_per_sm(int precision, size_t smem_bytes) {
+  // the attribute is per kernel, shared by every grid: allow the device's
+  // largest opt-in size once, and ask the occupancy of this grid's size
+  int dev = 0, optin = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  if (smem_bytes > (size_t)optin) return 0;
+  cudaError_t e;
+  if (precision == FK_F32) {
+    e = cudaFuncSetAttribute(step_stream_kernel<float>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_stream_kernel<float>, kBlock,
+                                                        smem_bytes);
+  } else {
+    e = cudaFuncSetAttribute(step_stream_kernel<double>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_stream_kernel<double>, kBlock,
+                                                        smem_bytes);
+  }
+  return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_step_stream(const StepArgs& a, int precision, cudaStream_t s) {
+  const int grid = a.geom.n_tiles * a.geom.n_chunks;
+  const size_t smem = stream_smem_bytes(precision, a.geom.stage_elems);
+  if (precision == FK_F32)
+    step_stream_kernel<float><<<grid, kBlock, smem, s>>>(a);
+  else
+    step_stream_kernel<double><<<grid, kBlock, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace fk

@@ -215,10 +215,15 @@ def fk_set_surface_charge(g, sigma):
     _check(load().fk_set_surface_charge(g, float(sigma)), "fk_set_surface_charge", g)
 
 
+FK_INFO_LEN = 10
+
+
 def fk_grid_info(g):
-    out = np.empty(6)
+    out = np.empty(FK_INFO_LEN)
     _check(load().fk_grid_info(g, _dp(out)), "fk_grid_info", g)
-    return dict(dx=out[0], dv1=out[1], dv2=out[2], dt=out[3], c2=out[4], cx_max=out[5])
+    return dict(dx=out[0], dv1=out[1], dv2=out[2], dt=out[3], c2=out[4], cx_max=out[5],
+                kernel="stream" if out[6] else "direct", n_tiles=int(out[7]),
+                n_chunks=int(out[8]), chunk_len=int(out[9]))
 
 
 def fk_set_kernel_timing(g, enabled):

@@ -49,17 +49,17 @@ def both(g, o, name, *args):
     getattr(o, name)(*args)
 
 
-def strong_physics(g, o, shape, seed=1, h=20e-6, V1=6e7, V2=3e7):
+def strong_physics(g, o, shape, seed=1, h=20e-6, V1=6e7, V2=3e7, c1f=0.25, c2f=0.2):
     """Every term active with large Courant numbers: E_x self-consistent and
-    changing sign across x, large E_y, SEE with a spread emission shape, a
-    strong source.  Returns (f0, sigma0)."""
+    changing sign across x (|c_1| up to about c1f), large E_y (c_2 = c2f),
+    SEE with a spread emission shape, a strong source.  Returns (f0, sigma0)."""
     nx, nv1, nv2 = shape
     info = o.info()
-    a2 = 0.2 * info["dv2"] / info["dt"]
+    a2 = c2f * info["dv2"] / info["dt"]
     both(g, o, "set_fields", -a2 * ME / QE, True, 0.0)
     both(g, o, "set_see", 3.0, 400.0, 1.0, 400.0)
-    both(g, o, "set_source", 1e7, 0.3 * h, 0.7 * h, 300.0)
-    emax = 0.25 * info["dv1"] / info["dt"] * ME / QE
+    both(g, o, "set_source", 1e7, 0.2 * h, 0.7 * h, 300.0)
+    emax = c1f * info["dv1"] / info["dt"] * ME / QE
     sigma = 2 * EPS0 * emax * 0.8
     n_tot = 1.6 * emax * EPS0 / QE
     amp = 2 * n_tot / (h * 2 * V1 * 2 * V2)
@@ -100,6 +100,28 @@ def test_fp64_per_step_parity_all_terms(shape):
         g.step(1)
         o.step(1)
         compare_state(g, o, 1e-12, 1e-12)
+    g.close()
+
+
+@pytest.mark.parametrize("kernel", ["stream", "direct"])
+@pytest.mark.parametrize("prec,tol", [(fk.FK_F64, 1e-12), (fk.FK_F32, 2e-7)])
+def test_both_step_kernels_per_step(kernel, prec, tol, monkeypatch):
+    """The streaming kernel and the direct-load kernel against the oracle."""
+    if kernel == "direct":
+        monkeypatch.setenv("FK_STEP_KERNEL", "direct")
+    else:
+        monkeypatch.delenv("FK_STEP_KERNEL", raising=False)
+    shape = (21, 70, 36)
+    g, o = make_pair(shape, prec=prec)
+    f0, sigma = strong_physics(g, o, shape, seed=12)
+    g.set_state(f0, sigma)
+    for _ in range(3):
+        o.set_state(g.get_f(), g.surface_charge())
+        g.step(1)
+        o.step(1)
+        assert rel_l1(g.get_f(), o.get_f()) <= tol
+        assert rel(g.surface_charge(), o.surface_charge()) <= 1e-12
+        assert rel(g.moments()[2], o.moments()[2]) <= 1e-12 if prec == fk.FK_F64 else True
     g.close()
 
 
@@ -271,7 +293,7 @@ def test_fp32_small_workload_1000_steps():
 def test_fp32_strong_1000_steps():
     shape = (16, 24, 20)
     g, o = make_pair(shape, prec=fk.FK_F32)
-    f0, sigma = strong_physics(g, o, shape, seed=8)
+    f0, sigma = strong_physics(g, o, shape, seed=8, c1f=0.05, c2f=0.2)  # stays within CFL
     g.set_state(f0, sigma)
     o.set_state(g.get_f(), sigma)
     g.step(1000)
