@@ -193,6 +193,33 @@ fk_status fk_set_kernel_timing(fk_grid *grid, int enabled);
  * The records are consumed. */
 fk_status fk_kernel_timing(fk_grid *grid, int64_t *launches, double *total_ms);
 
+/* Density moment without allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc themselves or
+ * let a library do it -- code that runs while a stream is being captured
+ * into a CUDA graph (allocation is not allowed there), applications whose
+ * device memory is owned by their own pool allocator, and loops that cannot
+ * afford the device-wide synchronisation an allocation may cause.
+ *
+ * Computes n_e[k] = dv1 dv2 * sum_{i,j} f[k][i][j] for k < nx from a
+ * distribution the caller already holds in device memory (f_dev: FP64,
+ * dense [nx][nv1][nv2]) into the caller's device array n_e_dev[nx], both on
+ * cuda_stream (NULL = the legacy default stream).  Stream-ordered and
+ * asynchronous; it allocates nothing.  Its scratch is one fixed array of
+ * FK_NOALLOC_MAX_PARTIALS doubles (1 MiB) in the library's device memory,
+ * held by every GPU that loads the library until the process exits, so
+ * nx <= FK_NOALLOC_MAX_PARTIALS / 16 = 8192; larger nx returns FK_EINVAL
+ * with the limit in fk_last_error(NULL).  Every call shares that array and
+ * overwrites the slots it uses before reading them, so nothing needs
+ * clearing; calls that overlap on the GPU (different streams or devices
+ * sharing one context) race on it and must be ordered by the caller.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * Errors: FK_EINVAL (NULL pointer, non-positive size or spacing, nx above
+ * the limit), FK_ECUDA (no current device, lookup or launch failure). */
+#define FK_NOALLOC_MAX_PARTIALS 131072
+fk_status fk_density_moment_noalloc(const double *f_dev, int32_t nx, int32_t nv1, int32_t nv2,
+                                    double dv1, double dv2, double *n_e_dev, void *cuda_stream);
+
 /* Text of the last error on this grid ("" if none).  grid may be NULL for
  * errors of fk_create_grid on the calling thread.  Valid until the next call
  * on the same grid. */

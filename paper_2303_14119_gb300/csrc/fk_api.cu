@@ -28,6 +28,8 @@ constexpr size_t kStageElems = size_t(1) << 23;  // FP64 staging chunk, 64 MB
 
 }  // namespace
 
+void fk::set_thread_error(const char* msg) { g_create_error = msg; }
+
 struct fk_grid {
   int dev = 0;
   cudaStream_t stream = nullptr;

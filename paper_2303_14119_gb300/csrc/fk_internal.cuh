@@ -140,4 +140,7 @@ cudaError_t launch_convert(const void* src, void* dst, size_t rows, int nv2, int
 
 enum FinalizeMode { kModeStep = 0, kModeRefresh = 1, kModeReset = 2 };
 
+// Error text for calls without a grid (read back by fk_last_error(NULL)).
+void set_thread_error(const char* msg);
+
 }  // namespace fk

@@ -319,3 +319,24 @@ class Grid:
 
     def kernel_timing(self):
         return fk_kernel_timing(self.h)
+
+
+FK_NOALLOC_MAX_PARTIALS = 131072
+_noalloc_ready = False
+
+
+def fk_density_moment_noalloc(f_dev_ptr, nx, nv1, nv2, dv1, dv2, n_e_dev_ptr, stream=None):
+    """Density moment of a caller-held device array without any allocation
+    by the library (see include/fk.h): f_dev_ptr and n_e_dev_ptr are raw
+    device addresses, e.g. ``tensor.data_ptr()`` of CUDA tensors."""
+    global _noalloc_ready
+    lib = load()
+    fn = lib.fk_density_moment_noalloc
+    if not _noalloc_ready:
+        fn.restype = C.c_int
+        fn.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
+                       C.c_void_p, C.c_void_p]
+        _noalloc_ready = True
+    _check(fn(C.c_void_p(f_dev_ptr), int(nx), int(nv1), int(nv2), float(dv1), float(dv2),
+              C.c_void_p(n_e_dev_ptr), C.c_void_p(stream) if stream else None),
+           "fk_density_moment_noalloc")
