@@ -62,7 +62,7 @@ typedef enum {
 } fk_precision;
 
 /* Grid description.
- * nx, nv1, nv2 >= 2 cells; h_max > 0 (m); v1_min < v1_max, v2_min < v2_max
+ * 2 <= nx <= 8192 and 2 <= nv1, nv2 <= 65536 cells; h_max > 0 (m); v1_min < v1_max, v2_min < v2_max
  * (m/s); dt > 0 (s), or dt <= 0 to take dt = cfl * dx / max(|v1_min|,
  * |v1_max|) with cfl > 0; history_capacity = rows kept in the device history
  * ring (0 selects 65536).  Sec. 2, paragraph on default parameters: "grid

@@ -180,11 +180,11 @@ fk_status rebuild_tables(fk_grid* g) {
 
 // Parameters changed: rebuild tables, re-evaluate the current state and
 // rewrite its history row.  Clears a CFL flag (the new fields may fix it).
-fk_status refresh(fk_grid* g) {
+fk_status refresh(fk_grid* g, bool tables) {
   fk_status s = clear_flags(g, kFlagCfl);
   if (s != FK_OK) return s;
   if ((s = upload_params(g)) != FK_OK) return s;
-  if ((s = rebuild_tables(g)) != FK_OK) return s;
+  if (tables && (s = rebuild_tables(g)) != FK_OK) return s;
   return evaluate(g, kModeRefresh);
 }
 
@@ -293,8 +293,8 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   const fk_grid_desc& d = *desc;
   if (d.nx < 2 || d.nv1 < 2 || d.nv2 < 2)
     return fail(nullptr, FK_EINVAL, "nx, nv1, nv2 must be >= 2");
-  if (d.nv1 > (1 << 16) || d.nv2 > (1 << 16) || d.nx > (1 << 20))
-    return fail(nullptr, FK_EINVAL, "grid dimension too large");
+  if (d.nv1 > (1 << 16) || d.nv2 > (1 << 16) || d.nx > 8192)
+    return fail(nullptr, FK_EINVAL, "grid too large: nx <= 8192, nv1, nv2 <= 65536");
   if (!(d.h_max > 0) || !(d.v1_min < d.v1_max) || !(d.v2_min < d.v2_max) ||
       !isfinite(d.h_max) || !isfinite(d.v1_min) || !isfinite(d.v1_max) ||
       !isfinite(d.v2_min) || !isfinite(d.v2_max))
@@ -336,6 +336,13 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   p.cx_max = cx_max;
   p.inj = 0;
   p.sat_tol = 1e-3;
+  // Gauss's law from the wall (E_x(0) = sigma / (2 eps0), space charge -e n)
+  // and the v1-Courant number c_1 = a1 dt / dv1 with a1 = -e E_x / m_e
+  p.ex_sigma = 1.0 / (2.0 * kEps0);
+  p.ex_n = kQe / kEps0 * g->dx;
+  p.c1_per_ex = -kQe / kMe * g->dt / g->dv1;
+  p.dvv = g->dv1 * g->dv2;
+  p.lv_scale = g->dx * g->dv1 * g->dv2 / g->dt;
   p.sat_window = 10000;
   p.hist_cap = d.history_capacity > 0 ? d.history_capacity : 65536;
   p.self_consistent = 1;
@@ -439,7 +446,7 @@ fk_status fk_set_fields(fk_grid* g, double Ey, int self_consistent, double Ex_ex
   g->prm.Ex_ext = Ex_external;
   g->prm.self_consistent = g->self_consistent;
   g->prm.c2 = (-kQe * Ey / kMe) * g->dt / g->dv2;
-  return refresh(g);
+  return refresh(g, false);  // the tables do not depend on the fields
 }
 
 fk_status fk_set_see(fk_grid* g, double delta_max, double A_max_eV, double k_s, double T_se_eV,
@@ -454,7 +461,7 @@ fk_status fk_set_see(fk_grid* g, double delta_max, double A_max_eV, double k_s, 
   g->T_se = T_se_eV;
   g->see_enabled = enabled ? 1 : 0;
   g->prm.see_enabled = g->see_enabled;
-  return refresh(g);
+  return refresh(g, true);
 }
 
 fk_status fk_set_source(fk_grid* g, double J, double x_lo, double x_hi, double T_fe_eV) {
@@ -482,7 +489,7 @@ fk_status fk_set_source(fk_grid* g, double J, double x_lo, double x_hi, double T
     g->prm.band_lo = g->prm.band_hi = 0;
     g->prm.inj = 0.0;
   }
-  return refresh(g);
+  return refresh(g, true);
 }
 
 fk_status fk_set_convergence(fk_grid* g, int64_t window, double rel_tol) {

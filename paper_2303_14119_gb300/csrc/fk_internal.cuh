@@ -33,6 +33,10 @@ struct Params {
   double cx_max;  // max_i |v1_i| dt / dx
   double inj;     // injected electrons per m^2 per s (J/e, 0 if off)
   double sat_tol;
+  // host-computed coefficients of the finalize kernel (no division on the
+  // device): E_x = sigma * ex_sigma - ex_n * (sum of n below + n_k / 2),
+  // c_1 = c1_per_ex * E_x, density scale dv1 dv2, loss scale dx dv1 dv2 / dt
+  double ex_sigma, ex_n, c1_per_ex, dvv, lv_scale;
   long long sat_window;
   long long hist_cap;
   int self_consistent;

@@ -264,6 +264,7 @@ cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cuda
 //  - CFL and finiteness checks (sticky flags), history row, convergence
 //    test (Sec. 2, paragraph after Eq. 18).
 constexpr int kFinThreads = 1024;
+constexpr int kFinMaxPer = 8;  // planes per thread held in registers (nx <= 8192)
 
 __global__ void __launch_bounds__(kFinThreads)
 finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, double* hist,
@@ -278,18 +279,25 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, do
   const int t = threadIdx.x;
   const int per = (nx + kFinThreads - 1) / kFinThreads;
   const int k0 = min(nx, t * per), k1 = min(nx, k0 + per);
-  const double dvv = p.dv1 * p.dv2;
-  // per-plane sums over units, fixed order
+  const double dvv = p.dvv;
+  // per-plane sums over units, fixed order; kept in registers
+  double nk[kFinMaxPer];
   double loc_n = 0.0, loc_lv = 0.0;
-  for (int k = k0; k < k1; k++) {
-    double sn = 0.0, sl = 0.0;
-    for (int u = 0; u < nu; u++) {
-      sn += a.part.n[(size_t)k * nu + u];
-      sl += a.part.lv[(size_t)k * nu + u];
+#pragma unroll
+  for (int q = 0; q < kFinMaxPer; q++) {
+    nk[q] = 0.0;
+    const int k = k0 + q;
+    if (k < k1) {
+      double sn = 0.0, sl = 0.0;
+      for (int u = 0; u < nu; u++) {
+        sn += a.part.n[(size_t)k * nu + u];
+        sl += a.part.lv[(size_t)k * nu + u];
+      }
+      nk[q] = sn * dvv;
+      ne[k] = nk[q];
+      loc_n += nk[q];
+      loc_lv += sl;
     }
-    ne[k] = sn * dvv;
-    loc_n += sn * dvv;
-    loc_lv += sl;
   }
   // exclusive scan of the per-thread chunk totals (fixed order)
   const int lane = t & 31, w = t >> 5;
@@ -326,7 +334,7 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, do
     see = p.see_enabled ? see * dvv : 0.0;
     vac *= dvv;
     if (mode == kModeStep) {
-      const double lv = lvtot * p.dx * dvv / p.dt;
+      const double lv = lvtot * p.lv_scale;
       st->cum_emit += p.dt * st->g_see;
       st->cum_see += p.dt * st->g_see;
       st->cum_pe += p.dt * st->g_pe;
@@ -354,21 +362,22 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, do
     bc[0] = st->sigma;
   }
   __syncthreads();
-  const double sigma = bc[0];
+  const double e_wall = bc[0] * p.ex_sigma;
   // E_x at cell centres and the v1-Courant numbers
   double run = before;
   double cmax = 0.0;
-  for (int k = k0; k < k1; k++) {
-    const double nk = ne[k];
-    const double e = p.self_consistent
-                         ? sigma / (2.0 * kEps0) - kQe / kEps0 * p.dx * (run + 0.5 * nk)
-                         : p.Ex_ext;
-    run += nk;
-    Ex[k] = e;
-    const double c = -kQe * e / kMe * p.dt / p.dv1;
-    c1[k] = c;
-    c1_32[k] = (float)c;
-    cmax = fmax(cmax, fabs(c));
+#pragma unroll
+  for (int q = 0; q < kFinMaxPer; q++) {
+    const int k = k0 + q;
+    if (k < k1) {
+      const double e = p.self_consistent ? e_wall - p.ex_n * (run + 0.5 * nk[q]) : p.Ex_ext;
+      run += nk[q];
+      Ex[k] = e;
+      const double c = p.c1_per_ex * e;
+      c1[k] = c;
+      c1_32[k] = (float)c;
+      cmax = fmax(cmax, fabs(c));
+    }
   }
   cmax = block_max<kFinThreads>(cmax, sh);
   __syncthreads();

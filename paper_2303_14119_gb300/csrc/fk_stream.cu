@@ -123,7 +123,7 @@ __host__ __device__ constexpr size_t stage_bytes(int stage_elems) {
 constexpr size_t kTailBytes =
     2 * kStages * sizeof(uint64_t) + kStages * kWarps * sizeof(double) + 16;
 
-template <typename T>
+template <typename T, bool PADDED>
 __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
   constexpr int VEC = Vec<T>::N;
   constexpr int M = kVecPerThread;
@@ -178,18 +178,34 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
 
   if (warp == kWarps) {
     // ============================ producer warp ============================
-    auto issue = [&](int q) {  // lane 0 only
+    // all 32 lanes: where the upwind v1 halo row lies outside the velocity
+    // grid, fill its slot with zeros (zero inflow through the v1 edge) so
+    // the consumers read a neighbour row without a bounds test; then lane 0
+    // copies plane k's tile rows plus the halo row inside the grid
+    auto issue = [&](int q) {
       const int k = item_plane(q);
       const float c1 = a.c1_32[k];
-      int lo = i0, hi = i1;
-      if (c1 > 0.f && i0 > 0) lo = i0 - 1;  // v1 halo row on the upwind side
-      if (c1 < 0.f && i1 < nv1) hi = i1 + 1;
       const int st = q % kStages;
-      T* dst = reinterpret_cast<T*>(stage_base + st * sbytes) + (size_t)(lo - (i0 - 1)) * pitch;
-      const T* src = fin + (size_t)k * plane + (size_t)lo * pitch;
-      const uint32_t bytes = (uint32_t)((hi - lo) * pitch * sizeof(T));
-      mbar_expect_tx(&full[st], bytes);
-      bulk_g2s(dst, src, bytes, &full[st]);
+      T* stage = reinterpret_cast<T*>(stage_base + st * sbytes);
+      int zrow = -1;
+      if (c1 > 0.f && i0 == 0) zrow = 0;
+      if (c1 < 0.f && i1 == nv1) zrow = rows + 1;
+      if (zrow >= 0) {
+        float4* z = reinterpret_cast<float4*>(stage + (size_t)zrow * pitch);
+        const int n16 = pitch * (int)sizeof(T) / 16;
+        for (int c = lane; c < n16; c += 32) z[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        int lo = i0, hi = i1;
+        if (c1 > 0.f && i0 > 0) lo = i0 - 1;  // v1 halo row on the upwind side
+        if (c1 < 0.f && i1 < nv1) hi = i1 + 1;
+        T* dst = stage + (size_t)(lo - (i0 - 1)) * pitch;
+        const T* src = fin + (size_t)k * plane + (size_t)lo * pitch;
+        const uint32_t bytes = (uint32_t)((hi - lo) * pitch * sizeof(T));
+        mbar_expect_tx(&full[st], bytes);  // release: the zero row is visible too
+        bulk_g2s(dst, src, bytes, &full[st]);
+      }
     };
     // a consumed compute item: partial sums of its plane (all 32 lanes)
     auto retire = [&](int q) {
@@ -259,7 +275,7 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
         retire(q - kStages);
         __syncwarp();  // the stage is read by every lane before it is refilled
       }
-      if (lane == 0) issue(q);
+      issue(q);
       issued = q + 1;
     }
     for (int q = max(0, issued - kStages); q < issued && ok; q++) {
@@ -276,21 +292,24 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
   }
 
   // ============================ consumer warps =============================
-  // this thread's cells: vectors v = tid + kThreads*m of the tile
-  int vi[M], vq[M];
+  // this thread's cells: vectors v = tid + kThreads*m of the tile, fixed for
+  // the whole march; per vector its offset in a stage and in a plane
+  int soff[M];  // global offset in a plane = soff + gbase
+  const int gbase = (i0 - 1) * pitch;
+  unsigned valid = 0, zleft = 0;  // bit m: vector m exists / starts a row
   T ax[M];
   T xr[M][VEC];
 #pragma unroll
   for (int m = 0; m < M; m++) {
     const int v = tid + kThreads * m;
-    vi[m] = -1;
-    vq[m] = 0;
+    soff[m] = 0;
     ax[m] = (T)0;
     if (v < rows * QV) {
-      const int r = v / QV;
-      vi[m] = i0 + r;
-      vq[m] = v - r * QV;
-      const T cx = sizeof(T) == 8 ? (T)a.tab.cx[vi[m]] : (T)a.tab.cx32[vi[m]];
+      const int r = v / QV, qv = v - r * QV;
+      valid |= 1u << m;
+      if (qv == 0) zleft |= 1u << m;
+      soff[m] = (r + 1) * pitch + qv * VEC;
+      const T cx = sizeof(T) == 8 ? (T)a.tab.cx[i0 + r] : (T)a.tab.cx32[i0 + r];
       ax[m] = cx < (T)0 ? -cx : cx;
     }
 #pragma unroll
@@ -302,17 +321,14 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
     const double gsee = a.st->g_see;
 #pragma unroll
     for (int m = 0; m < M; m++) {
-      if (vi[m] < 0) continue;
+      if (!(valid >> m & 1)) continue;
 #pragma unroll
-      for (int e = 0; e < VEC; e++)
-        xr[m][e] = (T)(gsee * a.tab.gse[(size_t)vi[m] * pitch + vq[m] * VEC + e]);
+      for (int e = 0; e < VEC; e++) xr[m][e] = (T)(gsee * a.tab.gse[soff[m] + gbase + e]);
     }
   }
   const T c2 = (T)p.c2;
   const T a2 = c2 < (T)0 ? -c2 : c2;
-  T dxm[M];  // 1 - |c_x| - |c_2|; the plane's |c_1| is subtracted per item
-#pragma unroll
-  for (int m = 0; m < M; m++) dxm[m] = (T)1 - ax[m] - a2;
+  const T* srcbase = sizeof(T) == 8 ? (const T*)a.tab.src : (const T*)a.tab.src32;
 
   for (int q = 0; q < n_items; q++) {
     const int st = q % kStages;
@@ -326,10 +342,8 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
     Vec<T> srcv[M];
 #pragma unroll
     for (int m = 0; m < M; m++) {
-      if (band && vi[m] >= 0) {
-        const T* sp = (sizeof(T) == 8 ? (const T*)a.tab.src : (const T*)a.tab.src32) +
-                      (size_t)vi[m] * pitch + vq[m] * VEC;
-        srcv[m] = *reinterpret_cast<const Vec<T>*>(sp);
+      if (band && (valid >> m & 1)) {
+        srcv[m] = *reinterpret_cast<const Vec<T>*>(srcbase + soff[m] + gbase);
       } else {
 #pragma unroll
         for (int e = 0; e < VEC; e++) srcv[m].e[e] = (T)0;
@@ -344,59 +358,48 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
     if (!compute) {
 #pragma unroll
       for (int m = 0; m < M; m++) {
-        if (vi[m] < 0) continue;
-        const Vec<T> own = *reinterpret_cast<const Vec<T>*>(
-            sb + (size_t)(vi[m] - i0 + 1) * pitch + vq[m] * VEC);
+        if (!(valid >> m & 1)) continue;
+        const Vec<T> own = *reinterpret_cast<const Vec<T>*>(sb + soff[m]);
 #pragma unroll
         for (int e = 0; e < VEC; e++) xr[m][e] = own.e[e];
       }
     } else {
+      // v1 upwind row: one row up (c_1 > 0), one down (c_1 < 0) or none;
       // the direction comes from the FP32 copy, as in the producer, so the
-      // halo row read below is always the one that was copied
-      const bool up1 = c1f > 0.f, dn1 = c1f < 0.f;
+      // row read is always one that was copied or zero-filled
+      const int nboff = c1f > 0.f ? -pitch : (c1f < 0.f ? pitch : 0);
+      const T dbase = (T)1 - a1 - a2;  // minus |c_x| per vector: the FP64 diagonal
       T sum_n = (T)0;
-      T* orow = fout + (size_t)k * plane;
+      T* oplane = fout + (size_t)k * plane;
 #pragma unroll
       for (int m = 0; m < M; m++) {
-        const int i = vi[m];
-        const int r = i - i0;  // garbage if invalid, unused then
-        const T* srow = sb + (size_t)(r + 1) * pitch;
         Vec<T> own;
-        if (i >= 0)
-          own = *reinterpret_cast<const Vec<T>*>(srow + vq[m] * VEC);
+        if (valid >> m & 1)
+          own = *reinterpret_cast<const Vec<T>*>(sb + soff[m]);
         else
 #pragma unroll
           for (int e = 0; e < VEC; e++) own.e[e] = (T)0;
         // v2 upwind (c_2 >= 0 since E_y <= 0): element j-1
         T left = __shfl_up_sync(0xffffffffu, own.e[VEC - 1], 1);
-        if (i < 0) continue;
-        if (vq[m] == 0)
+        if (!(valid >> m & 1)) continue;
+        if (zleft >> m & 1)
           left = (T)0;
         else if (lane == 0)
-          left = srow[vq[m] * VEC - 1];
-        // v1 upwind row
-        Vec<T> nb;
-        if (up1 && i > 0)
-          nb = *reinterpret_cast<const Vec<T>*>(srow - pitch + vq[m] * VEC);
-        else if (dn1 && i < nv1 - 1)
-          nb = *reinterpret_cast<const Vec<T>*>(srow + pitch + vq[m] * VEC);
-        else
-#pragma unroll
-          for (int e = 0; e < VEC; e++) nb.e[e] = (T)0;
-        const T d = dxm[m] - a1;
+          left = sb[soff[m] - 1];
+        const Vec<T> nb = *reinterpret_cast<const Vec<T>*>(sb + soff[m] + nboff);
+        const T d = dbase - ax[m];
         Vec<T> out;
-        const int j0 = vq[m] * VEC;
 #pragma unroll
         for (int e = 0; e < VEC; e++) {
           const T f = own.e[e];
           const T fw = e == 0 ? left : own.e[e - 1];
           T fn = upd<T>(f, xr[m][e], nb.e[e], fw, ax[m], a1, a2, srcv[m].e[e], d);
-          if (j0 + e >= nv2) fn = (T)0;  // row padding stays zero
+          if (PADDED && (soff[m] % pitch) + e >= nv2) fn = (T)0;  // row padding stays zero
           out.e[e] = fn;
           xr[m][e] = f;  // x-upwind value for the next plane is f^n here
           sum_n += fn;
         }
-        __stcs(reinterpret_cast<float4*>(orow + (size_t)i * pitch + j0),
+        __stcs(reinterpret_cast<float4*>(oplane + soff[m] + gbase),
                *reinterpret_cast<const float4*>(&out));
       }
       // warp sum of this plane's f^{n+1} (an FP32 grid sums its 32 lanes in
@@ -439,29 +442,40 @@ int stream_ctas_per_sm(int precision, size_t smem_bytes) {
     return 0;
   if (smem_bytes > (size_t)optin) return 0;
   cudaError_t e;
+  void (*kern[2])(StepArgs);
   if (precision == FK_F32) {
-    e = cudaFuncSetAttribute(step_stream_kernel<float>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_stream_kernel<float>, kBlock,
-                                                        smem_bytes);
+    kern[0] = step_stream_kernel<float, false>;
+    kern[1] = step_stream_kernel<float, true>;
   } else {
-    e = cudaFuncSetAttribute(step_stream_kernel<double>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_stream_kernel<double>, kBlock,
-                                                        smem_bytes);
+    kern[0] = step_stream_kernel<double, false>;
+    kern[1] = step_stream_kernel<double, true>;
   }
-  return e == cudaSuccess ? n : 0;
+  int best = 1 << 30;
+  for (int v = 0; v < 2; v++) {
+    e = cudaFuncSetAttribute(kern[v], cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern[v], kBlock, smem_bytes);
+    if (e != cudaSuccess) return 0;
+    best = n < best ? n : best;
+  }
+  return best;
 }
 
 cudaError_t launch_step_stream(const StepArgs& a, int precision, cudaStream_t s) {
   const int grid = a.geom.n_tiles * a.geom.n_chunks;
   const size_t smem = stream_smem_bytes(precision, a.geom.stage_elems);
-  if (precision == FK_F32)
-    step_stream_kernel<float><<<grid, kBlock, smem, s>>>(a);
-  else
-    step_stream_kernel<double><<<grid, kBlock, smem, s>>>(a);
+  const bool padded = a.pitch != a.nv2;
+  if (precision == FK_F32) {
+    if (padded)
+      step_stream_kernel<float, true><<<grid, kBlock, smem, s>>>(a);
+    else
+      step_stream_kernel<float, false><<<grid, kBlock, smem, s>>>(a);
+  } else {
+    if (padded)
+      step_stream_kernel<double, true><<<grid, kBlock, smem, s>>>(a);
+    else
+      step_stream_kernel<double, false><<<grid, kBlock, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
