@@ -53,6 +53,7 @@ struct fk_grid {
   bool use_stream = true;  // streaming kernel (else the direct-load kernel)
   double *d_ne = nullptr, *d_Ex = nullptr, *d_c1 = nullptr, *d_hist = nullptr;
   float* d_c1_32 = nullptr;
+  FinScratch fin{};
   void* d_stage = nullptr;
   // physics parameters as last set
   double Ey = 0, Ex_ext = 0;
@@ -139,7 +140,7 @@ fk_status sync_state(fk_grid* g, DevState* out) {
 fk_status evaluate(fk_grid* g, int mode) {
   StepArgs a = make_args(g, g->enq_cur);
   FK_CUDA(g, launch_step(a, g->prec, 1, g->stream));
-  FK_CUDA(g, launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, mode,
+  FK_CUDA(g, launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, g->fin, mode,
                              g->stream));
   return FK_OK;
 }
@@ -153,7 +154,7 @@ cudaError_t enqueue_step(fk_grid* g, int cur, cudaStream_t s, cudaEvent_t ev0, c
     e = g->use_stream ? launch_step_stream(a, g->prec, s) : launch_step(a, g->prec, 0, s);
   if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
   if (e == cudaSuccess)
-    e = launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, kModeStep, s);
+    e = launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, g->fin, kModeStep, s);
   return e;
 }
 
@@ -198,7 +199,7 @@ void free_grid(fk_grid* g) {
                   g->tab.cx32, g->tab.delta, g->tab.gse, g->tab.src, g->tab.src32,
                   g->tab.gfe_raw, g->part.n, g->part.lv, g->part.pe, g->part.see,
                   g->part.vac, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist,
-                  g->d_stage};
+                  g->d_stage, g->fin.pre, g->fin.bsum, g->fin.blv, g->fin.counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
@@ -405,6 +406,11 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   CREATE_CUDA(dalloc(&g->d_Ex, d.nx * sizeof(double)));
   CREATE_CUDA(dalloc(&g->d_c1, d.nx * sizeof(double)));
   CREATE_CUDA(dalloc(&g->d_c1_32, d.nx * sizeof(float)));
+  CREATE_CUDA(dalloc(&g->fin.pre, d.nx * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->fin.bsum, finalize_blocks(d.nx) * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->fin.blv, finalize_blocks(d.nx) * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->fin.counter, sizeof(int)));
+  CREATE_CUDA(cudaMemsetAsync(g->fin.counter, 0, sizeof(int), g->stream));
   CREATE_CUDA(dalloc(&g->d_hist, (size_t)p.hist_cap * FK_HISTORY_COLS * sizeof(double)));
   CREATE_CUDA(cudaMemsetAsync(g->d_f[0], 0, fbytes, g->stream));
   CREATE_CUDA(cudaMemsetAsync(g->d_f[1], 0, fbytes, g->stream));

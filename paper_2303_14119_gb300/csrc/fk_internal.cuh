@@ -137,8 +137,18 @@ cudaError_t launch_step_stream(const StepArgs& a, int precision, cudaStream_t s)
 int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per_block);
 size_t stream_smem_bytes(int precision, int stage_elems);
 int stream_ctas_per_sm(int precision, size_t smem_bytes);
+// Scratch of the finalize kernel: per-plane in-block prefix of n, per-block
+// sums, and the counter that elects the last block (zero between launches).
+struct FinScratch {
+  double* pre;   // [nx]
+  double* bsum;  // [blocks]
+  double* blv;   // [blocks]
+  int* counter;  // [1]
+};
+int finalize_blocks(int nx);
 cudaError_t launch_finalize(const StepArgs& a, double* ne, double* Ex, double* c1,
-                            float* c1_32, double* hist, int mode, cudaStream_t s);
+                            float* c1_32, double* hist, const FinScratch& fs, int mode,
+                            cudaStream_t s);
 cudaError_t launch_convert(const void* src, void* dst, size_t rows, int nv2, int pitch,
                            int to_f32, cudaStream_t s);
 

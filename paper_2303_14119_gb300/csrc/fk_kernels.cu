@@ -255,84 +255,95 @@ cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cuda
 }
 
 // ---------------------------------------------------------------------------
-// Finalize: one block.  Reduces the partials in a fixed order, then
+// Finalize, after every step kernel (and after a moments-only evaluation).
+//
+// Phase A, one thread per x-plane over kFinBlocks-sized blocks: the plane's
+// density n_k from its tile partials (fixed order), the velocity-edge loss,
+// and the exclusive prefix of n within the block.  Phase B, run by the last
+// block to finish (a counter in FinScratch decides which; its sums are in a
+// fixed order, so the result does not depend on which block it is):
 //  - step mode: ledger += dt * (fluxes of f^n), sigma^{n+1} = sigma^n +
 //    e dt (Gamma_see^n - Gamma_pe^n)  (Eq. 18 summed with Eq. 14), step++;
-//  - stores the fluxes of the new state, N, n_e;
+//  - the fluxes of the new state (Eqs. 12-14), N, and the history row;
 //  - E_x from Gauss's law integrated from the wall, E_x(0) = sigma/(2 eps0)
-//    (the Poisson problem of Sec. 2), and c_1 = -e E_x dt / (m_e dv1);
-//  - CFL and finiteness checks (sticky flags), history row, convergence
-//    test (Sec. 2, paragraph after Eq. 18).
-constexpr int kFinThreads = 1024;
-constexpr int kFinMaxPer = 8;  // planes per thread held in registers (nx <= 8192)
+//    (the Poisson problem of Sec. 2), c_1 = -e E_x dt / (m_e dv1);
+//  - CFL and finiteness checks (sticky flags) and the convergence test
+//    (Sec. 2, paragraph after Eq. 18).
+// Spreading phase A over many SMs matters on GB300, whose FP64 rate per SM
+// is a small fraction of its FP32 rate.
+constexpr int kFinThreads = 128;
+constexpr int kFinMaxBlocks = 64;  // nx <= 8192
 
 __global__ void __launch_bounds__(kFinThreads)
 finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, double* hist,
-                int mode) {
+                FinScratch fs, int mode) {
   __shared__ double sh[32];
-  __shared__ double wsum[32];
-  __shared__ double bc[8];
+  __shared__ double wscan[kFinThreads / 32];
+  __shared__ int s_last;
+  __shared__ double bc[4];
+  __shared__ double boff[kFinMaxBlocks];  // phase B: sum of n over blocks below
   const Params& p = *a.prm;
   DevState* st = a.st;
   if (mode == kModeStep && st->flags) return;
   const int nx = a.nx, nu = a.part.nu;
-  const int t = threadIdx.x;
-  const int per = (nx + kFinThreads - 1) / kFinThreads;
-  const int k0 = min(nx, t * per), k1 = min(nx, k0 + per);
-  const double dvv = p.dvv;
-  // per-plane sums over units, fixed order; kept in registers
-  double nk[kFinMaxPer];
-  double loc_n = 0.0, loc_lv = 0.0;
-#pragma unroll
-  for (int q = 0; q < kFinMaxPer; q++) {
-    nk[q] = 0.0;
-    const int k = k0 + q;
-    if (k < k1) {
-      double sn = 0.0, sl = 0.0;
-      for (int u = 0; u < nu; u++) {
-        sn += a.part.n[(size_t)k * nu + u];
-        sl += a.part.lv[(size_t)k * nu + u];
-      }
-      nk[q] = sn * dvv;
-      ne[k] = nk[q];
-      loc_n += nk[q];
-      loc_lv += sl;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int k = blockIdx.x * kFinThreads + t;
+  // ---- phase A
+  double nk = 0.0, lk = 0.0;
+  if (k < nx) {
+    double sn = 0.0, sl = 0.0;
+    for (int u = 0; u < nu; u++) {
+      sn += a.part.n[(size_t)k * nu + u];
+      sl += a.part.lv[(size_t)k * nu + u];
     }
+    nk = sn * p.dvv;
+    lk = sl;
+    ne[k] = nk;
   }
-  // exclusive scan of the per-thread chunk totals (fixed order)
-  const int lane = t & 31, w = t >> 5;
-  double incl = loc_n;
+  double incl = nk;
   for (int o = 1; o < 32; o <<= 1) {
     const double y = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += y;
   }
   double excl = __shfl_up_sync(0xffffffffu, incl, 1);
   if (lane == 0) excl = 0.0;
-  if (lane == 31) wsum[w] = incl;
+  if (lane == 31) wscan[w] = incl;
   __syncthreads();
-  if (w == 0) {
-    double x = wsum[lane];
-    double xi = x;
-    for (int o = 1; o < 32; o <<= 1) {
-      const double y = __shfl_up_sync(0xffffffffu, xi, o);
-      if (lane >= o) xi += y;
-    }
-    wsum[lane] = xi - x;  // exclusive over warps
+  double woff = 0.0;
+  for (int q = 0; q < w; q++) woff += wscan[q];
+  if (k < nx) fs.pre[k] = woff + excl;  // sum of n over the block's planes below k
+  const double btot = block_sum<kFinThreads>(nk, sh);
+  const double blv = block_sum<kFinThreads>(lk, sh);
+  if (t == 0) {
+    fs.bsum[blockIdx.x] = btot;
+    fs.blv[blockIdx.x] = blv;
+    __threadfence();
+    s_last = atomicAdd(fs.counter, 1) == (int)gridDim.x - 1;
   }
   __syncthreads();
-  const double before = wsum[w] + excl;  // sum of n over planes < k0
-  const double ntot = block_sum<kFinThreads>(loc_n, sh) * p.dx;
-  const double lvtot = block_sum<kFinThreads>(loc_lv, sh);
+  if (!s_last) return;
+  // ---- phase B (last block)
+  __threadfence();
+  const int nb = gridDim.x;
   if (t == 0) {
+    *fs.counter = 0;  // ready for the next launch
+    // other blocks' results are read past L1 (__ldcg)
+    double ntot = 0.0, lvtot = 0.0;
+    for (int b = 0; b < nb; b++) {
+      boff[b] = ntot;
+      ntot += __ldcg(fs.bsum + b);
+      lvtot += __ldcg(fs.blv + b);
+    }
+    ntot *= p.dx;
     double pe = 0.0, see = 0.0, vac = 0.0;
     for (int u = 0; u < nu; u++) {
       pe += a.part.pe[u];
       see += a.part.see[u];
       vac += a.part.vac[u];
     }
-    pe *= dvv;
-    see = p.see_enabled ? see * dvv : 0.0;
-    vac *= dvv;
+    pe *= p.dvv;
+    see = p.see_enabled ? see * p.dvv : 0.0;  // with SEE off every primary is deposited
+    vac *= p.dvv;
     if (mode == kModeStep) {
       const double lv = lvtot * p.lv_scale;
       st->cum_emit += p.dt * st->g_see;
@@ -364,20 +375,16 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, do
   __syncthreads();
   const double e_wall = bc[0] * p.ex_sigma;
   // E_x at cell centres and the v1-Courant numbers
-  double run = before;
   double cmax = 0.0;
-#pragma unroll
-  for (int q = 0; q < kFinMaxPer; q++) {
-    const int k = k0 + q;
-    if (k < k1) {
-      const double e = p.self_consistent ? e_wall - p.ex_n * (run + 0.5 * nk[q]) : p.Ex_ext;
-      run += nk[q];
-      Ex[k] = e;
-      const double c = p.c1_per_ex * e;
-      c1[k] = c;
-      c1_32[k] = (float)c;
-      cmax = fmax(cmax, fabs(c));
-    }
+  for (int kk = t; kk < nx; kk += kFinThreads) {
+    const double below = boff[kk / kFinThreads] + __ldcg(fs.pre + kk);
+    const double n_k = __ldcg(ne + kk);
+    const double e = p.self_consistent ? e_wall - p.ex_n * (below + 0.5 * n_k) : p.Ex_ext;
+    Ex[kk] = e;
+    const double c = p.c1_per_ex * e;
+    c1[kk] = c;
+    c1_32[kk] = (float)c;
+    cmax = fmax(cmax, fabs(c));
   }
   cmax = block_max<kFinThreads>(cmax, sh);
   __syncthreads();
@@ -406,10 +413,14 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, do
 }
 
 cudaError_t launch_finalize(const StepArgs& a, double* ne, double* Ex, double* c1,
-                            float* c1_32, double* hist, int mode, cudaStream_t s) {
-  finalize_kernel<<<1, kFinThreads, 0, s>>>(a, ne, Ex, c1, c1_32, hist, mode);
+                            float* c1_32, double* hist, const FinScratch& fs, int mode,
+                            cudaStream_t s) {
+  const int nb = (a.nx + kFinThreads - 1) / kFinThreads;
+  finalize_kernel<<<nb, kFinThreads, 0, s>>>(a, ne, Ex, c1, c1_32, hist, fs, mode);
   return cudaGetLastError();
 }
+
+int finalize_blocks(int nx) { return (nx + kFinThreads - 1) / kFinThreads; }
 
 // ---------------------------------------------------------------------------
 // FP64 rows <-> FP32 rows with a row pitch (host arrays are dense FP64).

@@ -118,10 +118,46 @@ template <typename T>
 __host__ __device__ constexpr size_t stage_bytes(int stage_elems) {
   return ((size_t)stage_elems * sizeof(T) + 127) / 128 * 128;
 }
-// mbarriers full[kStages], empty[kStages]; warp sums [kStages][kWarps];
-// two control ints
+// mbarriers full[kStages], empty[kStages]; warp sums [kStages][kWarps][4]
+// (density, wall primary flux, wall secondary flux, vacuum outflow); two
+// control ints
+constexpr int kWs = 4;
 constexpr size_t kTailBytes =
-    2 * kStages * sizeof(uint64_t) + kStages * kWarps * sizeof(double) + 16;
+    2 * kStages * sizeof(uint64_t) + kStages * kWarps * kWs * sizeof(double) + 16;
+
+// Wall (x = 0, v1 < 0: Eqs. 12-14) or vacuum (x = h_max, v1 > 0) sums of
+// f^{n+1} over this consumer thread's cells of one plane, read back from
+// its own stores.  Called only on those two planes of a march, so the main
+// loop carries no FP64 instruction for them.
+template <typename T>
+__device__ __noinline__ void wall_terms(const T* oplane, const double* v1tab,
+                                        const double* delta, int tid, int i0, int rows,
+                                        int nv2, int pitch, bool wall, double* out3) {
+  constexpr int VEC = 16 / sizeof(T);
+  const int QV = pitch / VEC;
+  double pe = 0.0, see = 0.0, vac = 0.0;
+  for (int m = 0; m < kVecPerThread; m++) {
+    const int v = tid + kThreads * m;
+    if (v >= rows * QV) break;
+    const int r = v / QV, q = v - (v / QV) * QV;
+    const int i = i0 + r;
+    const double v1 = v1tab[i];
+    for (int e = 0; e < VEC && q * VEC + e < nv2; e++) {
+      const size_t c = (size_t)i * pitch + q * VEC + e;
+      const double fn = (double)oplane[c];
+      if (wall) {
+        const double g = -v1 * fn;  // Eq. 13 without dv1 dv2
+        pe += g;
+        see += delta[c] * g;  // Eq. 12
+      } else {
+        vac += v1 * fn;
+      }
+    }
+  }
+  out3[0] = pe;
+  out3[1] = see;
+  out3[2] = vac;
+}
 
 template <typename T, bool PADDED>
 __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
@@ -133,8 +169,8 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
   unsigned char* stage_base = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * sbytes);
   uint64_t* empty = full + kStages;
-  double* wsum = reinterpret_cast<double*>(empty + kStages);  // [kStages][kWarps]
-  int* ctl = reinterpret_cast<int*>(wsum + kStages * kWarps);
+  double* wsum = reinterpret_cast<double*>(empty + kStages);  // [kStages][kWarps][kWs]
+  int* ctl = reinterpret_cast<int*>(wsum + kStages * kWarps * kWs);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = gm.n_tiles;
@@ -226,42 +262,25 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
       if (a2 > 0.0)
         for (int r = lane; r < rows; r += 32)
           lv += a2 * (double)sb[(size_t)(r + 1) * pitch + nv2 - 1];
-      // wall fluxes of f^{n+1} (Eqs. 12-14) and vacuum outflow; the
-      // consumers' stores are visible after the acquire on empty
-      double pe = 0.0, see = 0.0, vac = 0.0;
-      const bool wall = k == 0 && dir < 0, vout = k == nx - 1 && dir > 0;
-      if (wall || vout) {
-        const T* orow = fout + (size_t)k * plane;
-        for (int c = lane; c < rows * nv2; c += 32) {
-          const int r = c / nv2, j = c - (c / nv2) * nv2;
-          const int i = i0 + r;
-          const double fn = (double)orow[(size_t)i * pitch + j];
-          const double v1 = a.tab.v1[i];
-          if (wall) {
-            const double g = -v1 * fn;  // Eq. 13 without dv1 dv2
-            pe += g;
-            see += a.tab.delta[(size_t)i * pitch + j] * g;  // Eq. 12
-          } else {
-            vac += v1 * fn;
-          }
-        }
-      }
       lv = warp_sum(lv);
-      if (wall || vout) {
-        pe = warp_sum(pe);
-        see = warp_sum(see);
-        vac = warp_sum(vac);
-      }
       if (lane == 0) {
-        double sn = 0.0;
-        for (int w = 0; w < kWarps; w++) sn += wsum[st * kWarps + w];  // fixed order
+        // fold the consumer warps' sums in a fixed order
+        double sn = 0.0, spe = 0.0, ssee = 0.0, svac = 0.0;
+        const double* ws = wsum + st * kWarps * kWs;
+        for (int w = 0; w < kWarps; w++) sn += ws[w * kWs + 0];
+        if (k == 0 || k == nx - 1)
+          for (int w = 0; w < kWarps; w++) {
+            spe += ws[w * kWs + 1];
+            ssee += ws[w * kWs + 2];
+            svac += ws[w * kWs + 3];
+          }
         a.part.n[(size_t)k * nt + t] = sn;
         a.part.lv[(size_t)k * nt + t] = lv;
         if (k == 0) {
-          a.part.pe[t] = pe;
-          a.part.see[t] = see;
+          a.part.pe[t] = spe;
+          a.part.see[t] = ssee;
         }
-        if (k == nx - 1) a.part.vac[t] = vac;
+        if (k == nx - 1) a.part.vac[t] = svac;
       }
     };
     int issued = 0;
@@ -405,7 +424,21 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
       // warp sum of this plane's f^{n+1} (an FP32 grid sums its 32 lanes in
       // FP32; everything above a warp is FP64)
       const T ws = warp_sum(sum_n);
-      if (lane == 0) wsum[st * kWarps + warp] = (double)ws;
+      double* wsl = wsum + (st * kWarps + warp) * kWs;
+      if (lane == 0) wsl[0] = (double)ws;
+      const bool wall = k == 0 && dir < 0, vout = k == nx - 1 && dir > 0;
+      if (wall || vout) {  // uniform over the block
+        double b3[3];
+        wall_terms<T>(oplane, a.tab.v1, a.tab.delta, tid, i0, rows, nv2, pitch, wall, b3);
+        const double w1 = warp_sum(b3[0]), w2 = warp_sum(b3[1]), w3 = warp_sum(b3[2]);
+        if (lane == 0) {
+          wsl[1] = w1;
+          wsl[2] = w2;
+          wsl[3] = w3;
+        }
+      } else if (k == 0 || k == nx - 1) {
+        if (lane == 0) wsl[1] = wsl[2] = wsl[3] = 0.0;
+      }
     }
     mbar_arrive(&empty[st]);  // this thread is done with stage st
   }
