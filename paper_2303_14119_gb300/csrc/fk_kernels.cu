@@ -291,10 +291,28 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, do
   // ---- phase A
   double nk = 0.0, lk = 0.0;
   if (k < nx) {
+    // loads batched ahead of the (fixed-order) adds: in-order issue would
+    // otherwise serialise one L2 round trip per partial
+    const double* pn = a.part.n + (size_t)k * nu;
+    const double* pl = a.part.lv + (size_t)k * nu;
     double sn = 0.0, sl = 0.0;
-    for (int u = 0; u < nu; u++) {
-      sn += a.part.n[(size_t)k * nu + u];
-      sl += a.part.lv[(size_t)k * nu + u];
+    int u = 0;
+    for (; u + 8 <= nu; u += 8) {
+      double xn[8], xl[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        xn[q] = pn[u + q];
+        xl[q] = pl[u + q];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        sn += xn[q];
+        sl += xl[q];
+      }
+    }
+    for (; u < nu; u++) {
+      sn += pn[u];
+      sl += pl[u];
     }
     nk = sn * p.dvv;
     lk = sl;
@@ -325,57 +343,81 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, do
   // ---- phase B (last block)
   __threadfence();
   const int nb = gridDim.x;
-  if (t == 0) {
-    *fs.counter = 0;  // ready for the next launch
-    // other blocks' results are read past L1 (__ldcg)
-    double ntot = 0.0, lvtot = 0.0;
-    for (int b = 0; b < nb; b++) {
-      boff[b] = ntot;
-      ntot += __ldcg(fs.bsum + b);
-      lvtot += __ldcg(fs.blv + b);
+  if (w == 0) {
+    // block totals and their exclusive prefix, wall-flux tile partials:
+    // lane-strided loads, fixed shuffle trees (other blocks' results are
+    // read past L1 with __ldcg)
+    const double b0 = lane < nb ? __ldcg(fs.bsum + lane) : 0.0;
+    const double b1 = lane + 32 < nb ? __ldcg(fs.bsum + lane + 32) : 0.0;
+    double l = (lane < nb ? __ldcg(fs.blv + lane) : 0.0) +
+               (lane + 32 < nb ? __ldcg(fs.blv + lane + 32) : 0.0);
+    double i0s = b0, i1s = b1;  // inclusive scans of the two halves
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y0 = __shfl_up_sync(0xffffffffu, i0s, o);
+      const double y1 = __shfl_up_sync(0xffffffffu, i1s, o);
+      if (lane >= o) {
+        i0s += y0;
+        i1s += y1;
+      }
     }
-    ntot *= p.dx;
+    const double half = __shfl_sync(0xffffffffu, i0s, 31);
+    if (lane < nb) boff[lane] = i0s - b0;
+    if (lane + 32 < nb) boff[lane + 32] = half + i1s - b1;
+    const double ntot_raw = half + __shfl_sync(0xffffffffu, i1s, 31);
     double pe = 0.0, see = 0.0, vac = 0.0;
-    for (int u = 0; u < nu; u++) {
+    for (int u = lane; u < nu; u += 32) {
       pe += a.part.pe[u];
       see += a.part.see[u];
       vac += a.part.vac[u];
     }
-    pe *= p.dvv;
-    see = p.see_enabled ? see * p.dvv : 0.0;  // with SEE off every primary is deposited
-    vac *= p.dvv;
-    if (mode == kModeStep) {
-      const double lv = lvtot * p.lv_scale;
-      st->cum_emit += p.dt * st->g_see;
-      st->cum_see += p.dt * st->g_see;
-      st->cum_pe += p.dt * st->g_pe;
-      st->cum_vac += p.dt * st->g_vac;
-      st->cum_lv += p.dt * lv;
-      st->cum_inj += p.dt * p.inj;
-      st->sigma += kQe * p.dt * (st->g_see - st->g_pe);
-      st->step += 1;
+    for (int o = 16; o > 0; o >>= 1) {
+      l += __shfl_down_sync(0xffffffffu, l, o);
+      pe += __shfl_down_sync(0xffffffffu, pe, o);
+      see += __shfl_down_sync(0xffffffffu, see, o);
+      vac += __shfl_down_sync(0xffffffffu, vac, o);
     }
-    if (mode == kModeReset) {
-      st->step = 0;
-      st->hist_count = 0;
-      st->sat_step = -1;
-      st->cum_emit = st->cum_see = st->cum_pe = st->cum_vac = st->cum_lv = st->cum_inj = 0.0;
-      st->sigma0 = st->sigma;
-      st->n0 = ntot;
+    if (lane == 0) {
+      *fs.counter = 0;  // ready for the next launch
+      DevState d = *st;  // one batch of loads, updated in registers
+      const double ntot = ntot_raw * p.dx;
+      pe *= p.dvv;
+      see = p.see_enabled ? see * p.dvv : 0.0;  // with SEE off every primary is deposited
+      vac *= p.dvv;
+      if (mode == kModeStep) {
+        const double lv = l * p.lv_scale;
+        d.cum_emit += p.dt * d.g_see;
+        d.cum_see += p.dt * d.g_see;
+        d.cum_pe += p.dt * d.g_pe;
+        d.cum_vac += p.dt * d.g_vac;
+        d.cum_lv += p.dt * lv;
+        d.cum_inj += p.dt * p.inj;
+        d.sigma += kQe * p.dt * (d.g_see - d.g_pe);
+        d.step += 1;
+      }
+      if (mode == kModeReset) {
+        d.step = 0;
+        d.hist_count = 0;
+        d.sat_step = -1;
+        d.cum_emit = d.cum_see = d.cum_pe = d.cum_vac = d.cum_lv = d.cum_inj = 0.0;
+        d.sigma0 = d.sigma;
+        d.n0 = ntot;
+      }
+      d.g_pe = pe;
+      d.g_see = see;
+      d.g_vac = vac;
+      d.n_tot = ntot;
+      if (!isfinite(pe) || !isfinite(see) || !isfinite(vac) || !isfinite(ntot) ||
+          !isfinite(d.sigma))
+        d.flags |= kFlagNumeric;
+      *st = d;  // one batch of stores
+      bc[0] = d.sigma;
     }
-    st->g_pe = pe;
-    st->g_see = see;
-    st->g_vac = vac;
-    st->n_tot = ntot;
-    if (!isfinite(pe) || !isfinite(see) || !isfinite(vac) || !isfinite(ntot) ||
-        !isfinite(st->sigma))
-      st->flags |= kFlagNumeric;
-    bc[0] = st->sigma;
   }
   __syncthreads();
   const double e_wall = bc[0] * p.ex_sigma;
   // E_x at cell centres and the v1-Courant numbers
   double cmax = 0.0;
+#pragma unroll 4
   for (int kk = t; kk < nx; kk += kFinThreads) {
     const double below = boff[kk / kFinThreads] + __ldcg(fs.pre + kk);
     const double n_k = __ldcg(ne + kk);
@@ -389,26 +431,25 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, do
   cmax = block_max<kFinThreads>(cmax, sh);
   __syncthreads();
   if (t == 0) {
-    if (cmax + p.cx_max + fabs(p.c2) > 1.0 + 1e-12) st->flags |= kFlagCfl;
-    const long long row = st->step;
+    DevState d = *st;
+    if (cmax + p.cx_max + fabs(p.c2) > 1.0 + 1e-12) d.flags |= kFlagCfl;
+    const long long row = d.step;
     const long long cap = p.hist_cap;
+    double rr[FK_HISTORY_COLS] = {(double)row, (double)row * p.dt, d.sigma, d.g_pe,
+                                  d.g_see, d.g_vac, d.n_tot, Ex[0]};
     double* r = hist + (size_t)(row % cap) * FK_HISTORY_COLS;
-    r[0] = (double)row;
-    r[1] = (double)row * p.dt;
-    r[2] = st->sigma;
-    r[3] = st->g_pe;
-    r[4] = st->g_see;
-    r[5] = st->g_vac;
-    r[6] = st->n_tot;
-    r[7] = Ex[0];
-    if (row + 1 > st->hist_count) st->hist_count = row + 1;
-    if (mode == kModeStep && st->sat_step < 0 && row >= p.sat_window && p.sat_window < cap) {
+    for (int q = 0; q < FK_HISTORY_COLS; q++) r[q] = rr[q];
+    if (row + 1 > d.hist_count) d.hist_count = row + 1;
+    if (mode == kModeStep && d.sat_step < 0 && row >= p.sat_window && p.sat_window < cap) {
       const double* o = hist + (size_t)((row - p.sat_window) % cap) * FK_HISTORY_COLS;
       bool ok = true;
       for (int q = 2; q <= 4; q++)
-        if (!(fabs(r[q] - o[q]) <= p.sat_tol * fabs(r[q]))) ok = false;
-      if (ok) st->sat_step = row;
+        if (!(fabs(rr[q] - o[q]) <= p.sat_tol * fabs(rr[q]))) ok = false;
+      if (ok) d.sat_step = row;
     }
+    st->flags = d.flags;
+    st->hist_count = d.hist_count;
+    st->sat_step = d.sat_step;
   }
 }
 
