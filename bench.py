@@ -63,6 +63,23 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_over_ranks(value, dist, op="max"):
+    """Max (time) or sum (throughput) of a per-rank float over the process
+    group; the value itself when there is no group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t[0])
+
+
+def job_throughput(world, n_inst, cells, steps, ms_max):
+    """Whole-job cell-updates/s: every rank advanced its own n_inst instances
+    by `steps` steps; the job took the slowest rank's time."""
+    return world * n_inst * cells * steps / (ms_max / 1e3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -261,6 +278,13 @@ def cpu_baseline(w, seconds=15.0):
                       % (n, *shape, w["Ey"])}
 
 
+# GB300 FP64 FMA peak derived from unit counts and clock: 152 SMs x 2 FP64
+# FMA per cycle x 2.07 GHz = 0.629 T FMA/s = 1.26 TFLOP/s (NVIDIA's figure is
+# 1.25 TFLOP/s; a register-resident FMA loop measured 0.596 T FMA/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 * 2 / 1e12
+DFMA_PER_CELL = 4  # the FP64 update is four fused multiply-adds per cell
+
+
 def roofline(res, precision, peak, peak_kind):
     bpc = 4 if precision == "f32" else 8
     if res["launches"] == 0:
@@ -268,11 +292,21 @@ def roofline(res, precision, peak, peak_kind):
     avg_s = res["kernel_ms"] / res["launches"] / 1e3
     alg_bytes = 2 * bpc * res["cells"]  # one read of f^n, one write of f^{n+1}
     achieved = alg_bytes / avg_s / 1e9
-    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": kernel_traffic(precision),
-            "peak_kind": "%s (copy bandwidth)" % peak_kind,
-            "kernel": "fused upwind step", "avg_launch_us": round(avg_s * 1e6, 2),
-            "alg_bytes_per_launch": alg_bytes}
+    hbm = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+           "frac": round(achieved / peak, 4), "traffic": kernel_traffic(precision),
+           "peak_kind": "%s (copy bandwidth)" % peak_kind,
+           "kernel": "fused upwind step", "avg_launch_us": round(avg_s * 1e6, 2),
+           "alg_bytes_per_launch": alg_bytes}
+    if precision == "f32":
+        return hbm
+    # FP64 on GB300 is bound by the FP64 pipe, not by HBM
+    tflops = 2 * DFMA_PER_CELL * res["cells"] / avg_s / 1e12
+    return {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+            "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+            "traffic": hbm["traffic"], "peak_kind": "derived (FP64 FMA units x clock)",
+            "kernel": "fused upwind step", "avg_launch_us": hbm["avg_launch_us"],
+            "alg_flops_per_launch": 2 * DFMA_PER_CELL * res["cells"],
+            "hbm": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")}}
 
 
 def run_ours(args):
@@ -296,13 +330,8 @@ def run_ours(args):
     res = time_arm(fk, torch, w, prec, f0, args.steps, args.warmup, dist, local)
     for g in res.pop("grids"):
         g.close()
-    ms = res["ms"]
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
-    total_updates = world * res["n_inst"] * res["cells"] * args.steps
-    value = total_updates / (ms / 1e3)
+    ms = reduce_over_ranks(res["ms"], dist, "max")
+    value = job_throughput(world, res["n_inst"], res["cells"], args.steps, ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -330,10 +359,7 @@ def run_ours(args):
             "roofline": roofline(r2, other, peak, peak_kind), "clocks": r2["clocks"]}}
     if not args.no_e2e:
         e2e = e2e_arm(fk, torch, w, prec, f0, args.e2e_steps)
-        if dist is not None:
-            t = torch.tensor([e2e["value"]], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.SUM)
-            e2e["value"] = float(t[0])
+        e2e["value"] = reduce_over_ranks(e2e["value"], dist, "sum")
         line["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w)

@@ -122,8 +122,41 @@ __host__ __device__ constexpr size_t stage_bytes(int stage_elems) {
 // (density, wall primary flux, wall secondary flux, vacuum outflow); two
 // control ints
 constexpr int kWs = 4;
-constexpr size_t kTailBytes =
-    2 * kStages * sizeof(uint64_t) + kStages * kWarps * kWs * sizeof(double) + 16;
+constexpr int kMaxTileRows = 64;  // also bounds the per-stage diagonal table
+// ... plus, for FP64 grids, the per-stage diagonal 1 - |c_x| - |c_1| - |c_2|
+// of every tile row [kStages][kMaxTileRows] double
+template <typename T>
+__host__ __device__ constexpr size_t tail_bytes() {
+  return 2 * kStages * sizeof(uint64_t) + kStages * kWarps * kWs * sizeof(double) +
+         (sizeof(T) == 8 ? kStages * kMaxTileRows * sizeof(double) : 0) + 16;
+}
+
+// Exact split of a double x >= 2^-126 into hi + lo floats: hi keeps the top
+// 24 significant bits (truncated), lo the remaining 29 rounded to 24 bits,
+// so hi + lo = x to about 2^-47 relative.  Integer and FP32 operations only:
+// none of this runs on GB300's narrow FP64 pipe.  Smaller magnitudes (and
+// zero) give 0 + 0, negligible in a sum of phase-space densities.
+__device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int h32 = (unsigned int)(b >> 32);
+  const int E = (int)((h32 >> 20) & 0x7FF);
+  const unsigned int sign = h32 & 0x80000000u;
+  const unsigned int m23 = (unsigned int)(b >> 29) & 0x7FFFFFu;
+  const bool ok = E >= 897 && E <= 1150;  // hi is a normal float
+  hi = __int_as_float(ok ? (sign | ((unsigned int)(E - 896) << 23) | m23) : 0u);
+  const unsigned int r29 = (unsigned int)b & 0x1FFFFFFFu;
+  // scale 2^(E-1075) as a float: exponent field E - 948 (0 below 2^-74)
+  const float scale = __int_as_float(E >= 949 ? ((unsigned int)(E - 948) << 23) : 0u);
+  const float l = __uint2float_rn(r29) * scale;
+  lo = ok ? (sign ? -l : l) : 0.f;
+}
+// s + c += x, exactly in s (TwoSum), the rounding error collected in c
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  c += (s - (t - bp)) + (x - bp);
+  s = t;
+}
 
 // Wall (x = 0, v1 < 0: Eqs. 12-14) or vacuum (x = h_max, v1 > 0) sums of
 // f^{n+1} over this consumer thread's cells of one plane, read back from
@@ -170,7 +203,8 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * sbytes);
   uint64_t* empty = full + kStages;
   double* wsum = reinterpret_cast<double*>(empty + kStages);  // [kStages][kWarps][kWs]
-  int* ctl = reinterpret_cast<int*>(wsum + kStages * kWarps * kWs);
+  double* dgl = wsum + kStages * kWarps * kWs;                 // [kStages][kMaxTileRows], FP64
+  int* ctl = reinterpret_cast<int*>(dgl + (sizeof(T) == 8 ? kStages * kMaxTileRows : 0));
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = gm.n_tiles;
@@ -230,6 +264,13 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
         float4* z = reinterpret_cast<float4*>(stage + (size_t)zrow * pitch);
         const int n16 = pitch * (int)sizeof(T) / 16;
         for (int c = lane; c < n16; c += 32) z[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      if (sizeof(T) == 8) {
+        // FP64 diagonal of the convex update per tile row, once per plane
+        // here rather than per vector in the consumers
+        const double a1 = c1 == 0.f ? 0.0 : fabs(a.c1[k]);
+        const double db = 1.0 - a1 - fabs(p.c2);
+        for (int r = lane; r < rows; r += 32) dgl[st * kMaxTileRows + r] = db - fabs(a.tab.cx[i0 + r]);
       }
       __syncwarp();
       if (lane == 0) {
@@ -327,7 +368,7 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
       const int r = v / QV, qv = v - r * QV;
       valid |= 1u << m;
       if (qv == 0) zleft |= 1u << m;
-      soff[m] = (r + 1) * pitch + qv * VEC;
+      soff[m] = ((r + 1) * pitch + qv * VEC) | (r << 24);  // row in the top byte
       const T cx = sizeof(T) == 8 ? (T)a.tab.cx[i0 + r] : (T)a.tab.cx32[i0 + r];
       ax[m] = cx < (T)0 ? -cx : cx;
     }
@@ -342,7 +383,8 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
     for (int m = 0; m < M; m++) {
       if (!(valid >> m & 1)) continue;
 #pragma unroll
-      for (int e = 0; e < VEC; e++) xr[m][e] = (T)(gsee * a.tab.gse[soff[m] + gbase + e]);
+      for (int e = 0; e < VEC; e++)
+        xr[m][e] = (T)(gsee * a.tab.gse[(soff[m] & 0xFFFFFF) + gbase + e]);
     }
   }
   const T c2 = (T)p.c2;
@@ -358,11 +400,14 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
     const float c1f = a.c1_32[k];
     const T a1 = c1f == 0.f ? (T)0 : (sizeof(T) == 8 ? (T)fabs(a.c1[k]) : (T)fabsf(c1f));
     const bool band = compute && k >= p.band_lo && k < p.band_hi;
-    Vec<T> srcv[M];
+    // FP32 grids prefetch the source rows; FP64 grids (bound by the FP64
+    // pipe, short of registers) load them in the update loop
+    constexpr int MS = sizeof(T) == 4 ? M : 1;
+    Vec<T> srcv[MS];
 #pragma unroll
-    for (int m = 0; m < M; m++) {
-      if (band && (valid >> m & 1)) {
-        srcv[m] = *reinterpret_cast<const Vec<T>*>(srcbase + soff[m] + gbase);
+    for (int m = 0; m < MS; m++) {
+      if (sizeof(T) == 4 && band && (valid >> m & 1)) {
+        srcv[m] = *reinterpret_cast<const Vec<T>*>(srcbase + (soff[m] & 0xFFFFFF) + gbase);
       } else {
 #pragma unroll
         for (int e = 0; e < VEC; e++) srcv[m].e[e] = (T)0;
@@ -378,7 +423,7 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
 #pragma unroll
       for (int m = 0; m < M; m++) {
         if (!(valid >> m & 1)) continue;
-        const Vec<T> own = *reinterpret_cast<const Vec<T>*>(sb + soff[m]);
+        const Vec<T> own = *reinterpret_cast<const Vec<T>*>(sb + (soff[m] & 0xFFFFFF));
 #pragma unroll
         for (int e = 0; e < VEC; e++) xr[m][e] = own.e[e];
       }
@@ -387,14 +432,16 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
       // the direction comes from the FP32 copy, as in the producer, so the
       // row read is always one that was copied or zero-filled
       const int nboff = c1f > 0.f ? -pitch : (c1f < 0.f ? pitch : 0);
-      const T dbase = (T)1 - a1 - a2;  // minus |c_x| per vector: the FP64 diagonal
+      const double* dg = dgl + st * kMaxTileRows;
       T sum_n = (T)0;
+      float sh_ = 0.f, sc_ = 0.f, sl_ = 0.f;  // FP64 grids: compensated FP32 sum
       T* oplane = fout + (size_t)k * plane;
 #pragma unroll
       for (int m = 0; m < M; m++) {
+        const int so = soff[m] & 0xFFFFFF;
         Vec<T> own;
         if (valid >> m & 1)
-          own = *reinterpret_cast<const Vec<T>*>(sb + soff[m]);
+          own = *reinterpret_cast<const Vec<T>*>(sb + so);
         else
 #pragma unroll
           for (int e = 0; e < VEC; e++) own.e[e] = (T)0;
@@ -404,28 +451,51 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
         if (zleft >> m & 1)
           left = (T)0;
         else if (lane == 0)
-          left = sb[soff[m] - 1];
-        const Vec<T> nb = *reinterpret_cast<const Vec<T>*>(sb + soff[m] + nboff);
-        const T d = dbase - ax[m];
+          left = sb[so - 1];
+        const Vec<T> nb = *reinterpret_cast<const Vec<T>*>(sb + so + nboff);
+        const T d = sizeof(T) == 8 ? (T)dg[soff[m] >> 24] : (T)0;  // unused on FP32 grids
+        Vec<T> src = srcv[sizeof(T) == 4 ? m : 0];
+        if (sizeof(T) == 8 && band)
+          src = *reinterpret_cast<const Vec<T>*>(srcbase + so + gbase);
         Vec<T> out;
 #pragma unroll
         for (int e = 0; e < VEC; e++) {
           const T f = own.e[e];
           const T fw = e == 0 ? left : own.e[e - 1];
-          T fn = upd<T>(f, xr[m][e], nb.e[e], fw, ax[m], a1, a2, srcv[m].e[e], d);
-          if (PADDED && (soff[m] % pitch) + e >= nv2) fn = (T)0;  // row padding stays zero
+          T fn = upd<T>(f, xr[m][e], nb.e[e], fw, ax[m], a1, a2, src.e[e], d);
+          if (PADDED && (so % pitch) + e >= nv2) fn = (T)0;  // row padding stays zero
           out.e[e] = fn;
           xr[m][e] = f;  // x-upwind value for the next plane is f^n here
-          sum_n += fn;
+          if (sizeof(T) == 4) {
+            sum_n += fn;
+          } else {
+            float h, l;
+            split_double((double)fn, h, l);
+            two_sum_acc(sh_, sc_, h);
+            sl_ += l;
+          }
         }
-        __stcs(reinterpret_cast<float4*>(oplane + soff[m] + gbase),
+        __stcs(reinterpret_cast<float4*>(oplane + so + gbase),
                *reinterpret_cast<const float4*>(&out));
       }
       // warp sum of this plane's f^{n+1} (an FP32 grid sums its 32 lanes in
       // FP32; everything above a warp is FP64)
-      const T ws = warp_sum(sum_n);
       double* wsl = wsum + (st * kWarps + warp) * kWs;
-      if (lane == 0) wsl[0] = (double)ws;
+      if (sizeof(T) == 4) {
+        const T ws = warp_sum(sum_n);
+        if (lane == 0) wsl[0] = (double)ws;
+      } else {
+        // fold the lanes' (hi, error) pairs in FP32 with TwoSum, convert once
+        float lo = sc_ + sl_;
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_down_sync(0xffffffffu, sh_, o);
+          const float ol = __shfl_down_sync(0xffffffffu, lo, o);
+          float c = 0.f;
+          two_sum_acc(sh_, c, oh);
+          lo += ol + c;
+        }
+        if (lane == 0) wsl[0] = (double)sh_ + (double)lo;
+      }
       const bool wall = k == 0 && dir < 0, vout = k == nx - 1 && dir > 0;
       if (wall || vout) {  // uniform over the block
         double b3[3];
@@ -452,8 +522,10 @@ int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per
   const int cells = kThreads * kVecPerThread * vec;
   if (pitch > cells) return 0;
   int rows = cells / pitch;
+  if (rows > kMaxTileRows) rows = kMaxTileRows;
   // two CTAs per SM: each holds kStages stages of (rows + 2) * pitch elements
-  const long budget = (long)smem_per_sm / 2 - reserved_per_block - (long)kTailBytes;
+  const long tail = (long)(precision == FK_F32 ? tail_bytes<float>() : tail_bytes<double>());
+  const long budget = (long)smem_per_sm / 2 - reserved_per_block - tail;
   const long stage = budget / kStages / 128 * 128;
   const long fit = stage / ((long)pitch * esize) - 2;
   if (fit < rows) rows = (int)fit;
@@ -461,9 +533,8 @@ int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per
 }
 
 size_t stream_smem_bytes(int precision, int stage_elems) {
-  const size_t sb = precision == FK_F32 ? stage_bytes<float>(stage_elems)
-                                        : stage_bytes<double>(stage_elems);
-  return kStages * sb + kTailBytes;
+  if (precision == FK_F32) return kStages * stage_bytes<float>(stage_elems) + tail_bytes<float>();
+  return kStages * stage_bytes<double>(stage_elems) + tail_bytes<double>();
 }
 
 int stream_ctas_per_sm(int precision, size_t smem_bytes) {

@@ -1,0 +1,55 @@
+"""The multi-rank host logic of bench.py on CPU: two gloo ranks, each with its
+own independent instances (replicas), reduce the time by max and the
+end-to-end throughput by sum.  No GPU is used."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, lr = bench.dist_env()
+    ms_local = 10.0 + 5.0 * rank  # rank 1 is the slow one
+    ms = bench.reduce_over_ranks(ms_local, dist, "max")
+    e2e = bench.reduce_over_ranks(100.0 * (rank + 1), dist, "sum")
+    value = bench.job_throughput(w, 3, 1000, 20, ms)
+    q.put((r, w, lr, ms, e2e, value))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_like_the_bench():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r, (rank, w, lr, ms, e2e, value) in enumerate(out):
+        assert (rank, w, lr) == (r, 2, r)
+        assert ms == 15.0  # max over ranks
+        assert e2e == 300.0  # sum over ranks
+        assert value == pytest.approx(2 * 3 * 1000 * 20 / 0.015)
+
+
+def test_single_process_defaults():
+    import bench
+    assert bench.reduce_over_ranks(7.0, None) == 7.0
+    assert bench.job_throughput(1, 3, 10, 2, 1000.0) == pytest.approx(60.0)
