@@ -339,3 +339,46 @@ def test_full_size_fp32_against_fp64_gpu():
         g.close()
     assert rel_l1(res[1][0], res[0][0]) <= 1e-5
     assert rel(res[1][2]["N"], res[0][2]["N"]) <= 1e-5
+
+
+# ----------------------------------------------------------------- 2048 x 384 x 384
+def test_large_fp32_against_fp64_gpu():
+    """Mixed-precision workload 2048 x 384 x 384 (302 M cells), E_y = -2e6 V/m:
+    FP32 f with FP64 accumulators against the FP64 path, 1000 steps, both on
+    the GPU from the same f0."""
+    w = synth.WORKLOADS["large_2048x384x384"]
+    shape = (w["nx"], w["nv1"], w["nv2"])
+    f0 = synth.initial_f(shape, w["seed"], w["noise_rel"], w["J"], w["T_fe"])
+    res = []
+    for prec in (fk.FK_F64, fk.FK_F32):
+        g = fk.Grid(*shape, w["h_max"], -w["v1_span"], w["v1_span"], -w["v2_span"],
+                    w["v2_span"], cfl=w["cfl"], precision=prec)
+        g.set_fields(w["Ey"])
+        g.set_see(w["delta_max"], w["A_max"], w["k_s"], w["T_se"])
+        g.set_source(w["J"], w["x_lo"], w["x_hi"], w["T_fe"])
+        g.set_f(f0)
+        g.step(1000)
+        res.append((g.get_f(), g.surface_charge(), g.history(1001)))
+        g.close()
+    assert rel_l1(res[1][0], res[0][0]) <= 1e-5
+    assert rel(res[1][1], res[0][1]) <= 1e-4
+    h64, h32 = res[0][2], res[1][2]
+    for c in (3, 4, 6):  # Gamma_pe, Gamma_see, N histories
+        assert np.abs(h32[:, c] - h64[:, c]).max() <= 1e-4 * np.abs(h64[:, c]).max()
+
+
+def test_coarse_copy_fp32_against_oracle():
+    """The 4x-coarsened copy of the mixed-precision workload, 512 x 96 x 96,
+    FP32 path against the FP64 oracle for 100 steps."""
+    w = synth.WORKLOADS["coarse_512x96x96"]
+    shape = (w["nx"], w["nv1"], w["nv2"])
+    g, o = make_pair(shape, prec=fk.FK_F32, cfl=w["cfl"])
+    workload_physics(g, o, w)
+    f0 = synth.initial_f(shape, w["seed"], w["noise_rel"], w["J"], w["T_fe"])
+    g.set_f(f0)
+    o.set_state(f0, 0.0)
+    g.step(100)
+    o.step(100)
+    assert rel_l1(g.get_f(), o.get_f()) <= 1e-5
+    assert rel(g.surface_charge(), o.surface_charge()) <= 1e-4
+    g.close()
