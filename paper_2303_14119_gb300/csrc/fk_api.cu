@@ -197,7 +197,8 @@ void free_grid(fk_grid* g) {
     if (g->graph[p]) cudaGraphExecDestroy(g->graph[p]);
   void* ptrs[] = {g->d_prm, g->d_st, g->d_f[0], g->d_f[1], g->tab.v1, g->tab.cx,
                   g->tab.cx32, g->tab.delta, g->tab.gse, g->tab.src, g->tab.src32,
-                  g->tab.gfe_raw, g->part.n, g->part.lv, g->part.pe, g->part.see,
+                  g->tab.gfe_raw, g->tab.srow32, g->tab.scol32, g->part.n, g->part.lv,
+                  g->part.pe, g->part.see,
                   g->part.vac, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist,
                   g->d_stage, g->fin.pre, g->fin.bsum, g->fin.blv, g->fin.counter};
   for (void* p : ptrs)
@@ -265,11 +266,12 @@ fk_status plan_geometry(fk_grid* g) {
   split(i_neg, &m.t_neg, &m.ti_neg);
   split(g->nv1 - i_neg, &t_pos, &m.ti_pos);
   m.n_tiles = m.t_neg + t_pos;
-  m.stage_elems = (std::max(m.ti_neg, m.ti_pos) + 2) * g->pitch;
+  m.stage_elems = (std::max(m.ti_neg, m.ti_pos) + (g->use_stream ? 1 : 2)) * g->pitch;
   m.n_chunks = 1;
   m.chunk_len = g->nx;
   if (g->use_stream) {
-    const int per_sm = stream_ctas_per_sm(g->prec, stream_smem_bytes(g->prec, m.stage_elems));
+    const int per_sm =
+        stream_ctas_per_sm(g->prec, stream_smem_bytes(g->prec, m.stage_elems, g->pitch));
     if (per_sm <= 0) {
       g->use_stream = false;
     } else {
@@ -397,6 +399,8 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   CREATE_CUDA(dalloc(&g->tab.src, nv * sizeof(double)));
   CREATE_CUDA(dalloc(&g->tab.src32, nv * sizeof(float)));
   CREATE_CUDA(dalloc(&g->tab.gfe_raw, nv * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->tab.srow32, d.nv1 * sizeof(float)));
+  CREATE_CUDA(dalloc(&g->tab.scol32, g->pitch * sizeof(float)));
   CREATE_CUDA(dalloc(&g->part.n, nparts * sizeof(double)));
   CREATE_CUDA(dalloc(&g->part.lv, nparts * sizeof(double)));
   CREATE_CUDA(dalloc(&g->part.pe, g->part.nu * sizeof(double)));

@@ -77,6 +77,10 @@ struct Tables {
   double* src;    // [nv1][pitch] dt (J/e)/W g_fe, added on source planes
   float* src32;   // same rounded to FP32
   double* gfe_raw;// [nv1][pitch] scratch for the source shape
+  // the source shape is separable (Maxwellian in v1 times half-Maxwellian
+  // in v2, normalised per factor): src(i, j) = srow32[i] * scol32[j]
+  float* srow32;  // [nv1] dt (J/e)/W times the normalised v1 factor
+  float* scol32;  // [pitch] normalised v2 factor, zero for v2 <= 0 and padding
 };
 
 // Work decomposition shared by the step kernels and the finalize kernel.
@@ -135,7 +139,7 @@ cudaError_t launch_step_stream(const StepArgs& a, int precision, cudaStream_t s)
 // so that two CTAs fit on an SM (0 if a row does not fit), its shared
 // memory per CTA, resident CTAs per SM.
 int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per_block);
-size_t stream_smem_bytes(int precision, int stage_elems);
+size_t stream_smem_bytes(int precision, int stage_elems, int pitch);
 int stream_ctas_per_sm(int precision, size_t smem_bytes);
 // Scratch of the finalize kernel: per-plane in-block prefix of n, per-block
 // sums, and the counter that elects the last block (zero between launches).

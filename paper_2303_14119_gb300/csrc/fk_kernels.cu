@@ -107,6 +107,38 @@ tables_kernel(Tables t, int nv1, int nv2, int pitch, double v1_min, double v2_mi
     t.cx[i] = __ddiv_rn(__dmul_rn(v1, dt), dx);
     t.cx32[i] = (float)t.cx[i];
   }
+  // separable factors of the source shape (FP32 step kernel)
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < nv1; i += blockDim.x) {
+    const double v1 = cell_centre(v1_min, i, dv1);
+    s1 += exp(-kMe * v1 * v1 / (2.0 * Tfe * kQe));
+  }
+  for (int j = threadIdx.x; j < nv2; j += blockDim.x) {
+    const double v2 = cell_centre(v2_min, j, dv2);
+    s2 += v2 > 0.0 ? exp(-kMe * v2 * v2 / (2.0 * Tfe * kQe)) : 0.0;
+  }
+  s1 = block_sum<kTabThreads>(s1, sh);
+  s2 = block_sum<kTabThreads>(s2, sh);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    norms[0] = s1 * dv1;
+    norms[1] = s2 * dv2;
+  }
+  __syncthreads();
+  const double n1 = norms[0], n2 = norms[1];
+  const bool on = nfe > 0.0 && n1 > 0.0 && n2 > 0.0;
+  for (int i = threadIdx.x; i < nv1; i += blockDim.x) {
+    const double v1 = cell_centre(v1_min, i, dv1);
+    t.srow32[i] = on ? (float)(dt * j_over_ew * exp(-kMe * v1 * v1 / (2.0 * Tfe * kQe)) / n1) : 0.f;
+  }
+  for (int j = threadIdx.x; j < pitch; j += blockDim.x) {
+    double g = 0.0;
+    if (on && j < nv2) {
+      const double v2 = cell_centre(v2_min, j, dv2);
+      g = v2 > 0.0 ? exp(-kMe * v2 * v2 / (2.0 * Tfe * kQe)) / n2 : 0.0;
+    }
+    t.scol32[j] = (float)g;
+  }
 }
 
 cudaError_t launch_tables(const Tables& t, int nv1, int nv2, int pitch, double v1_min,

@@ -125,10 +125,14 @@ constexpr int kWs = 4;
 constexpr int kMaxTileRows = 64;  // also bounds the per-stage diagonal table
 // ... plus, for FP64 grids, the per-stage diagonal 1 - |c_x| - |c_1| - |c_2|
 // of every tile row [kStages][kMaxTileRows] double
+// ... plus, for FP32 grids, the separable source factors of the tile rows
+// [kMaxTileRows] and of the row cells [pitch] (float)
 template <typename T>
-__host__ __device__ constexpr size_t tail_bytes() {
+__host__ __device__ constexpr size_t tail_bytes(int pitch) {
   return 2 * kStages * sizeof(uint64_t) + kStages * kWarps * kWs * sizeof(double) +
-         (sizeof(T) == 8 ? kStages * kMaxTileRows * sizeof(double) : 0) + 16;
+         (sizeof(T) == 8 ? kStages * kMaxTileRows * sizeof(double)
+                         : ((size_t)(kMaxTileRows + pitch) * sizeof(float) + 15) / 16 * 16) +
+         16;
 }
 
 // Exact split of a double x >= 2^-126 into hi + lo floats: hi keeps the top
@@ -204,7 +208,12 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
   uint64_t* empty = full + kStages;
   double* wsum = reinterpret_cast<double*>(empty + kStages);  // [kStages][kWarps][kWs]
   double* dgl = wsum + kStages * kWarps * kWs;                 // [kStages][kMaxTileRows], FP64
-  int* ctl = reinterpret_cast<int*>(dgl + (sizeof(T) == 8 ? kStages * kMaxTileRows : 0));
+  float* srow_s = reinterpret_cast<float*>(dgl);               // [kMaxTileRows], FP32
+  float* scol_s = srow_s + kMaxTileRows;                       // [pitch], FP32
+  int* ctl = reinterpret_cast<int*>(
+      reinterpret_cast<unsigned char*>(dgl) +
+      (sizeof(T) == 8 ? kStages * kMaxTileRows * sizeof(double)
+                      : ((size_t)(kMaxTileRows + a.pitch) * sizeof(float) + 15) / 16 * 16));
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = gm.n_tiles;
@@ -228,6 +237,10 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
     return dir > 0 ? s : nx - 1 - s;
   };
 
+  if (sizeof(T) == 4) {  // source factors of this tile (FP32 grids)
+    for (int r = tid; r < i1 - i0; r += blockDim.x) srow_s[r] = a.tab.srow32[i0 + r];
+    for (int j = tid; j < pitch; j += blockDim.x) scol_s[j] = a.tab.scol32[j];
+  }
   if (tid == 0) {
     ctl[0] = (int)a.st->flags;
     for (int s = 0; s < kStages; s++) {
@@ -257,9 +270,11 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
       const float c1 = a.c1_32[k];
       const int st = q % kStages;
       T* stage = reinterpret_cast<T*>(stage_base + st * sbytes);
+      // stage layout: the tile's rows start at row 1 when the halo lies
+      // above (c_1 > 0), at row 0 otherwise (halo, if any, at row `rows`)
       int zrow = -1;
       if (c1 > 0.f && i0 == 0) zrow = 0;
-      if (c1 < 0.f && i1 == nv1) zrow = rows + 1;
+      if (c1 < 0.f && i1 == nv1) zrow = rows;
       if (zrow >= 0) {
         float4* z = reinterpret_cast<float4*>(stage + (size_t)zrow * pitch);
         const int n16 = pitch * (int)sizeof(T) / 16;
@@ -277,7 +292,7 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
         int lo = i0, hi = i1;
         if (c1 > 0.f && i0 > 0) lo = i0 - 1;  // v1 halo row on the upwind side
         if (c1 < 0.f && i1 < nv1) hi = i1 + 1;
-        T* dst = stage + (size_t)(lo - (i0 - 1)) * pitch;
+        T* dst = stage + (size_t)(lo - i0 + (c1 > 0.f ? 1 : 0)) * pitch;
         const T* src = fin + (size_t)k * plane + (size_t)lo * pitch;
         const uint32_t bytes = (uint32_t)((hi - lo) * pitch * sizeof(T));
         mbar_expect_tx(&full[st], bytes);  // release: the zero row is visible too
@@ -293,17 +308,20 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
       const float c1f = a.c1_32[k];
       const double a1 = c1f == 0.f ? 0.0 : fabs(a.c1[k]);
       const double a2 = fabs(p.c2);
-      // ledger: outflow of f^n through the downwind velocity edges
-      double lv = 0.0;
+      // ledger: outflow of f^n through the downwind velocity edges, summed
+      // in the grid's precision per lane (a ledger diagnostic: FP32 grids
+      // keep FP64 instructions off this per-plane path), FP64 across lanes
+      T lvt = (T)0;
+      const T a1t = (T)a1, a2t = (T)a2;
       const int erow = (c1f > 0.f && i1 == nv1) ? nv1 - 1 : ((c1f < 0.f && i0 == 0) ? 0 : -1);
+      const int rb = c1f > 0.f ? 1 : 0;  // stage row of the tile's first row
       if (erow >= 0) {
-        const T* r = sb + (size_t)(erow - i0 + 1) * pitch;
-        for (int j = lane; j < nv2; j += 32) lv += a1 * (double)r[j];
+        const T* r = sb + (size_t)(erow - i0 + rb) * pitch;
+        for (int j = lane; j < nv2; j += 32) lvt += a1t * r[j];
       }
       if (a2 > 0.0)
-        for (int r = lane; r < rows; r += 32)
-          lv += a2 * (double)sb[(size_t)(r + 1) * pitch + nv2 - 1];
-      lv = warp_sum(lv);
+        for (int r = lane; r < rows; r += 32) lvt += a2t * sb[(size_t)(r + rb) * pitch + nv2 - 1];
+      const double lv = warp_sum((double)lvt);
       if (lane == 0) {
         // fold the consumer warps' sums in a fixed order
         double sn = 0.0, spe = 0.0, ssee = 0.0, svac = 0.0;
@@ -354,8 +372,8 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
   // ============================ consumer warps =============================
   // this thread's cells: vectors v = tid + kThreads*m of the tile, fixed for
   // the whole march; per vector its offset in a stage and in a plane
-  int soff[M];  // global offset in a plane = soff + gbase
-  const int gbase = (i0 - 1) * pitch;
+  int soff[M];  // offset from the tile's first cell (low 24 bits) and row (top byte)
+  const int gbase = i0 * pitch;  // the tile's first cell in a plane
   unsigned valid = 0, zleft = 0;  // bit m: vector m exists / starts a row
   T ax[M];
   T xr[M][VEC];
@@ -368,7 +386,7 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
       const int r = v / QV, qv = v - r * QV;
       valid |= 1u << m;
       if (qv == 0) zleft |= 1u << m;
-      soff[m] = ((r + 1) * pitch + qv * VEC) | (r << 24);  // row in the top byte
+      soff[m] = (r * pitch + qv * VEC) | (r << 24);
       const T cx = sizeof(T) == 8 ? (T)a.tab.cx[i0 + r] : (T)a.tab.cx32[i0 + r];
       ax[m] = cx < (T)0 ? -cx : cx;
     }
@@ -400,25 +418,16 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
     const float c1f = a.c1_32[k];
     const T a1 = c1f == 0.f ? (T)0 : (sizeof(T) == 8 ? (T)fabs(a.c1[k]) : (T)fabsf(c1f));
     const bool band = compute && k >= p.band_lo && k < p.band_hi;
-    // FP32 grids prefetch the source rows; FP64 grids (bound by the FP64
-    // pipe, short of registers) load them in the update loop
-    constexpr int MS = sizeof(T) == 4 ? M : 1;
-    Vec<T> srcv[MS];
-#pragma unroll
-    for (int m = 0; m < MS; m++) {
-      if (sizeof(T) == 4 && band && (valid >> m & 1)) {
-        srcv[m] = *reinterpret_cast<const Vec<T>*>(srcbase + (soff[m] & 0xFFFFFF) + gbase);
-      } else {
-#pragma unroll
-        for (int e = 0; e < VEC; e++) srcv[m].e[e] = (T)0;
-      }
-    }
+    // source term: FP32 grids rebuild it from the separable factors in
+    // shared memory, FP64 grids load the 2D table in the update loop
     const bool ok = mbar_wait(&full[st], (uint32_t)((q / kStages) & 1));
     if (__any_sync(0xffffffffu, !ok)) {
       if (lane == 0) atomicOr(&a.st->flags, kFlagTimeout);
       return;
     }
-    const T* sb = reinterpret_cast<const T*>(stage_base + st * sbytes);
+    // the tile's first row sits at stage row 1 when this plane's halo lies
+    // above (c_1 > 0), at row 0 otherwise
+    const T* sb = reinterpret_cast<const T*>(stage_base + st * sbytes) + (c1f > 0.f ? pitch : 0);
     if (!compute) {
 #pragma unroll
       for (int m = 0; m < M; m++) {
@@ -454,9 +463,21 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
           left = sb[so - 1];
         const Vec<T> nb = *reinterpret_cast<const Vec<T>*>(sb + so + nboff);
         const T d = sizeof(T) == 8 ? (T)dg[soff[m] >> 24] : (T)0;  // unused on FP32 grids
-        Vec<T> src = srcv[sizeof(T) == 4 ? m : 0];
-        if (sizeof(T) == 8 && band)
-          src = *reinterpret_cast<const Vec<T>*>(srcbase + so + gbase);
+        Vec<T> src;
+#pragma unroll
+        for (int e = 0; e < VEC; e++) src.e[e] = (T)0;
+        if (band) {
+          if constexpr (sizeof(T) == 4) {
+            const int r = soff[m] >> 24;
+            const float sr = srow_s[r];
+            const Vec<float> sc =
+                *reinterpret_cast<const Vec<float>*>(scol_s + (so - r * pitch));
+#pragma unroll
+            for (int e = 0; e < VEC; e++) src.e[e] = sr * sc.e[e];
+          } else {
+            src = *reinterpret_cast<const Vec<T>*>(srcbase + so + gbase);
+          }
+        }
         Vec<T> out;
 #pragma unroll
         for (int e = 0; e < VEC; e++) {
@@ -523,18 +544,20 @@ int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per
   if (pitch > cells) return 0;
   int rows = cells / pitch;
   if (rows > kMaxTileRows) rows = kMaxTileRows;
-  // two CTAs per SM: each holds kStages stages of (rows + 2) * pitch elements
-  const long tail = (long)(precision == FK_F32 ? tail_bytes<float>() : tail_bytes<double>());
+  // two CTAs per SM: each holds kStages stages of (rows + 1) * pitch elements
+  const long tail =
+      (long)(precision == FK_F32 ? tail_bytes<float>(pitch) : tail_bytes<double>(pitch));
   const long budget = (long)smem_per_sm / 2 - reserved_per_block - tail;
   const long stage = budget / kStages / 128 * 128;
-  const long fit = stage / ((long)pitch * esize) - 2;
+  const long fit = stage / ((long)pitch * esize) - 1;  // one halo slot per stage
   if (fit < rows) rows = (int)fit;
   return rows > 0 ? rows : 0;
 }
 
-size_t stream_smem_bytes(int precision, int stage_elems) {
-  if (precision == FK_F32) return kStages * stage_bytes<float>(stage_elems) + tail_bytes<float>();
-  return kStages * stage_bytes<double>(stage_elems) + tail_bytes<double>();
+size_t stream_smem_bytes(int precision, int stage_elems, int pitch) {
+  if (precision == FK_F32)
+    return kStages * stage_bytes<float>(stage_elems) + tail_bytes<float>(pitch);
+  return kStages * stage_bytes<double>(stage_elems) + tail_bytes<double>(pitch);
 }
 
 int stream_ctas_per_sm(int precision, size_t smem_bytes) {
@@ -567,7 +590,7 @@ int stream_ctas_per_sm(int precision, size_t smem_bytes) {
 
 cudaError_t launch_step_stream(const StepArgs& a, int precision, cudaStream_t s) {
   const int grid = a.geom.n_tiles * a.geom.n_chunks;
-  const size_t smem = stream_smem_bytes(precision, a.geom.stage_elems);
+  const size_t smem = stream_smem_bytes(precision, a.geom.stage_elems, a.pitch);
   const bool padded = a.pitch != a.nv2;
   if (precision == FK_F32) {
     if (padded)
