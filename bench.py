@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--no-batch", action="store_true",
+                    help="step each instance alone instead of as one batch")
     return ap.parse_args()
 
 
@@ -171,7 +173,11 @@ def make_grids(fk, w, precision, stream):
     return grids
 
 
-def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device):
+def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=True):
+    """Time `steps` steps of the workload's instances after `warmup` steps.
+    batch: the instances step together (one step-kernel launch and one
+    finalize launch per step for all of them, x-chunks autotuned during the
+    warm-up); else each instance is stepped alone."""
     # every grid runs on torch's current stream (a created stream, not the
     # legacy default), so the events below bracket exactly the grids' work
     stream = torch.cuda.current_stream().cuda_stream
@@ -179,12 +185,21 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device):
     grids = make_grids(fk, w, precision, stream)
     for g in grids:
         g.set_f(f0)
+    b = fk.Batch(grids, stream) if batch else None
+    tuned = b.autotune(2) if b is not None else 0
     for _ in range(warmup):
+        if b is not None:
+            b.step(1)
+        else:
+            for g in grids:
+                g.step(1)
+    if b is not None:
+        assert b.sync() == [fk.FK_OK] * len(grids)
+        b.set_kernel_timing(True)
+    else:
         for g in grids:
-            g.step(1)
-    for g in grids:
-        g.sync()
-        g.set_kernel_timing(True)
+            g.sync()
+            g.set_kernel_timing(True)
     clocks = ClockSampler(device)
     clocks.start()
     if dist is not None:
@@ -194,33 +209,52 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(steps):
-        for g in grids:
-            g.step(1)
+        if b is not None:
+            b.step(1)
+        else:
+            for g in grids:
+                g.step(1)
     e1.record()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     ms = e0.elapsed_time(e1)
     ck = clocks.stop()
-    launches, kms = 0, 0.0
-    for g in grids:
-        n, t = g.kernel_timing()
-        launches += n
-        kms += t
-        g.set_kernel_timing(False)
-        g.sync()
     cells = w["nx"] * w["nv1"] * w["nv2"]
-    info = grids[0].info()
-    res = dict(ms=ms, launches=launches, kernel_ms=kms, cells=cells, n_inst=len(grids),
-               clocks=ck, grids=grids,
-               kernel={k: info[k] for k in ("kernel", "n_tiles", "n_chunks", "chunk_len")})
-    return res
+    if b is not None:
+        launches, kms = b.kernel_timing()
+        b.set_kernel_timing(False)
+        assert b.sync() == [fk.FK_OK] * len(grids)
+        info = b.info()
+        plan = dict(mode="batch", units=info["units"], smem_bytes=info["smem_bytes"],
+                    ctas_per_sm=info["ctas_per_sm"], chunk_len=b.chunks(),
+                    n_tiles=grids[0].info()["n_tiles"], autotune_steps=tuned)
+        cells_per_launch = cells * len(grids)
+        gpu_launches = 2 * steps
+        b.close()
+    else:
+        launches, kms = 0, 0.0
+        for g in grids:
+            n, t = g.kernel_timing()
+            launches += n
+            kms += t
+            g.set_kernel_timing(False)
+            g.sync()
+        info = grids[0].info()
+        plan = dict(mode="per-instance",
+                    **{k: info[k] for k in ("kernel", "n_tiles", "n_chunks", "chunk_len")})
+        cells_per_launch = cells
+        gpu_launches = 2 * steps * len(grids)
+    return dict(ms=ms, launches=launches, kernel_ms=kms, cells=cells, n_inst=len(grids),
+                cells_per_launch=cells_per_launch, gpu_launches=gpu_launches, clocks=ck,
+                grids=grids, kernel=plan)
 
 
-def e2e_arm(fk, torch, w, precision, f0_pinned, steps):
+def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True):
     """The user's loop through the C ABI with host buffers: upload f0 from
-    pinned host memory, then per step advance and read sigma and the wall
-    fluxes back, finally read f back; all inside the timed region."""
+    pinned host memory, then per step advance (the instances as one batch,
+    or each alone) and read sigma and the wall fluxes back, finally read f
+    back; all inside the timed region."""
     stream = torch.cuda.current_stream().cuda_stream
     assert stream, "e2e_arm needs a non-default current stream"
     grids = make_grids(fk, w, precision, stream)
@@ -232,15 +266,21 @@ def e2e_arm(fk, torch, w, precision, f0_pinned, steps):
     t0 = time.perf_counter()
     for g in grids:
         g.set_f(f0_pinned)
+    b = fk.Batch(grids, stream) if batch else None
     for _ in range(steps):
+        if b is not None:
+            b.step(1)
         for g in grids:
-            g.step(1)
+            if b is None:
+                g.step(1)
             fk.fk_moments(g.h, nx, ne, ex)
             g.surface_charge()
     for g in grids:
         g.get_f(out_f)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    if b is not None:
+        b.close()
     for g in grids:
         g.close()
     cells = w["nx"] * w["nv1"] * w["nv2"]
@@ -290,7 +330,7 @@ def roofline(res, precision, peak, peak_kind):
     if res["launches"] == 0:
         return None
     avg_s = res["kernel_ms"] / res["launches"] / 1e3
-    alg_bytes = 2 * bpc * res["cells"]  # one read of f^n, one write of f^{n+1}
+    alg_bytes = 2 * bpc * res["cells_per_launch"]  # one read of f^n, one write of f^{n+1}
     achieved = alg_bytes / avg_s / 1e9
     hbm = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
            "frac": round(achieved / peak, 4), "traffic": kernel_traffic(precision),
@@ -300,12 +340,12 @@ def roofline(res, precision, peak, peak_kind):
     if precision == "f32":
         return hbm
     # FP64 on GB300 is bound by the FP64 pipe, not by HBM
-    tflops = 2 * DFMA_PER_CELL * res["cells"] / avg_s / 1e12
+    tflops = 2 * DFMA_PER_CELL * res["cells_per_launch"] / avg_s / 1e12
     return {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
             "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
             "traffic": hbm["traffic"], "peak_kind": "derived (FP64 FMA units x clock)",
             "kernel": "fused upwind step", "avg_launch_us": hbm["avg_launch_us"],
-            "alg_flops_per_launch": 2 * DFMA_PER_CELL * res["cells"],
+            "alg_flops_per_launch": 2 * DFMA_PER_CELL * res["cells_per_launch"],
             "hbm": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")}}
 
 
@@ -327,7 +367,8 @@ def run_ours(args):
     f0[...] = synth.initial_f(shape, w["seed"], w["noise_rel"], w["J"], w["T_fe"])
     peak, peak_kind = measured_peaks()
     prec = fk.FK_F32 if args.precision == "f32" else fk.FK_F64
-    res = time_arm(fk, torch, w, prec, f0, args.steps, args.warmup, dist, local)
+    res = time_arm(fk, torch, w, prec, f0, args.steps, args.warmup, dist, local,
+                   batch=not args.no_batch)
     for g in res.pop("grids"):
         g.close()
     ms = reduce_over_ranks(res["ms"], dist, "max")
@@ -343,14 +384,15 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline(res, args.precision, peak, peak_kind),
         "kernel_plan": res["kernel"],
-        "gpu_launches": args.steps * res["n_inst"] * 2,
+        "gpu_launches": res["gpu_launches"],
         "clocks": res["clocks"],
     }
     if not args.no_side:
         other = "f64" if args.precision == "f32" else "f32"
         oprec = fk.FK_F64 if other == "f64" else fk.FK_F32
         osteps = max(1, args.steps // (2 if other == "f64" else 1))
-        r2 = time_arm(fk, torch, w, oprec, f0, osteps, args.warmup, dist, local)
+        r2 = time_arm(fk, torch, w, oprec, f0, osteps, args.warmup, dist, local,
+                      batch=not args.no_batch)
         for g in r2.pop("grids"):
             g.close()
         line["side_by_side"] = {other: {
@@ -358,11 +400,151 @@ def run_ours(args):
             "ms_per_step": r2["ms"] / osteps, "steps": osteps,
             "roofline": roofline(r2, other, peak, peak_kind), "clocks": r2["clocks"]}}
     if not args.no_e2e:
-        e2e = e2e_arm(fk, torch, w, prec, f0, args.e2e_steps)
+        e2e = e2e_arm(fk, torch, w, prec, f0, args.e2e_steps, batch=not args.no_batch)
         e2e["value"] = reduce_over_ranks(e2e["value"], dist, "sum")
         line["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def make_sweep_grids(fk, instances, precision, stream):
+    """One grid per sweep instance, f0 = 0 and sigma = 0 (the run starts
+    from an uncharged, empty gap)."""
+    grids = []
+    for p in instances:
+        g = fk.Grid(p["nx"], p["nv1"], p["nv2"], p["h_max"], -p["v1_span"], p["v1_span"],
+                    -p["v2_span"], p["v2_span"], cfl=p["cfl"], precision=precision,
+                    stream=stream)
+        g.set_fields(p["Ey"])
+        g.set_see(p["delta_max"], p["A_max"], p["k_s"], p["T_se"])
+        g.set_source(p["J"], p["x_lo"], p["x_hi"], p["T_fe"])
+        grids.append(g)
+    return grids
+
+
+def run_sweep(args):
+    """Parameter sweep: every instance of synth.sweep_instances stepped as
+    one batch (x-chunks autotuned per size bucket), against the same
+    instances stepped one after another with fk_step (each instance's steps
+    as CUDA-graph replays).  Both arms give bitwise identical states; the
+    metric is instances per hour at the workload's steps per instance,
+    from the timed per-step rate."""
+    rank, world, local = dist_env()
+    import torch
+    from paper_2303_14119_gb300 import fk
+    fk.load()
+    torch.cuda.set_device(local)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("gloo")
+        dist = td
+    stream = torch.cuda.current_stream().cuda_stream
+    w = synth.WORKLOADS[args.workload]
+    ins = synth.sweep_instances(w["sweep"], w["seed"])
+    prec = fk.FK_F32 if args.precision == "f32" else fk.FK_F64
+    steps = args.steps
+    grids = make_sweep_grids(fk, ins, prec, stream)
+    twins = make_sweep_grids(fk, ins, prec, stream)
+    cells = float(sum(p["nx"] * p["nv1"] * p["nv2"] for p in ins))
+    b = fk.Batch(grids, stream)
+    t0 = time.perf_counter()
+    tuned = b.autotune(2)
+    tune_s = time.perf_counter() - t0
+    b.step(args.warmup)
+    # kernel durations for the roofline (direct launches with event pairs)
+    kt_steps = 8
+    b.set_kernel_timing(True)
+    b.step(kt_steps)
+    launches, kms = b.kernel_timing()
+    b.set_kernel_timing(False)
+    pre = tuned + args.warmup + kt_steps
+    assert b.sync() == [fk.FK_OK] * len(ins)
+    # batched arm: graph replay
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms_b = reduce_over_ranks(e0.elapsed_time(e1), dist, "max")
+    ck = clocks.stop()
+    st_b = b.sync()
+    # sequential arm: the twins reach the same step untimed, then each
+    # instance runs its timed steps alone, one instance after another
+    for g in twins:
+        g.step(pre)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0.record()
+    for g in twins:
+        g.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms_s = reduce_over_ranks(e0.elapsed_time(e1), dist, "max")
+    # equal accuracy: identical states (sigma of every instance, f of a few)
+    same_sigma = sum(int(ga.surface_charge() == gb.surface_charge())
+                     for ga, gb in zip(grids, twins))
+    checks = list(range(0, len(ins), max(1, len(ins) // 8)))
+    same_f = sum(int(np.array_equal(grids[q].get_f(), twins[q].get_f())) for q in checks)
+    info = b.info()
+    chunks = b.chunks()
+    b.close()
+    for g in grids + twins:
+        g.close()
+    per_inst = w["steps"]
+    ms_step_b = ms_b / steps
+    ms_step_s = ms_s / steps
+    value = world * len(ins) * 3600.0 / (ms_step_b * per_inst / 1e3)
+    seq = world * len(ins) * 3600.0 / (ms_step_s * per_inst / 1e3)
+    peak, peak_kind = measured_peaks()
+    res = dict(launches=launches, kernel_ms=kms, cells_per_launch=cells)
+    roof = roofline(res, args.precision, peak, peak_kind)
+    if roof is not None:
+        roof["kernel"] = "batched fused upwind step (all %d instances per launch)" % len(ins)
+        roof["traffic"] = None
+    line = {
+        "metric": "batched instances/hr (%d steps per instance)" % per_inst, "value": value,
+        "unit": "instances/hr", "n_gpus": world, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": ms_step_b, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": "%s: %d instances, nx 128-512, nv1 = nv2 64-192, E_y log-uniform "
+                               "3e5-5e6 V/m, delta_max 2-4, A_max 250-600 eV, T_se 1-5 eV, "
+                               "one seed (%d); f0 = 0" % (args.workload, len(ins), w["seed"]),
+                   "cells_all_instances": cells, "steps_per_instance": per_inst,
+                   "rate": "instances/hr from the timed per-step time x %d steps" % per_inst,
+                   "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "cell_updates_per_s": world * cells * steps / (ms_b / 1e3),
+        "sequential": {"value": seq, "unit": "instances/hr", "ms_per_step": ms_step_s,
+                       "cell_updates_per_s": world * cells * steps / (ms_s / 1e3),
+                       "how": "fk_step(n) per instance, one instance after another"},
+        "speedup_vs_sequential": ms_s / ms_b,
+        "equal_accuracy": {"sigma_bitwise_identical": "%d/%d" % (same_sigma, len(ins)),
+                           "f_bitwise_identical": "%d/%d checked" % (same_f, len(checks)),
+                           "status_ok": "%d/%d" % (st_b.count(fk.FK_OK), len(ins))},
+        "autotune": {"steps": tuned, "seconds": round(tune_s, 3), "buckets": info["buckets"],
+                     "units_per_launch": info["units"],
+                     "chunk_len_range": [min(chunks), max(chunks)]},
+        "roofline": roof,
+        "gpu_launches": 2 * steps,
+        "clocks": ck,
+    }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -377,6 +559,8 @@ def run_reference(args):
         return
     import oracle
     w = synth.WORKLOADS[args.workload]
+    if "sweep" in w:  # the sampled instance: the sweep's first
+        w = synth.sweep_instances(w["sweep"], w["seed"])[0]
     shape = (w["nx"], w["nv1"], w["nv2"])
     o = oracle.Oracle(*shape, w["h_max"], -w["v1_span"], w["v1_span"], -w["v2_span"],
                       w["v2_span"], cfl=w["cfl"])
@@ -408,6 +592,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif "sweep" in synth.WORKLOADS[args.workload]:
+        run_sweep(args)
     else:
         run_ours(args)
 

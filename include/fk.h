@@ -42,6 +42,7 @@ extern "C" {
 #endif
 
 typedef struct fk_grid fk_grid; /* opaque, library-owned */
+typedef struct fk_batch fk_batch; /* opaque, library-owned; see fk_batch_create */
 
 typedef enum {
   FK_OK = 0,
@@ -219,6 +220,83 @@ fk_status fk_kernel_timing(fk_grid *grid, int64_t *launches, double *total_ms);
 #define FK_NOALLOC_MAX_PARTIALS 131072
 fk_status fk_density_moment_noalloc(const double *f_dev, int32_t nx, int32_t nv1, int32_t nv2,
                                     double dv1, double dv2, double *n_e_dev, void *cuda_stream);
+
+/* ---- Batched stepping of many grids (parameter sweeps) --------------------
+ * The paper's design studies (Sec. 3: scans over E_y, delta_max, A_max and
+ * T_se, each point a separate run) are many small independent runs.  A batch
+ * steps a set of existing grids together: every batch step is ONE launch of
+ * the streaming step kernel over the work units (v1-row tile x x-chunk) of
+ * all grids, largest units first, followed by ONE launch of the finalize
+ * kernel over all grids' planes, replayed 32 steps per CUDA graph.  Each
+ * grid's arithmetic is exactly that of fk_step on the same grid: the x-chunk
+ * split (the only thing the batch chooses) changes which CTA updates a cell,
+ * not how, so a batch step and fk_step give bitwise identical states.
+ *
+ * Ownership and state rules:
+ *  - The batch borrows the grids; the caller keeps ownership.  While a grid
+ *    belongs to a batch, every call that changes it (fk_step, the setters,
+ *    fk_set_f, fk_set_surface_charge, fk_set_kernel_timing and
+ *    fk_destroy_grid) returns FK_ESTATE; the getters work and see every
+ *    batch step enqueued before them.  fk_batch_destroy releases the grids.
+ *  - A grid that meets a sticky device error (FK_ECFL, FK_ENUMERIC,
+ *    FK_ETIMEOUT) freezes at its last valid state; the other grids go on.
+ *    fk_batch_sync reports each grid's status.
+ *  - Work is ordered on the batch's stream. */
+
+/* Create a batch of n >= 1 distinct grids, none already in a batch, all on
+ * one device, all of one precision, all using the streaming step kernel
+ * (fk_grid_info's kernel entry is 1).  Waits for each grid's pending work.
+ * cuda_stream: stream for the batch's work, or NULL for one it owns.
+ * Errors: FK_EINVAL (NULL, n < 1, duplicates, mixed device or precision, a
+ * grid on the direct-load kernel), FK_ESTATE (a grid already in a batch),
+ * FK_ENOMEM / FK_ECUDA. */
+fk_status fk_batch_create(fk_grid *const *grids, int32_t n, void *cuda_stream, fk_batch **out);
+
+/* Wait for the batch's work, release its grids (each re-synchronised so it
+ * can be stepped alone again) and free the batch.  NULL is accepted. */
+fk_status fk_batch_destroy(fk_batch *batch);
+
+/* Advance every grid of the batch by n >= 0 steps (stream-ordered,
+ * asynchronous; frozen grids stay frozen).  Returns FK_OK unless the work
+ * could not be enqueued. */
+fk_status fk_batch_step(fk_batch *batch, int64_t n);
+
+/* Wait for the batch's stream and read each grid's sticky status into
+ * status[i] (may be NULL).  Returns FK_OK if every grid is OK, else the
+ * status of the first grid that is not (its message in fk_batch_last_error). */
+fk_status fk_batch_sync(fk_batch *batch, int32_t *status);
+
+/* Autotuner: picks the x-chunk length (planes per work unit) of every size
+ * bucket of the batch -- grids grouped by plane size and nx, each a power of
+ * two -- by timing real steps: one trial of steps_per_trial >= 1 batch steps
+ * per candidate length (4 planes up to the whole x range), bucket by bucket,
+ * largest bucket first, keeping the fastest.  The trials advance every grid
+ * (bitwise as fk_batch_step would); *steps_taken (may be NULL) receives how
+ * many steps they took.  The v1-row tile of each grid is fixed by its shared-
+ * memory plan (the most rows for which two CTAs fit on an SM). */
+fk_status fk_batch_autotune(fk_batch *batch, int32_t steps_per_trial, int64_t *steps_taken);
+
+/* Read (chunk_len[n]) or set the planes per x-chunk of every grid.  Set:
+ * each value is clamped to [1, nx]; the next fk_batch_step uses it. */
+fk_status fk_batch_get_chunks(const fk_batch *batch, int32_t *chunk_len);
+fk_status fk_batch_set_chunks(fk_batch *batch, const int32_t *chunk_len);
+
+/* Batch facts, FK_BATCH_INFO_LEN doubles: grids, work units of one step
+ * kernel launch, finalize blocks, dynamic shared memory per CTA (bytes),
+ * CTAs per SM, phase-space cells of all grids, size buckets, batch steps
+ * enqueued.  Host-side, no synchronisation. */
+#define FK_BATCH_INFO_LEN 8
+fk_status fk_batch_info(const fk_batch *batch, double *out);
+
+/* Kernel timing for the batch, as fk_set_kernel_timing / fk_kernel_timing:
+ * with enabled != 0 every batch step is launched directly with an event
+ * pair around the batched step kernel. */
+fk_status fk_batch_set_kernel_timing(fk_batch *batch, int enabled);
+fk_status fk_batch_kernel_timing(fk_batch *batch, int64_t *launches, double *total_ms);
+
+/* Text of the last error on this batch ("" if none); NULL: errors of
+ * fk_batch_create on the calling thread. */
+const char *fk_batch_last_error(const fk_batch *batch);
 
 /* Text of the last error on this grid ("" if none).  grid may be NULL for
  * errors of fk_create_grid on the calling thread.  Valid until the next call

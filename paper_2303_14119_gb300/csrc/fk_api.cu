@@ -14,7 +14,7 @@
 #include <string>
 #include <vector>
 
-#include "fk_internal.cuh"
+#include "fk_host.cuh"
 
 using namespace fk;
 
@@ -30,45 +30,6 @@ constexpr size_t kStageElems = size_t(1) << 23;  // FP64 staging chunk, 64 MB
 
 void fk::set_thread_error(const char* msg) { g_create_error = msg; }
 
-struct fk_grid {
-  int dev = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  cudaStream_t cap_stream = nullptr;
-  fk_grid_desc desc{};
-  int prec = FK_F64;
-  int nx = 0, nv1 = 0, nv2 = 0, pitch = 0;
-  size_t esize = 8;
-  double dx = 0, dv1 = 0, dv2 = 0, dt = 0;
-  Params prm{};
-  Params* d_prm = nullptr;
-  DevState* d_st = nullptr;
-  void* d_f[2] = {nullptr, nullptr};
-  int enq_cur = 0;            // buffer the next enqueued step reads
-  int base_cur = 0;           // buffer that held state base_step
-  long long base_step = 0;
-  Tables tab{};
-  Partials part{};
-  Geom geom{};
-  bool use_stream = true;  // streaming kernel (else the direct-load kernel)
-  double *d_ne = nullptr, *d_Ex = nullptr, *d_c1 = nullptr, *d_hist = nullptr;
-  float* d_c1_32 = nullptr;
-  FinScratch fin{};
-  void* d_stage = nullptr;
-  // physics parameters as last set
-  double Ey = 0, Ex_ext = 0;
-  int self_consistent = 1;
-  double delta_max = 0, A_max = 1, k_s = 1, T_se = 1;
-  int see_enabled = 0;
-  double J = 0, x_lo = 0, x_hi = 0, T_fe = 1;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  unsigned known_flags = 0;
-  // kernel timing
-  bool timing = false;
-  std::vector<cudaEvent_t> ev;  // pairs: 2*r = start, 2*r+1 = stop
-  int ev_used = 0;              // pairs recorded since the last read
-  std::string err;
-};
 
 namespace {
 
@@ -91,7 +52,9 @@ fk_status cuda_fail(fk_grid* g, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail((g), e_, #call); \
   } while (0)
 
-fk_status flags_status(fk_grid* g, unsigned flags) {
+}  // namespace
+
+fk_status fk::flags_status(fk_grid* g, unsigned flags) {
   if (flags & kFlagTimeout) return fail(g, FK_ETIMEOUT, "a bounded wait inside the step kernel ran out");
   if (flags & kFlagNumeric) return fail(g, FK_ENUMERIC, "a moment or flux became non-finite");
   if (flags & kFlagCfl)
@@ -99,7 +62,11 @@ fk_status flags_status(fk_grid* g, unsigned flags) {
   return FK_OK;
 }
 
-StepArgs make_args(fk_grid* g, int cur) {
+namespace {
+
+}  // namespace
+
+StepArgs fk::make_args(fk_grid* g, int cur) {
   StepArgs a{};
   a.f_in = g->d_f[cur];
   a.f_out = g->d_f[cur ^ 1];
@@ -117,6 +84,8 @@ StepArgs make_args(fk_grid* g, int cur) {
   return a;
 }
 
+namespace {
+
 fk_status upload_params(fk_grid* g) {
   FK_CUDA(g, cudaMemcpyAsync(g->d_prm, &g->prm, sizeof(Params), cudaMemcpyHostToDevice, g->stream));
   return FK_OK;
@@ -124,8 +93,11 @@ fk_status upload_params(fk_grid* g) {
 
 // Synchronise, read the device scalars, and re-base the buffer bookkeeping
 // on the last valid state.
-fk_status sync_state(fk_grid* g, DevState* out) {
+}  // namespace
+
+fk_status fk::sync_state(fk_grid* g, DevState* out) {
   FK_CUDA(g, cudaSetDevice(g->dev));
+  if (g->batch_done) FK_CUDA(g, cudaStreamWaitEvent(g->stream, g->batch_done, 0));
   FK_CUDA(g, cudaMemcpyAsync(out, g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
   FK_CUDA(g, cudaStreamSynchronize(g->stream));
   const long long adv = out->step - g->base_step;
@@ -135,6 +107,8 @@ fk_status sync_state(fk_grid* g, DevState* out) {
   g->known_flags = out->flags;
   return FK_OK;
 }
+
+namespace {
 
 // Evaluate the current state: moments of f, then finalize in `mode`.
 fk_status evaluate(fk_grid* g, int mode) {
@@ -157,6 +131,13 @@ cudaError_t enqueue_step(fk_grid* g, int cur, cudaStream_t s, cudaEvent_t ev0, c
     e = launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, g->fin, kModeStep, s);
   return e;
 }
+
+// Calls that change a grid's state are refused while a batch steps it.
+#define FK_NOT_IN_BATCH(g)                                                          \
+  do {                                                                              \
+    if ((g)->batch)                                                                 \
+      return fail((g), FK_ESTATE, "the grid is stepped by a batch: destroy the batch first"); \
+  } while (0)
 
 fk_status clear_flags(fk_grid* g, unsigned mask) {
   // flags live in DevState; clear with a read-modify-write through the host
@@ -441,12 +422,14 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
 }
 
 fk_status fk_destroy_grid(fk_grid* g) {
+  if (g) FK_NOT_IN_BATCH(g);
   free_grid(g);
   return FK_OK;
 }
 
 fk_status fk_set_fields(fk_grid* g, double Ey, int self_consistent, double Ex_external) {
   if (!g) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
   if (!(Ey <= 0.0) || !isfinite(Ey) || !isfinite(Ex_external))
     return fail(g, FK_EINVAL, "E_y must be finite and <= 0 (cathode on the left); E_x finite");
   g->Ey = Ey;
@@ -462,6 +445,7 @@ fk_status fk_set_fields(fk_grid* g, double Ey, int self_consistent, double Ex_ex
 fk_status fk_set_see(fk_grid* g, double delta_max, double A_max_eV, double k_s, double T_se_eV,
                      int enabled) {
   if (!g) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
   if (!(delta_max >= 0.0) || !(A_max_eV > 0.0) || !(k_s >= 0.0) || !(T_se_eV > 0.0) ||
       !isfinite(delta_max) || !isfinite(A_max_eV) || !isfinite(k_s) || !isfinite(T_se_eV))
     return fail(g, FK_EINVAL, "need delta_max >= 0, A_max > 0, k_s >= 0, T_se > 0");
@@ -476,6 +460,7 @@ fk_status fk_set_see(fk_grid* g, double delta_max, double A_max_eV, double k_s, 
 
 fk_status fk_set_source(fk_grid* g, double J, double x_lo, double x_hi, double T_fe_eV) {
   if (!g) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
   if (!(J >= 0.0) || !(x_lo <= x_hi) || !(T_fe_eV > 0.0) || !isfinite(J) || !isfinite(T_fe_eV))
     return fail(g, FK_EINVAL, "need J >= 0, x_lo <= x_hi, T_fe > 0");
   int lo = -1, hi = -1;
@@ -504,6 +489,7 @@ fk_status fk_set_source(fk_grid* g, double J, double x_lo, double x_hi, double T
 
 fk_status fk_set_convergence(fk_grid* g, int64_t window, double rel_tol) {
   if (!g) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
   if (window < 1 || window >= g->prm.hist_cap || !(rel_tol >= 0.0))
     return fail(g, FK_EINVAL, "need 1 <= window < history_capacity and rel_tol >= 0");
   g->prm.sat_window = window;
@@ -513,6 +499,7 @@ fk_status fk_set_convergence(fk_grid* g, int64_t window, double rel_tol) {
 
 fk_status fk_step(fk_grid* g, int64_t n) {
   if (!g) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
   if (n < 0) return fail(g, FK_EINVAL, "n must be >= 0");
   if (g->known_flags) return flags_status(g, g->known_flags);
   FK_CUDA(g, cudaSetDevice(g->dev));
@@ -645,6 +632,7 @@ fk_status fk_get_f(fk_grid* g, double* host_f) {
 
 fk_status fk_set_f(fk_grid* g, const double* host_f) {
   if (!g || !host_f) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
   DevState st;
   fk_status s = sync_state(g, &st);
   if (s != FK_OK) return s;
@@ -678,6 +666,7 @@ fk_status fk_set_f(fk_grid* g, const double* host_f) {
 
 fk_status fk_set_surface_charge(fk_grid* g, double sigma) {
   if (!g || !isfinite(sigma)) return g ? fail(g, FK_EINVAL, "sigma must be finite") : FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
   DevState st;
   fk_status s = sync_state(g, &st);
   if (s != FK_OK) return s;
@@ -709,6 +698,7 @@ fk_status fk_grid_info(const fk_grid* g, double* out) {
 
 fk_status fk_set_kernel_timing(fk_grid* g, int enabled) {
   if (!g) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
   FK_CUDA(g, cudaSetDevice(g->dev));
   if (enabled && g->ev.empty()) {
     g->ev.resize(2 * kMaxTimed, nullptr);

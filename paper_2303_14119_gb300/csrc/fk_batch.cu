@@ -1,0 +1,570 @@
+// Batched stepping of many independent grids (the parameter scans of
+// Sec. 3 of Sun et al., arXiv 2303.14119, run as one sweep): per batch step
+// one launch of the streaming step kernel over the work units of every grid
+// and one launch of the finalize kernel over every grid's planes, replayed
+// 32 steps per CUDA graph; an autotuner for the x-chunk length per size
+// bucket.  The C ABI is declared in include/fk.h.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fk_host.cuh"
+
+using namespace fk;
+
+namespace {
+
+thread_local std::string g_batch_create_error;
+
+constexpr int kBatchGraphSteps = 32;  // steps per captured graph (even)
+constexpr int kBatchMaxTimed = 8192;  // step-kernel launches timed between reads
+constexpr int kMinChunk = 4;          // fewest planes per x-chunk the planner picks
+constexpr double kDefaultWaves = 4.0; // default plan: about this many CTA waves
+
+}  // namespace
+
+struct fk_batch {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;
+  int prec = FK_F64;
+  bool padded = false;  // some grid has row padding (pitch > nv2)
+  int n = 0;
+  std::vector<fk_grid*> grids;
+  std::vector<int> cur0;       // buffer holding each grid's f at batch step 0
+  std::vector<int> chunk_len;  // planes per x-chunk, per grid
+  std::vector<int> bucket;     // size bucket per grid
+  int n_buckets = 0;
+  long long steps = 0;         // batch steps enqueued
+  double cells = 0;            // phase-space cells of all grids
+  BatchInst* d_inst = nullptr; // [2][n]: grid arguments for even / odd batch steps
+  int2* d_units = nullptr;     // [max_units] work units, largest first
+  int n_units = 0, max_units = 0;
+  int2* d_fblk = nullptr;      // [n_fblk] finalize blocks
+  int n_fblk = 0;
+  size_t smem = 0;             // dynamic shared memory per CTA of the step kernel
+  int per_sm = 0, sms = 0;
+  bool dirty = true;           // units / arguments must be re-uploaded
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaEvent_t done = nullptr;  // recorded after the last enqueued batch step
+  bool timing = false;
+  std::vector<cudaEvent_t> ev; // pairs around the step kernel
+  int ev_used = 0;
+  std::string err;
+};
+
+namespace {
+
+fk_status bfail(fk_batch* b, fk_status s, const std::string& msg) {
+  if (b)
+    b->err = msg;
+  else
+    g_batch_create_error = msg;
+  return s;
+}
+
+fk_status bcuda_fail(fk_batch* b, cudaError_t e, const char* what) {
+  return bfail(b, e == cudaErrorMemoryAllocation ? FK_ENOMEM : FK_ECUDA,
+               std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define BK_CUDA(b, call)                                      \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return bcuda_fail((b), e_, #call); \
+  } while (0)
+
+int chunks_of(int nx, int len) { return (nx + len - 1) / len; }
+
+// Equal chunks of at most len planes.
+int even_chunk_len(int nx, int len) {
+  len = std::max(1, std::min(len, nx));
+  const int nc = chunks_of(nx, len);
+  return (nx + nc - 1) / nc;
+}
+
+// Grid i's geometry with the batch's x-chunking.
+Geom batch_geom(const fk_batch* b, int i) {
+  Geom gm = b->grids[i]->geom;
+  gm.chunk_len = b->chunk_len[i];
+  gm.n_chunks = chunks_of(b->grids[i]->nx, gm.chunk_len);
+  return gm;
+}
+
+// Cells a unit reads: its rows x pitch over its planes plus the upwind plane
+// loaded first (every chunk but the first along the march).
+long long unit_cells(const fk_grid* g, const Geom& gm, int t, int c) {
+  int i0, i1, dir;
+  tile_rows(gm, g->nv1, t, &i0, &i1, &dir);
+  const int s0 = c * gm.chunk_len;
+  const int s1 = std::min(g->nx, s0 + gm.chunk_len);
+  if (s0 >= s1 || i0 >= i1) return 0;
+  return (long long)(i1 - i0) * g->pitch * (s1 - s0 + (s0 > 0 ? 1 : 0));
+}
+
+// Work units of the current chunking, largest first (ties in grid, tile,
+// chunk order), so that the block scheduler hands out the long units before
+// the short ones that fill the last wave.
+std::vector<int2> plan_units(const fk_batch* b) {
+  struct U {
+    long long cells;
+    int inst, local;
+  };
+  std::vector<U> us;
+  for (int i = 0; i < b->n; i++) {
+    const Geom gm = batch_geom(b, i);
+    for (int c = 0; c < gm.n_chunks; c++)
+      for (int t = 0; t < gm.n_tiles; t++) {
+        const long long w = unit_cells(b->grids[i], gm, t, c);
+        if (w > 0) us.push_back({w, i, t + gm.n_tiles * c});
+      }
+  }
+  std::stable_sort(us.begin(), us.end(), [](const U& x, const U& y) { return x.cells > y.cells; });
+  std::vector<int2> out(us.size());
+  for (size_t q = 0; q < us.size(); q++) out[q] = make_int2(us[q].inst, us[q].local);
+  return out;
+}
+
+// Default chunking: units of about (all cells) / (kDefaultWaves x resident
+// CTAs), at least kMinChunk planes, one chunk if the grid is smaller.
+void default_chunks(fk_batch* b) {
+  const double slots = (double)b->sms * b->per_sm;
+  const double target = b->cells / (kDefaultWaves * slots);
+  for (int i = 0; i < b->n; i++) {
+    const fk_grid* g = b->grids[i];
+    const double per_tile = (double)g->nx * g->nv1 * g->pitch / g->geom.n_tiles;
+    int nc = (int)lround(per_tile / std::max(target, 1.0));
+    nc = std::max(1, std::min(nc, std::max(1, g->nx / kMinChunk)));
+    b->chunk_len[i] = (g->nx + nc - 1) / nc;
+  }
+}
+
+// Size buckets: grids with the same power-of-two class of plane size and nx.
+void assign_buckets(fk_batch* b) {
+  std::map<std::pair<int, int>, int> ids;
+  for (int i = 0; i < b->n; i++) {
+    const fk_grid* g = b->grids[i];
+    const int lp = (int)floor(log2((double)g->nv1 * g->pitch));
+    const int lx = (int)floor(log2((double)g->nx));
+    auto it = ids.find({lp, lx});
+    if (it == ids.end()) it = ids.emplace(std::make_pair(lp, lx), (int)ids.size()).first;
+    b->bucket[i] = it->second;
+  }
+  b->n_buckets = (int)ids.size();
+}
+
+}  // namespace
+
+namespace {
+
+void drop_graphs(fk_batch* b) {
+  for (int p = 0; p < 2; p++)
+    if (b->graph[p]) {
+      cudaGraphExecDestroy(b->graph[p]);
+      b->graph[p] = nullptr;
+    }
+}
+
+// Upload both parities' grid arguments and the unit list of the current
+// chunking (after the batch's earlier work: the buffers may be in use).
+fk_status upload_plan(fk_batch* b) {
+  std::vector<BatchInst> h(2 * (size_t)b->n);
+  for (int p = 0; p < 2; p++)
+    for (int i = 0; i < b->n; i++) {
+      fk_grid* g = b->grids[i];
+      BatchInst& bi = h[(size_t)p * b->n + i];
+      bi.a = make_args(g, b->cur0[i] ^ p);
+      bi.a.geom = batch_geom(b, i);
+      bi.o = FinOut{g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, g->fin};
+    }
+  const std::vector<int2> units = plan_units(b);
+  BK_CUDA(b, cudaStreamSynchronize(b->stream));
+  drop_graphs(b);
+  if ((int)units.size() > b->max_units) {
+    if (b->d_units) BK_CUDA(b, cudaFree(b->d_units));
+    b->d_units = nullptr;
+    b->max_units = 0;
+    BK_CUDA(b, cudaMalloc(&b->d_units, units.size() * sizeof(int2)));
+    b->max_units = (int)units.size();
+  }
+  b->n_units = (int)units.size();
+  BK_CUDA(b, cudaMemcpyAsync(b->d_inst, h.data(), h.size() * sizeof(BatchInst),
+                             cudaMemcpyHostToDevice, b->stream));
+  if (b->n_units)
+    BK_CUDA(b, cudaMemcpyAsync(b->d_units, units.data(), units.size() * sizeof(int2),
+                               cudaMemcpyHostToDevice, b->stream));
+  BK_CUDA(b, cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
+  b->dirty = false;
+  return FK_OK;
+}
+
+// One batch step whose grids read the buffers of parity p: the batched step
+// kernel (optionally between two events) then the batched finalize.
+cudaError_t enqueue_batch_step(fk_batch* b, int p, cudaStream_t s, cudaEvent_t ev0,
+                               cudaEvent_t ev1) {
+  const BatchInst* inst = b->d_inst + (size_t)p * b->n;
+  cudaError_t e = cudaSuccess;
+  if (ev0) e = cudaEventRecord(ev0, s);
+  if (e == cudaSuccess)
+    e = launch_step_stream_batch(inst, b->d_units, b->n_units, b->prec, b->padded, b->smem, s);
+  if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
+  if (e == cudaSuccess) e = launch_finalize_batch(inst, b->d_fblk, b->n_fblk, s);
+  return e;
+}
+
+fk_status build_batch_graph(fk_batch* b, int parity) {
+  cudaStream_t cs = b->cap_stream;
+  BK_CUDA(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < kBatchGraphSteps && e == cudaSuccess; s++)
+    e = enqueue_batch_step(b, (parity + s) & 1, cs, nullptr, nullptr);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return bcuda_fail(b, e, "capturing the batch step graph");
+  }
+  if (e2 != cudaSuccess) return bcuda_fail(b, e2, "cudaStreamEndCapture");
+  const cudaError_t e3 = cudaGraphInstantiate(&b->graph[parity], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e3 != cudaSuccess) return bcuda_fail(b, e3, "cudaGraphInstantiate");
+  return FK_OK;
+}
+
+// Enqueue n steps (graphs of kBatchGraphSteps where possible; direct launches
+// with event pairs in timing mode) and mark the batch's progress.
+fk_status enqueue_steps(fk_batch* b, long long n) {
+  if (b->dirty) {
+    const fk_status s = upload_plan(b);
+    if (s != FK_OK) return s;
+  }
+  while (n > 0) {
+    const int p = (int)(b->steps & 1);
+    if (b->timing) {
+      const bool rec = b->ev_used < kBatchMaxTimed;
+      BK_CUDA(b, enqueue_batch_step(b, p, b->stream, rec ? b->ev[2 * b->ev_used] : nullptr,
+                                    rec ? b->ev[2 * b->ev_used + 1] : nullptr));
+      if (rec) b->ev_used++;
+      b->steps += 1;
+      n -= 1;
+    } else if (n >= kBatchGraphSteps) {
+      if (!b->graph[p]) {
+        const fk_status s = build_batch_graph(b, p);
+        if (s != FK_OK) return s;
+      }
+      BK_CUDA(b, cudaGraphLaunch(b->graph[p], b->stream));
+      b->steps += kBatchGraphSteps;  // even: the parity is unchanged
+      n -= kBatchGraphSteps;
+    } else {
+      BK_CUDA(b, enqueue_batch_step(b, p, b->stream, nullptr, nullptr));
+      b->steps += 1;
+      n -= 1;
+    }
+  }
+  BK_CUDA(b, cudaEventRecord(b->done, b->stream));
+  return FK_OK;
+}
+
+// Release the grids (re-based on their device step counters) and free.
+void free_batch(fk_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->dev);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_graphs(b);
+  for (fk_grid* g : b->grids) {
+    if (!g || g->batch != b) continue;
+    g->batch = nullptr;
+    g->batch_done = nullptr;
+    DevState st;
+    sync_state(g, &st);
+  }
+  void* ptrs[] = {b->d_inst, b->d_units, b->d_fblk};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+fk_status fk_batch_create(fk_grid* const* grids, int32_t n, void* cuda_stream, fk_batch** out) {
+  g_batch_create_error.clear();
+  if (!grids || !out || n < 1)
+    return bfail(nullptr, FK_EINVAL, "grids and out must not be NULL and n must be >= 1");
+  *out = nullptr;
+  std::vector<fk_grid*> gs(grids, grids + n);
+  for (int i = 0; i < n; i++) {
+    fk_grid* g = gs[i];
+    const std::string who = "grid " + std::to_string(i);
+    if (!g) return bfail(nullptr, FK_EINVAL, who + " is NULL");
+    if (g->batch) return bfail(nullptr, FK_ESTATE, who + " already belongs to a batch");
+    if (g->dev != gs[0]->dev) return bfail(nullptr, FK_EINVAL, who + " is on another device");
+    if (g->prec != gs[0]->prec) return bfail(nullptr, FK_EINVAL, who + " has another precision");
+    if (!g->use_stream)
+      return bfail(nullptr, FK_EINVAL, who + " uses the direct-load step kernel (rows too wide)");
+  }
+  {
+    std::vector<fk_grid*> sorted(gs);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return bfail(nullptr, FK_EINVAL, "a grid appears twice");
+  }
+  fk_batch* b = new (std::nothrow) fk_batch();
+  if (!b) return bfail(nullptr, FK_ENOMEM, "host allocation failed");
+  b->dev = gs[0]->dev;
+  b->prec = gs[0]->prec;
+  b->n = n;
+  b->grids = gs;
+  b->cur0.assign(n, 0);
+  b->chunk_len.assign(n, 1);
+  b->bucket.assign(n, 0);
+
+#define CREATE_B(call)                                          \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) {                                    \
+      const fk_status s_ = bcuda_fail(nullptr, e_, #call);      \
+      free_batch(b);                                            \
+      return s_;                                                \
+    }                                                           \
+  } while (0)
+
+  CREATE_B(cudaSetDevice(b->dev));
+  if (cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    CREATE_B(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    b->own_stream = true;
+  }
+  CREATE_B(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  CREATE_B(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
+  CREATE_B(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev));
+  std::vector<int2> fblk;
+  for (int i = 0; i < n; i++) {
+    fk_grid* g = gs[i];
+    b->smem = std::max(b->smem, stream_smem_bytes(g->prec, g->geom.stage_elems, g->pitch));
+    if (g->pitch != g->nv2) b->padded = true;
+    b->cells += (double)g->nx * g->nv1 * g->nv2;
+    for (int q = 0; q < finalize_blocks(g->nx); q++) fblk.push_back(make_int2(i, q));
+    DevState st;
+    const fk_status s = sync_state(g, &st);  // the grid's own work is done
+    if (s != FK_OK) {
+      g_batch_create_error = "grid " + std::to_string(i) + ": " + g->err;
+      free_batch(b);
+      return s;
+    }
+    b->cur0[i] = g->enq_cur;
+  }
+  b->per_sm = stream_ctas_per_sm(b->prec, b->smem);
+  if (b->per_sm <= 0) {
+    free_batch(b);
+    return bfail(nullptr, FK_EINVAL, "the grids' shared-memory plans do not fit an SM");
+  }
+  b->n_fblk = (int)fblk.size();
+  CREATE_B(cudaMalloc(&b->d_inst, 2 * (size_t)n * sizeof(BatchInst)));
+  CREATE_B(cudaMalloc(&b->d_fblk, fblk.size() * sizeof(int2)));
+  CREATE_B(cudaMemcpy(b->d_fblk, fblk.data(), fblk.size() * sizeof(int2),
+                      cudaMemcpyHostToDevice));
+#undef CREATE_B
+  default_chunks(b);
+  assign_buckets(b);
+  fk_status s = upload_plan(b);
+  if (s != FK_OK) {
+    g_batch_create_error = b->err;
+    free_batch(b);
+    return s;
+  }
+  for (fk_grid* g : gs) {
+    g->batch = b;
+    g->batch_done = b->done;
+  }
+  *out = b;
+  return FK_OK;
+}
+
+fk_status fk_batch_destroy(fk_batch* b) {
+  free_batch(b);
+  return FK_OK;
+}
+
+fk_status fk_batch_step(fk_batch* b, int64_t n) {
+  if (!b) return FK_EINVAL;
+  if (n < 0) return bfail(b, FK_EINVAL, "n must be >= 0");
+  BK_CUDA(b, cudaSetDevice(b->dev));
+  return enqueue_steps(b, n);
+}
+
+fk_status fk_batch_sync(fk_batch* b, int32_t* status) {
+  if (!b) return FK_EINVAL;
+  BK_CUDA(b, cudaSetDevice(b->dev));
+  BK_CUDA(b, cudaStreamSynchronize(b->stream));
+  std::vector<DevState> st(b->n);
+  for (int i = 0; i < b->n; i++)
+    BK_CUDA(b, cudaMemcpyAsync(&st[i], b->grids[i]->d_st, sizeof(DevState),
+                               cudaMemcpyDeviceToHost, b->stream));
+  BK_CUDA(b, cudaStreamSynchronize(b->stream));
+  fk_status first = FK_OK;
+  for (int i = 0; i < b->n; i++) {
+    fk_grid* g = b->grids[i];
+    const fk_status s = flags_status(g, st[i].flags);
+    if (status) status[i] = s;
+    if (s != FK_OK && first == FK_OK) {
+      first = s;
+      b->err = "grid " + std::to_string(i) + ": " + g->err;
+    }
+  }
+  return first;
+}
+
+fk_status fk_batch_get_chunks(const fk_batch* b, int32_t* chunk_len) {
+  if (!b || !chunk_len) return FK_EINVAL;
+  for (int i = 0; i < b->n; i++) chunk_len[i] = b->chunk_len[i];
+  return FK_OK;
+}
+
+fk_status fk_batch_set_chunks(fk_batch* b, const int32_t* chunk_len) {
+  if (!b || !chunk_len) return FK_EINVAL;
+  for (int i = 0; i < b->n; i++)
+    b->chunk_len[i] = std::max(1, std::min((int)chunk_len[i], b->grids[i]->nx));
+  b->dirty = true;
+  return FK_OK;
+}
+
+fk_status fk_batch_info(const fk_batch* b, double* out) {
+  if (!b || !out) return FK_EINVAL;
+  // the unit count of the chunking in force (re-planned if it changed)
+  const int units = b->dirty ? (int)plan_units(b).size() : b->n_units;
+  out[0] = b->n;
+  out[1] = units;
+  out[2] = b->n_fblk;
+  out[3] = (double)b->smem;
+  out[4] = b->per_sm;
+  out[5] = b->cells;
+  out[6] = b->n_buckets;
+  out[7] = (double)b->steps;
+  return FK_OK;
+}
+
+fk_status fk_batch_autotune(fk_batch* b, int32_t steps_per_trial, int64_t* steps_taken) {
+  if (!b) return FK_EINVAL;
+  if (steps_per_trial < 1) return bfail(b, FK_EINVAL, "steps_per_trial must be >= 1");
+  BK_CUDA(b, cudaSetDevice(b->dev));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BK_CUDA(b, cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return bcuda_fail(b, ce, "cudaEventCreate");
+  }
+  long long taken = 0;
+  // one trial: steps_per_trial real batch steps of the current chunking,
+  // timed on the batch's stream
+  auto trial = [&](float* ms) -> fk_status {
+    if (b->dirty) {
+      const fk_status s = upload_plan(b);
+      if (s != FK_OK) return s;
+    }
+    BK_CUDA(b, cudaEventRecord(e0, b->stream));
+    for (int q = 0; q < steps_per_trial; q++) {
+      BK_CUDA(b, enqueue_batch_step(b, (int)(b->steps & 1), b->stream, nullptr, nullptr));
+      b->steps += 1;
+    }
+    BK_CUDA(b, cudaEventRecord(e1, b->stream));
+    BK_CUDA(b, cudaEventRecord(b->done, b->stream));
+    BK_CUDA(b, cudaEventSynchronize(e1));
+    BK_CUDA(b, cudaEventElapsedTime(ms, e0, e1));
+    taken += steps_per_trial;
+    return FK_OK;
+  };
+  fk_status s = FK_OK;
+  float best = 0.f, ms = 0.f;
+  // buckets by their cells, largest first
+  std::vector<double> bcells(b->n_buckets, 0.0);
+  std::vector<int> bmax_nx(b->n_buckets, 1);
+  for (int i = 0; i < b->n; i++) {
+    const fk_grid* g = b->grids[i];
+    bcells[b->bucket[i]] += (double)g->nx * g->nv1 * g->pitch;
+    bmax_nx[b->bucket[i]] = std::max(bmax_nx[b->bucket[i]], g->nx);
+  }
+  std::vector<int> order(b->n_buckets);
+  for (int q = 0; q < b->n_buckets; q++) order[q] = q;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return bcells[x] > bcells[y]; });
+  s = trial(&ms);  // warm-up (first touch of the plan)
+  if (s == FK_OK) s = trial(&best);
+  std::vector<int> keep = b->chunk_len;
+  for (size_t oi = 0; oi < order.size() && s == FK_OK; oi++) {
+    const int q = order[oi];
+    for (int L = kMinChunk; s == FK_OK; L *= 2) {
+      const int Lc = std::min(L, bmax_nx[q]);
+      bool changed = false;
+      for (int i = 0; i < b->n; i++)
+        if (b->bucket[i] == q) {
+          const int len = even_chunk_len(b->grids[i]->nx, Lc);
+          changed |= len != b->chunk_len[i];
+          b->chunk_len[i] = len;
+        }
+      if (changed) {
+        b->dirty = true;
+        s = trial(&ms);
+        if (s == FK_OK && ms < best) {
+          best = ms;
+          keep = b->chunk_len;
+        }
+      }
+      b->chunk_len = keep;
+      b->dirty = true;
+      if (Lc >= bmax_nx[q]) break;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (steps_taken) *steps_taken = taken;
+  return s;
+}
+
+fk_status fk_batch_set_kernel_timing(fk_batch* b, int enabled) {
+  if (!b) return FK_EINVAL;
+  BK_CUDA(b, cudaSetDevice(b->dev));
+  if (enabled && b->ev.empty()) {
+    b->ev.resize(2 * kBatchMaxTimed, nullptr);
+    for (auto& e : b->ev) BK_CUDA(b, cudaEventCreate(&e));
+  }
+  BK_CUDA(b, cudaStreamSynchronize(b->stream));
+  b->timing = enabled != 0;
+  b->ev_used = 0;
+  return FK_OK;
+}
+
+fk_status fk_batch_kernel_timing(fk_batch* b, int64_t* launches, double* total_ms) {
+  if (!b || !launches || !total_ms) return FK_EINVAL;
+  BK_CUDA(b, cudaSetDevice(b->dev));
+  BK_CUDA(b, cudaStreamSynchronize(b->stream));
+  double tot = 0.0;
+  for (int r = 0; r < b->ev_used; r++) {
+    float ms = 0.f;
+    BK_CUDA(b, cudaEventElapsedTime(&ms, b->ev[2 * r], b->ev[2 * r + 1]));
+    tot += ms;
+  }
+  *launches = b->ev_used;
+  *total_ms = tot;
+  b->ev_used = 0;
+  return FK_OK;
+}
+
+const char* fk_batch_last_error(const fk_batch* b) {
+  return b ? b->err.c_str() : g_batch_create_error.c_str();
+}
+
+}  // extern "C"

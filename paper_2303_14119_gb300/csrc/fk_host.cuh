@@ -1,0 +1,64 @@
+// Host-side definition of the grid object, shared by the grid API and the
+// batch API (internal; the public ABI is include/fk.h).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "fk_internal.cuh"
+
+struct fk_grid {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;
+  fk_grid_desc desc{};
+  int prec = FK_F64;
+  int nx = 0, nv1 = 0, nv2 = 0, pitch = 0;
+  size_t esize = 8;
+  double dx = 0, dv1 = 0, dv2 = 0, dt = 0;
+  fk::Params prm{};
+  fk::Params* d_prm = nullptr;
+  fk::DevState* d_st = nullptr;
+  void* d_f[2] = {nullptr, nullptr};
+  int enq_cur = 0;            // buffer the next enqueued step reads
+  int base_cur = 0;           // buffer that held state base_step
+  long long base_step = 0;
+  fk::Tables tab{};
+  fk::Partials part{};
+  fk::Geom geom{};
+  bool use_stream = true;  // streaming kernel (else the direct-load kernel)
+  double *d_ne = nullptr, *d_Ex = nullptr, *d_c1 = nullptr, *d_hist = nullptr;
+  float* d_c1_32 = nullptr;
+  fk::FinScratch fin{};
+  void* d_stage = nullptr;
+  // physics parameters as last set
+  double Ey = 0, Ex_ext = 0;
+  int self_consistent = 1;
+  double delta_max = 0, A_max = 1, k_s = 1, T_se = 1;
+  int see_enabled = 0;
+  double J = 0, x_lo = 0, x_hi = 0, T_fe = 1;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  unsigned known_flags = 0;
+  // kernel timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;  // pairs: 2*r = start, 2*r+1 = stop
+  int ev_used = 0;              // pairs recorded since the last read
+  // batch that steps this grid: while set, calls that change the state are
+  // refused and the getters wait for the batch's last enqueued step
+  fk_batch* batch = nullptr;
+  cudaEvent_t batch_done = nullptr;
+  std::string err;
+};
+
+namespace fk {
+
+// Per-step arguments of the grid with f^n in buffer cur.
+StepArgs make_args(fk_grid* g, int cur);
+// Synchronise the grid's stream (after the batch that steps it, if any),
+// read the device scalars and re-base the buffer bookkeeping.
+fk_status sync_state(fk_grid* g, DevState* out);
+// Status for sticky device flags (FK_OK if none); sets the grid's message.
+fk_status flags_status(fk_grid* g, unsigned flags);
+
+}  // namespace fk

@@ -112,7 +112,7 @@ __host__ __device__ inline void tile_rows(const Geom& g, int nv1, int t, int* i0
   }
 }
 
-struct StepArgs {
+struct alignas(16) StepArgs {
   const void* f_in;
   void* f_out;
   int nx, nv1, nv2, pitch;  // pitch = row stride of f in elements (>= nv2)
@@ -123,6 +123,32 @@ struct StepArgs {
   Tables tab;
   Partials part;
   Geom geom;
+};
+
+// Scratch of the finalize kernel: per-plane in-block prefix of n, per-block
+// sums, and the counter that elects the last block (zero between launches).
+struct FinScratch {
+  double* pre;   // [nx]
+  double* bsum;  // [blocks]
+  double* blv;   // [blocks]
+  int* counter;  // [1]
+};
+
+// Outputs of the finalize kernel for one grid.
+struct FinOut {
+  double* ne;     // [nx] n_e of the new state
+  double* Ex;     // [nx] E_x
+  double* c1;     // [nx] v1-Courant numbers for the next step
+  float* c1_32;   // [nx] the same rounded to FP32
+  double* hist;   // [hist_cap][FK_HISTORY_COLS] history ring
+  FinScratch fs;
+};
+
+// One grid of a batch: the step kernel's arguments (with the batch's
+// x-chunking) and the finalize kernel's outputs.
+struct BatchInst {
+  StepArgs a;
+  FinOut o;
 };
 
 // Launchers (return the launch error).
@@ -141,14 +167,16 @@ cudaError_t launch_step_stream(const StepArgs& a, int precision, cudaStream_t s)
 int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per_block);
 size_t stream_smem_bytes(int precision, int stage_elems, int pitch);
 int stream_ctas_per_sm(int precision, size_t smem_bytes);
-// Scratch of the finalize kernel: per-plane in-block prefix of n, per-block
-// sums, and the counter that elects the last block (zero between launches).
-struct FinScratch {
-  double* pre;   // [nx]
-  double* bsum;  // [blocks]
-  double* blv;   // [blocks]
-  int* counter;  // [1]
-};
+// Batched streaming step: CTA b runs unit units[b] = (grid index into inst,
+// tile + n_tiles * chunk of that grid); smem_bytes >= every grid's
+// stream_smem_bytes.  padded: some grid has pitch > nv2.
+cudaError_t launch_step_stream_batch(const BatchInst* inst, const int2* units, int n_units,
+                                     int precision, bool padded, size_t smem_bytes,
+                                     cudaStream_t s);
+// Batched finalize (step mode): block b finalizes block blocks[b].y of grid
+// blocks[b].x; every grid's blocks 0 .. finalize_blocks(nx) - 1 appear once.
+cudaError_t launch_finalize_batch(const BatchInst* inst, const int2* blocks, int n_blocks,
+                                  cudaStream_t s);
 int finalize_blocks(int nx);
 cudaError_t launch_finalize(const StepArgs& a, double* ne, double* Ex, double* c1,
                             float* c1_32, double* hist, const FinScratch& fs, int mode,

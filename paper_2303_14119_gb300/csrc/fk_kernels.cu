@@ -306,9 +306,15 @@ cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cuda
 constexpr int kFinThreads = 128;
 constexpr int kFinMaxBlocks = 64;  // nx <= 8192
 
-__global__ void __launch_bounds__(kFinThreads)
-finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, double* hist,
-                FinScratch fs, int mode) {
+// Block blk of nblk finalizing one grid.
+__device__ __forceinline__ void finalize_body(const StepArgs& a, const FinOut& o, const int blk,
+                                              const int nblk, const int mode) {
+  double* const ne = o.ne;
+  double* const Ex = o.Ex;
+  double* const c1 = o.c1;
+  float* const c1_32 = o.c1_32;
+  double* const hist = o.hist;
+  const FinScratch& fs = o.fs;
   __shared__ double sh[32];
   __shared__ double wscan[kFinThreads / 32];
   __shared__ int s_last;
@@ -319,7 +325,7 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, do
   if (mode == kModeStep && st->flags) return;
   const int nx = a.nx, nu = a.part.nu;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int k = blockIdx.x * kFinThreads + t;
+  const int k = blk * kFinThreads + t;
   // ---- phase A
   double nk = 0.0, lk = 0.0;
   if (k < nx) {
@@ -365,16 +371,16 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, do
   const double btot = block_sum<kFinThreads>(nk, sh);
   const double blv = block_sum<kFinThreads>(lk, sh);
   if (t == 0) {
-    fs.bsum[blockIdx.x] = btot;
-    fs.blv[blockIdx.x] = blv;
+    fs.bsum[blk] = btot;
+    fs.blv[blk] = blv;
     __threadfence();
-    s_last = atomicAdd(fs.counter, 1) == (int)gridDim.x - 1;
+    s_last = atomicAdd(fs.counter, 1) == nblk - 1;
   }
   __syncthreads();
   if (!s_last) return;
   // ---- phase B (last block)
   __threadfence();
-  const int nb = gridDim.x;
+  const int nb = nblk;
   if (w == 0) {
     // block totals and their exclusive prefix, wall-flux tile partials:
     // lane-strided loads, fixed shuffle trees (other blocks' results are
@@ -485,11 +491,37 @@ finalize_kernel(StepArgs a, double* ne, double* Ex, double* c1, float* c1_32, do
   }
 }
 
+__global__ void __launch_bounds__(kFinThreads)
+finalize_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ FinOut o, int mode) {
+  finalize_body(a, o, blockIdx.x, gridDim.x, mode);
+}
+
+// Many grids in one launch (step mode): block b is block blocks[b].y of grid
+// blocks[b].x; each grid elects its own last block with its own counter.
+__global__ void __launch_bounds__(kFinThreads)
+finalize_batch_kernel(const BatchInst* __restrict__ inst, const int2* __restrict__ blocks) {
+  __shared__ BatchInst bi;
+  const int2 m = blocks[blockIdx.x];
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(inst + m.x);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&bi);
+  for (int w = threadIdx.x; w < (int)(sizeof(BatchInst) / 8); w += blockDim.x) dst[w] = src[w];
+  __syncthreads();
+  finalize_body(bi.a, bi.o, m.y, (bi.a.nx + kFinThreads - 1) / kFinThreads, kModeStep);
+}
+
 cudaError_t launch_finalize(const StepArgs& a, double* ne, double* Ex, double* c1,
                             float* c1_32, double* hist, const FinScratch& fs, int mode,
                             cudaStream_t s) {
   const int nb = (a.nx + kFinThreads - 1) / kFinThreads;
-  finalize_kernel<<<nb, kFinThreads, 0, s>>>(a, ne, Ex, c1, c1_32, hist, fs, mode);
+  const FinOut o{ne, Ex, c1, c1_32, hist, fs};
+  finalize_kernel<<<nb, kFinThreads, 0, s>>>(a, o, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batch(const BatchInst* inst, const int2* blocks, int n_blocks,
+                                  cudaStream_t s) {
+  if (n_blocks <= 0) return cudaSuccess;
+  finalize_batch_kernel<<<n_blocks, kFinThreads, 0, s>>>(inst, blocks);
   return cudaGetLastError();
 }
 

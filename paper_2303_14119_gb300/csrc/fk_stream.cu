@@ -127,9 +127,15 @@ constexpr int kMaxTileRows = 64;  // also bounds the per-stage diagonal table
 // of every tile row [kStages][kMaxTileRows] double
 // ... plus, for FP32 grids, the separable source factors of the tile rows
 // [kMaxTileRows] and of the row cells [pitch] (float)
+// The dynamic shared memory of both kernels starts with a slot for the
+// unit's StepArgs (filled by the batched kernel), so that one tile plan fits
+// a grid stepped alone or in a batch.
+constexpr int kArgsBytes = 256;
+static_assert(sizeof(StepArgs) <= kArgsBytes && sizeof(StepArgs) % 8 == 0,
+              "StepArgs must fit its shared-memory slot");
 template <typename T>
 __host__ __device__ constexpr size_t tail_bytes(int pitch) {
-  return 2 * kStages * sizeof(uint64_t) + kStages * kWarps * kWs * sizeof(double) +
+  return kArgsBytes + 2 * kStages * sizeof(uint64_t) + kStages * kWarps * kWs * sizeof(double) +
          (sizeof(T) == 8 ? kStages * kMaxTileRows * sizeof(double)
                          : ((size_t)(kMaxTileRows + pitch) * sizeof(float) + 15) / 16 * 16) +
          16;
@@ -196,11 +202,13 @@ __device__ __noinline__ void wall_terms(const T* oplane, const double* v1tab,
   out3[2] = vac;
 }
 
+// One unit (tile t, chunk) of a grid; smem is the CTA's dynamic shared
+// memory past the argument slot.
 template <typename T, bool PADDED>
-__global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
+__device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, const int chunk,
+                                            unsigned char* smem) {
   constexpr int VEC = Vec<T>::N;
   constexpr int M = kVecPerThread;
-  extern __shared__ __align__(128) unsigned char smem[];
   const Geom& gm = a.geom;
   const size_t sbytes = stage_bytes<T>(gm.stage_elems);
   unsigned char* stage_base = smem;
@@ -217,7 +225,6 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = gm.n_tiles;
-  const int t = blockIdx.x % nt, chunk = blockIdx.x / nt;
   const int nx = a.nx, nv1 = a.nv1, nv2 = a.nv2, pitch = a.pitch;
   int i0, i1, dir;
   tile_rows(gm, nv1, t, &i0, &i1, &dir);
@@ -535,6 +542,31 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(StepArgs a) {
   }
 }
 
+// One grid: CTA b runs tile b % n_tiles of chunk b / n_tiles.
+template <typename T, bool PADDED>
+__global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(const __grid_constant__ StepArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int nt = a.geom.n_tiles;
+  stream_unit<T, PADDED>(a, blockIdx.x % nt, blockIdx.x / nt, smem + kArgsBytes);
+}
+
+// Many grids in one launch: CTA b copies the arguments of grid units[b].x
+// into the slot at the start of its shared memory and runs that grid's unit
+// units[b].y = tile + n_tiles * chunk.
+template <typename T, bool PADDED>
+__global__ void __launch_bounds__(kBlock, 2)
+step_stream_batch_kernel(const BatchInst* __restrict__ inst, const int2* __restrict__ units) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int2 u = units[blockIdx.x];
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&inst[u.x].a);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(smem);
+  for (int w = threadIdx.x; w < (int)(sizeof(StepArgs) / 8); w += blockDim.x) dst[w] = src[w];
+  __syncthreads();
+  const StepArgs& a = *reinterpret_cast<const StepArgs*>(smem);
+  const int nt = a.geom.n_tiles;
+  stream_unit<T, PADDED>(a, u.y % nt, u.y / nt, smem + kArgsBytes);
+}
+
 }  // namespace
 
 int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per_block) {
@@ -560,32 +592,39 @@ size_t stream_smem_bytes(int precision, int stage_elems, int pitch) {
   return kStages * stage_bytes<double>(stage_elems) + tail_bytes<double>(pitch);
 }
 
+namespace {
+// allow the device's largest opt-in shared memory for kernel k and ask how
+// many CTAs of smem_bytes fit on an SM
+template <typename K>
+cudaError_t fit_kernel(K k, int optin, size_t smem_bytes, int* best) {
+  int n = 0;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kBlock, smem_bytes);
+  if (e == cudaSuccess && n < *best) *best = n;
+  return e;
+}
+template <typename T>
+int ctas_per_sm(int optin, size_t smem_bytes) {
+  int best = 1 << 30;
+  cudaError_t e = fit_kernel(step_stream_kernel<T, false>, optin, smem_bytes, &best);
+  if (e == cudaSuccess) e = fit_kernel(step_stream_kernel<T, true>, optin, smem_bytes, &best);
+  if (e == cudaSuccess) e = fit_kernel(step_stream_batch_kernel<T, false>, optin, smem_bytes, &best);
+  if (e == cudaSuccess) e = fit_kernel(step_stream_batch_kernel<T, true>, optin, smem_bytes, &best);
+  return e == cudaSuccess ? best : 0;
+}
+}  // namespace
+
 int stream_ctas_per_sm(int precision, size_t smem_bytes) {
-  // the attribute is per kernel, shared by every grid: allow the device's
-  // largest opt-in size once, and ask the occupancy of this grid's size
-  int dev = 0, optin = 0, n = 0;
+  // the attribute is per kernel, shared by every grid and batch: allow the
+  // device's largest opt-in size once, and ask the occupancy of this size
+  // (the smallest over the single-grid and batched variants)
+  int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return 0;
   if (smem_bytes > (size_t)optin) return 0;
-  cudaError_t e;
-  void (*kern[2])(StepArgs);
-  if (precision == FK_F32) {
-    kern[0] = step_stream_kernel<float, false>;
-    kern[1] = step_stream_kernel<float, true>;
-  } else {
-    kern[0] = step_stream_kernel<double, false>;
-    kern[1] = step_stream_kernel<double, true>;
-  }
-  int best = 1 << 30;
-  for (int v = 0; v < 2; v++) {
-    e = cudaFuncSetAttribute(kern[v], cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern[v], kBlock, smem_bytes);
-    if (e != cudaSuccess) return 0;
-    best = n < best ? n : best;
-  }
-  return best;
+  return precision == FK_F32 ? ctas_per_sm<float>(optin, smem_bytes)
+                             : ctas_per_sm<double>(optin, smem_bytes);
 }
 
 cudaError_t launch_step_stream(const StepArgs& a, int precision, cudaStream_t s) {
@@ -602,6 +641,24 @@ cudaError_t launch_step_stream(const StepArgs& a, int precision, cudaStream_t s)
       step_stream_kernel<double, true><<<grid, kBlock, smem, s>>>(a);
     else
       step_stream_kernel<double, false><<<grid, kBlock, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_stream_batch(const BatchInst* inst, const int2* units, int n_units,
+                                     int precision, bool padded, size_t smem_bytes,
+                                     cudaStream_t s) {
+  if (n_units <= 0) return cudaSuccess;
+  if (precision == FK_F32) {
+    if (padded)
+      step_stream_batch_kernel<float, true><<<n_units, kBlock, smem_bytes, s>>>(inst, units);
+    else
+      step_stream_batch_kernel<float, false><<<n_units, kBlock, smem_bytes, s>>>(inst, units);
+  } else {
+    if (padded)
+      step_stream_batch_kernel<double, true><<<n_units, kBlock, smem_bytes, s>>>(inst, units);
+    else
+      step_stream_batch_kernel<double, false><<<n_units, kBlock, smem_bytes, s>>>(inst, units);
   }
   return cudaGetLastError();
 }

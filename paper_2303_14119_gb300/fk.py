@@ -82,6 +82,16 @@ def load(build_if_missing: bool = True):
         "fk_grid_info": [P, dp],
         "fk_set_kernel_timing": [P, I],
         "fk_kernel_timing": [P, i64p, dp],
+        "fk_batch_create": [C.POINTER(P), C.c_int32, P, C.POINTER(P)],
+        "fk_batch_destroy": [P],
+        "fk_batch_step": [P, I64],
+        "fk_batch_sync": [P, C.POINTER(C.c_int32)],
+        "fk_batch_autotune": [P, C.c_int32, i64p],
+        "fk_batch_get_chunks": [P, C.POINTER(C.c_int32)],
+        "fk_batch_set_chunks": [P, C.POINTER(C.c_int32)],
+        "fk_batch_info": [P, dp],
+        "fk_batch_set_kernel_timing": [P, I],
+        "fk_batch_kernel_timing": [P, i64p, dp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -89,6 +99,8 @@ def load(build_if_missing: bool = True):
         fn.argtypes = args
     lib.fk_last_error.restype = C.c_char_p
     lib.fk_last_error.argtypes = [P]
+    lib.fk_batch_last_error.restype = C.c_char_p
+    lib.fk_batch_last_error.argtypes = [P]
     _lib = lib
     return lib
 
@@ -319,6 +331,132 @@ class Grid:
 
     def kernel_timing(self):
         return fk_kernel_timing(self.h)
+
+
+# --- batches ---------------------------------------------------------------
+FK_BATCH_INFO_LEN = 8
+
+
+def _bcheck(status, what, handle=None):
+    if status != FK_OK:
+        msg = load().fk_batch_last_error(handle).decode(errors="replace")
+        raise FkError(status, what, msg)
+
+
+def fk_batch_create(grids, stream=None):
+    """grids: sequence of grid handles (ints from fk_create_grid)."""
+    n = len(grids)
+    arr = (C.c_void_p * max(n, 1))(*[C.c_void_p(g) for g in grids])
+    h = C.c_void_p()
+    st = load().fk_batch_create(arr, int(n), C.c_void_p(stream) if stream else None, C.byref(h))
+    _bcheck(st, "fk_batch_create")
+    return h.value
+
+
+def fk_batch_destroy(b):
+    _bcheck(load().fk_batch_destroy(b), "fk_batch_destroy", b)
+
+
+def fk_batch_step(b, n=1):
+    _bcheck(load().fk_batch_step(b, int(n)), "fk_batch_step", b)
+
+
+def fk_batch_sync(b, n):
+    """Per-grid statuses (list of ints); never raises for a grid's sticky
+    device error (the list reports it)."""
+    out = (C.c_int32 * n)()
+    st = load().fk_batch_sync(b, out)
+    if st in (FK_EINVAL, FK_ECUDA, FK_ENOMEM):
+        _bcheck(st, "fk_batch_sync", b)
+    return list(out)
+
+
+def fk_batch_autotune(b, steps_per_trial=2):
+    taken = C.c_int64()
+    _bcheck(load().fk_batch_autotune(b, int(steps_per_trial), C.byref(taken)),
+            "fk_batch_autotune", b)
+    return taken.value
+
+
+def fk_batch_get_chunks(b, n):
+    out = (C.c_int32 * n)()
+    _bcheck(load().fk_batch_get_chunks(b, out), "fk_batch_get_chunks", b)
+    return list(out)
+
+
+def fk_batch_set_chunks(b, chunk_len):
+    arr = (C.c_int32 * len(chunk_len))(*[int(c) for c in chunk_len])
+    _bcheck(load().fk_batch_set_chunks(b, arr), "fk_batch_set_chunks", b)
+
+
+def fk_batch_info(b):
+    out = np.empty(FK_BATCH_INFO_LEN)
+    _bcheck(load().fk_batch_info(b, _dp(out)), "fk_batch_info", b)
+    return dict(grids=int(out[0]), units=int(out[1]), finalize_blocks=int(out[2]),
+                smem_bytes=int(out[3]), ctas_per_sm=int(out[4]), cells=float(out[5]),
+                buckets=int(out[6]), steps=int(out[7]))
+
+
+def fk_batch_set_kernel_timing(b, enabled):
+    _bcheck(load().fk_batch_set_kernel_timing(b, int(bool(enabled))),
+            "fk_batch_set_kernel_timing", b)
+
+
+def fk_batch_kernel_timing(b):
+    n = C.c_int64()
+    ms = np.empty(1)
+    _bcheck(load().fk_batch_kernel_timing(b, C.byref(n), _dp(ms)), "fk_batch_kernel_timing", b)
+    return n.value, float(ms[0])
+
+
+def fk_batch_last_error(b=None):
+    return load().fk_batch_last_error(b).decode(errors="replace")
+
+
+class Batch:
+    """Owning handle around one ``fk_batch`` over existing ``Grid`` objects
+    (which must outlive it)."""
+
+    def __init__(self, grids, stream=None):
+        self.grids = list(grids)
+        self.h = fk_batch_create([g.h for g in self.grids], stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fk_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, n=1):
+        fk_batch_step(self.h, n)
+
+    def sync(self):
+        return fk_batch_sync(self.h, len(self.grids))
+
+    def autotune(self, steps_per_trial=2):
+        return fk_batch_autotune(self.h, steps_per_trial)
+
+    def chunks(self):
+        return fk_batch_get_chunks(self.h, len(self.grids))
+
+    def set_chunks(self, chunk_len):
+        fk_batch_set_chunks(self.h, chunk_len)
+
+    def info(self):
+        return fk_batch_info(self.h)
+
+    def set_kernel_timing(self, enabled):
+        fk_batch_set_kernel_timing(self.h, enabled)
+
+    def kernel_timing(self):
+        return fk_batch_kernel_timing(self.h)
 
 
 FK_NOALLOC_MAX_PARTIALS = 131072

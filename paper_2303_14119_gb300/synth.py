@@ -80,4 +80,29 @@ WORKLOADS = {
     # mixed precision 2048 x 384 x 384 and its 4x-coarsened copy
     "large_2048x384x384": dict(BASE, nx=2048, nv1=384, nv2=384, Ey=-2e6, steps=10000),
     "coarse_512x96x96": dict(BASE, nx=512, nv1=96, nv2=96, Ey=-2e6, steps=10000),
+    # parameter sweep: 256 independent instances of uneven size, each run
+    # 5000 steps, every size and parameter drawn from one seed (sweep_instances)
+    "sweep_256": dict(BASE, sweep=256, steps=5000, seed=2023),
 }
+
+# Offset of the sweep's draws in the SplitMix64 stream (far from the cell
+# indices the distributions use).
+_SWEEP_OFFSET = 1 << 60
+
+
+def sweep_instances(n: int = 256, seed: int = 2023):
+    """n parameter-sweep instances drawn from one seed: nx uniform in
+    {128..512}, nv1 = nv2 uniform in {64..192}, applied field log-uniform in
+    [3e5, 5e6] V/m (E_y = -|E|), delta_max uniform in [2, 4], A_max uniform in
+    [250, 600] eV, emission temperature T_se uniform in [1, 5] eV; the rest
+    (spans, CFL, injection, noise) as BASE, noise seed seed + 1 + index."""
+    u = uniform(seed, 6 * n, offset=_SWEEP_OFFSET).reshape(n, 6)
+    out = []
+    for q in range(n):
+        e = float(np.exp(np.log(3e5) + u[q, 2] * (np.log(5e6) - np.log(3e5))))
+        nv = 64 + int(u[q, 1] * 129)
+        out.append(dict(BASE, nx=128 + int(u[q, 0] * 385), nv1=nv, nv2=nv, Ey=-e,
+                        delta_max=2.0 + 2.0 * float(u[q, 3]),
+                        A_max=250.0 + 350.0 * float(u[q, 4]),
+                        T_se=1.0 + 4.0 * float(u[q, 5]), seed=seed + 1 + q))
+    return out

@@ -68,3 +68,29 @@ def test_null_arguments():
     assert lib.fk_destroy_grid(None) == fk.FK_OK
     assert lib.fk_step(None, 1) == fk.FK_EINVAL
     assert lib.fk_sync(None) == fk.FK_EINVAL
+
+
+def test_batch_create_rejects_bad_arguments_on_host():
+    lib = fk.load()
+    h = C.c_void_p()
+    assert lib.fk_batch_create(None, 1, None, C.byref(h)) == fk.FK_EINVAL
+    arr = (C.c_void_p * 2)(None, None)
+    assert lib.fk_batch_create(arr, 0, None, C.byref(h)) == fk.FK_EINVAL
+    assert lib.fk_batch_create(arr, -3, None, C.byref(h)) == fk.FK_EINVAL
+    assert lib.fk_batch_create(arr, 2, None, C.byref(h)) == fk.FK_EINVAL
+    assert h.value is None
+    assert "NULL" in lib.fk_batch_last_error(None).decode()
+
+
+def test_batch_calls_reject_null_handles():
+    lib = fk.load()
+    n = C.c_int64()
+    d = C.c_double()
+    assert lib.fk_batch_step(None, 1) == fk.FK_EINVAL
+    assert lib.fk_batch_sync(None, None) == fk.FK_EINVAL
+    assert lib.fk_batch_autotune(None, 1, C.byref(n)) == fk.FK_EINVAL
+    assert lib.fk_batch_get_chunks(None, None) == fk.FK_EINVAL
+    assert lib.fk_batch_set_chunks(None, None) == fk.FK_EINVAL
+    assert lib.fk_batch_info(None, C.byref(d)) == fk.FK_EINVAL
+    assert lib.fk_batch_kernel_timing(None, C.byref(n), C.byref(d)) == fk.FK_EINVAL
+    assert lib.fk_batch_destroy(None) == fk.FK_OK
