@@ -178,7 +178,7 @@ void free_grid(fk_grid* g) {
     if (g->graph[p]) cudaGraphExecDestroy(g->graph[p]);
   void* ptrs[] = {g->d_prm, g->d_st, g->d_f[0], g->d_f[1], g->tab.v1, g->tab.cx,
                   g->tab.cx32, g->tab.delta, g->tab.gse, g->tab.src, g->tab.src32,
-                  g->tab.gfe_raw, g->tab.srow32, g->tab.scol32, g->part.n, g->part.lv,
+                  g->tab.gfe_raw, g->tab.srow32, g->tab.scol32, g->tab.tsum, g->part.n, g->part.lv,
                   g->part.pe, g->part.see,
                   g->part.vac, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist,
                   g->d_stage, g->fin.pre, g->fin.bsum, g->fin.blv, g->fin.counter};
@@ -382,6 +382,7 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   CREATE_CUDA(dalloc(&g->tab.gfe_raw, nv * sizeof(double)));
   CREATE_CUDA(dalloc(&g->tab.srow32, d.nv1 * sizeof(float)));
   CREATE_CUDA(dalloc(&g->tab.scol32, g->pitch * sizeof(float)));
+  CREATE_CUDA(dalloc(&g->tab.tsum, tables_scratch_doubles() * sizeof(double)));
   CREATE_CUDA(dalloc(&g->part.n, nparts * sizeof(double)));
   CREATE_CUDA(dalloc(&g->part.lv, nparts * sizeof(double)));
   CREATE_CUDA(dalloc(&g->part.pe, g->part.nu * sizeof(double)));

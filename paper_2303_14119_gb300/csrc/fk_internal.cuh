@@ -81,6 +81,7 @@ struct Tables {
   // in v2, normalised per factor): src(i, j) = srow32[i] * scol32[j]
   float* srow32;  // [nv1] dt (J/e)/W times the normalised v1 factor
   float* scol32;  // [pitch] normalised v2 factor, zero for v2 <= 0 and padding
+  double* tsum;   // [tables_scratch_doubles()] normalisation partials and norms
 };
 
 // Work decomposition shared by the step kernels and the finalize kernel.
@@ -157,6 +158,7 @@ cudaError_t launch_tables(const Tables& t, int nv1, int nv2, int pitch,
                           double dt, double dx, double delta_max, double A_max,
                           double k_s, double T_se, double T_fe, double J_over_eW,
                           cudaStream_t s);
+int tables_scratch_doubles();
 // Direct-load step (and moments-only evaluation): one block per (plane, tile).
 cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cudaStream_t s);
 // Streaming step: one CTA per (tile, chunk), bulk-async staged planes.

@@ -42,12 +42,19 @@ __device__ double block_max(double v, double* sh) {
 }
 
 // ---------------------------------------------------------------------------
-// Tables (one block, deterministic sums).
-//  delta: SEE yield of Eqs. 8-11 where v1 < 0.
-//  gse:   Eq. 15 shape on v1 > 0, normalised to unit flux sum v1 g dv1 dv2.
-//  src:   dt (J/e)/W times the Eq. 7 shape (Maxwellian in v1, half
-//         Maxwellian on v2 > 0), normalised to unit density.
-constexpr int kTabThreads = 1024;
+// Tables, in three launches with deterministic sums:
+//  1. kTabBlocks blocks over the cells: delta (SEE yield of Eqs. 8-11 where
+//     v1 < 0), the raw Eq. 15 emission shape and the raw Eq. 7 source shape,
+//     and per-block partial sums of their normalisations;
+//  2. one block: the partials folded in block order, the 1D tables (v1, c_x)
+//     and the separable source factors;
+//  3. kTabBlocks blocks: gse scaled to unit flux sum v1 g dv1 dv2, src = dt
+//     (J/e)/W times the source shape scaled to unit density.
+// The per-cell special functions run in FP64 on every SM (GB300's FP64 rate
+// per SM is small, so one block would take milliseconds).
+constexpr int kTabBlocks = 256;
+constexpr int kTabThreads = 256;
+constexpr int kTabFoldThreads = 1024;
 
 // Cell centre lo + (i + 1/2) h with separate roundings (no fused multiply-
 // add), so the velocity grid is bit-identical to a host computation.
@@ -56,14 +63,13 @@ __device__ __forceinline__ double cell_centre(double lo, int i, double h) {
 }
 
 __global__ void __launch_bounds__(kTabThreads)
-tables_kernel(Tables t, int nv1, int nv2, int pitch, double v1_min, double v2_min, double dv1,
-              double dv2, double dt, double dx, double dmax, double amax, double ks,
-              double Tse, double Tfe, double j_over_ew) {
+tables_cells_kernel(Tables t, int nv1, int nv2, int pitch, double v1_min, double v2_min,
+                    double dv1, double dv2, double dmax, double amax, double ks, double Tse,
+                    double Tfe) {
   __shared__ double sh[32];
-  __shared__ double norms[2];
   double s_se = 0.0, s_fe = 0.0;
   const int ncell = nv1 * pitch;
-  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+  for (int c = blockIdx.x * kTabThreads + threadIdx.x; c < ncell; c += kTabBlocks * kTabThreads) {
     const int i = c / pitch, j = c - (c / pitch) * pitch;
     double d = 0.0, gs = 0.0, gf = 0.0;
     if (j < nv2) {
@@ -88,19 +94,26 @@ tables_kernel(Tables t, int nv1, int nv2, int pitch, double v1_min, double v2_mi
     t.gfe_raw[c] = gf;
   }
   s_se = block_sum<kTabThreads>(s_se, sh);
+  __syncthreads();
   s_fe = block_sum<kTabThreads>(s_fe, sh);
   if (threadIdx.x == 0) {
-    norms[0] = s_se * dv1 * dv2;
-    norms[1] = s_fe * dv1 * dv2;
+    t.tsum[2 * blockIdx.x] = s_se;
+    t.tsum[2 * blockIdx.x + 1] = s_fe;
   }
+}
+
+__global__ void __launch_bounds__(kTabFoldThreads)
+tables_fold_kernel(Tables t, int nv1, int nv2, int pitch, double v1_min, double v2_min,
+                   double dv1, double dv2, double dt, double dx, double Tfe, double j_over_ew) {
+  __shared__ double sh[32];
+  __shared__ double norms[4];
+  // block partials in block order (one per thread, kTabBlocks <= threads)
+  const int b = threadIdx.x;
+  double s_se = b < kTabBlocks ? t.tsum[2 * b] : 0.0;
+  double s_fe = b < kTabBlocks ? t.tsum[2 * b + 1] : 0.0;
+  s_se = block_sum<kTabFoldThreads>(s_se, sh);
   __syncthreads();
-  const double nse = norms[0], nfe = norms[1];
-  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-    t.gse[c] = nse > 0.0 ? t.gse[c] / nse : 0.0;
-    const double s = nfe > 0.0 ? dt * j_over_ew * (t.gfe_raw[c] / nfe) : 0.0;
-    t.src[c] = s;
-    t.src32[c] = (float)s;
-  }
+  s_fe = block_sum<kTabFoldThreads>(s_fe, sh);
   for (int i = threadIdx.x; i < nv1; i += blockDim.x) {
     const double v1 = cell_centre(v1_min, i, dv1);
     t.v1[i] = v1;
@@ -117,15 +130,20 @@ tables_kernel(Tables t, int nv1, int nv2, int pitch, double v1_min, double v2_mi
     const double v2 = cell_centre(v2_min, j, dv2);
     s2 += v2 > 0.0 ? exp(-kMe * v2 * v2 / (2.0 * Tfe * kQe)) : 0.0;
   }
-  s1 = block_sum<kTabThreads>(s1, sh);
-  s2 = block_sum<kTabThreads>(s2, sh);
   __syncthreads();
+  s1 = block_sum<kTabFoldThreads>(s1, sh);
+  __syncthreads();
+  s2 = block_sum<kTabFoldThreads>(s2, sh);
   if (threadIdx.x == 0) {
-    norms[0] = s1 * dv1;
-    norms[1] = s2 * dv2;
+    norms[0] = s_se * dv1 * dv2;
+    norms[1] = s_fe * dv1 * dv2;
+    norms[2] = s1 * dv1;
+    norms[3] = s2 * dv2;
+    t.tsum[2 * kTabBlocks] = norms[0];
+    t.tsum[2 * kTabBlocks + 1] = norms[1];
   }
   __syncthreads();
-  const double n1 = norms[0], n2 = norms[1];
+  const double nfe = norms[1], n1 = norms[2], n2 = norms[3];
   const bool on = nfe > 0.0 && n1 > 0.0 && n2 > 0.0;
   for (int i = threadIdx.x; i < nv1; i += blockDim.x) {
     const double v1 = cell_centre(v1_min, i, dv1);
@@ -141,12 +159,28 @@ tables_kernel(Tables t, int nv1, int nv2, int pitch, double v1_min, double v2_mi
   }
 }
 
+__global__ void __launch_bounds__(kTabThreads)
+tables_scale_kernel(Tables t, int ncell, double dt, double j_over_ew) {
+  const double nse = t.tsum[2 * kTabBlocks], nfe = t.tsum[2 * kTabBlocks + 1];
+  for (int c = blockIdx.x * kTabThreads + threadIdx.x; c < ncell; c += kTabBlocks * kTabThreads) {
+    t.gse[c] = nse > 0.0 ? t.gse[c] / nse : 0.0;
+    const double s = nfe > 0.0 ? dt * j_over_ew * (t.gfe_raw[c] / nfe) : 0.0;
+    t.src[c] = s;
+    t.src32[c] = (float)s;
+  }
+}
+
+int tables_scratch_doubles() { return 2 * kTabBlocks + 2; }
+
 cudaError_t launch_tables(const Tables& t, int nv1, int nv2, int pitch, double v1_min,
                           double v2_min, double dv1, double dv2, double dt, double dx,
                           double delta_max, double A_max, double k_s, double T_se,
                           double T_fe, double j_over_ew, cudaStream_t s) {
-  tables_kernel<<<1, kTabThreads, 0, s>>>(t, nv1, nv2, pitch, v1_min, v2_min, dv1, dv2, dt, dx,
-                                          delta_max, A_max, k_s, T_se, T_fe, j_over_ew);
+  tables_cells_kernel<<<kTabBlocks, kTabThreads, 0, s>>>(t, nv1, nv2, pitch, v1_min, v2_min, dv1,
+                                                         dv2, delta_max, A_max, k_s, T_se, T_fe);
+  tables_fold_kernel<<<1, kTabFoldThreads, 0, s>>>(t, nv1, nv2, pitch, v1_min, v2_min, dv1, dv2,
+                                                   dt, dx, T_fe, j_over_ew);
+  tables_scale_kernel<<<kTabBlocks, kTabThreads, 0, s>>>(t, nv1 * pitch, dt, j_over_ew);
   return cudaGetLastError();
 }
 

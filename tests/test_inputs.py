@@ -32,5 +32,28 @@ def test_initial_f_scale_and_shape():
 
 def test_workloads_are_consistent():
     for name, w in synth.WORKLOADS.items():
+        if "sweep" in w:
+            continue
         assert w["nx"] >= 2 and w["Ey"] < 0
         assert f"{w['nx']}x{w['nv1']}x{w['nv2']}" in name
+
+
+def test_sweep_instances_ranges_and_determinism():
+    w = synth.WORKLOADS["sweep_256"]
+    ins = synth.sweep_instances(w["sweep"], w["seed"])
+    assert len(ins) == 256
+    assert ins == synth.sweep_instances(w["sweep"], w["seed"])
+    assert ins != synth.sweep_instances(w["sweep"], w["seed"] + 1)
+    nx = np.array([p["nx"] for p in ins])
+    nv = np.array([p["nv1"] for p in ins])
+    e = np.array([-p["Ey"] for p in ins])
+    assert nx.min() >= 128 and nx.max() <= 512 and len(set(nx)) > 100
+    assert nv.min() >= 64 and nv.max() <= 192 and all(p["nv1"] == p["nv2"] for p in ins)
+    assert e.min() >= 3e5 and e.max() <= 5e6
+    # log-uniform: about half the draws lie below the geometric midpoint
+    frac_low = np.mean(np.log(e) < 0.5 * (np.log(3e5) + np.log(5e6)))
+    assert 0.4 < frac_low < 0.6
+    for key, lo, hi in (("delta_max", 2.0, 4.0), ("A_max", 250.0, 600.0), ("T_se", 1.0, 5.0)):
+        v = np.array([p[key] for p in ins])
+        assert v.min() >= lo and v.max() <= hi and v.std() > 0.2 * (hi - lo)
+    assert len({p["seed"] for p in ins}) == 256
