@@ -1,0 +1,219 @@
+// Dense layers of the surface-charge surrogate on the tensor cores:
+// C = A * B^T with bf16 A [M][K] and B [N][K] (both K-major), FP32
+// accumulation in tensor memory (tcgen05.mma, operands in shared memory),
+// and the epilogues the surrogate's training needs (bias, GELU and its
+// derivative, bf16 copies in both layouts).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "fk_internal.cuh"
+#include "fk_mlp.h"
+#include "fk_mlp_internal.cuh"
+#include "fk_tc.cuh"
+
+namespace fk {
+
+namespace {
+
+constexpr int kMTile = 128;   // rows per CTA (one MMA M)
+constexpr int kKChunk = 64;   // K staged per round (4 MMAs of K = 16)
+constexpr int kNMax = 256;    // columns per CTA (one MMA N)
+constexpr int kGemmThreads = 128;  // 4 warps: one per 32-lane slice of tensor memory
+constexpr int kCoreBytes = 128;    // one 8 x 16-byte core matrix
+// A tile: [kMTile/8 row groups][kKChunk/8 K groups] core matrices
+constexpr int kLboBytes = kCoreBytes;                        // next core matrix along K
+constexpr int kSboBytes = (kKChunk / 8) * kCoreBytes;        // next 8-row group
+constexpr int kATileBytes = kMTile * kKChunk * 2;            // 16 KB
+constexpr int kBTileBytes = kNMax * kKChunk * 2;             // 32 KB
+// dynamic shared memory per CTA: the two tiles, padded so that at most two
+// CTAs share an SM (2 x 256 tensor-memory columns = all 512)
+constexpr int kGemmSmem = 100 * 1024;
+static_assert(kATileBytes + kBTileBytes <= kGemmSmem, "GEMM tiles exceed the shared memory");
+
+__device__ __forceinline__ uint16_t f32_to_bf16(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+// GELU with the exact (erf) form and its derivative
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
+         z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// Copy rows [r0, r0 + rows) x K columns [k0, k0 + kKChunk) of a K-major bf16
+// matrix into the core-matrix layout; zeros outside [0, nrows) x [0, K).
+__device__ __forceinline__ void stage_tile(unsigned char* dst, const uint16_t* src, long long ld,
+                                           int r0, int rows, int nrows, int k0, int K) {
+  const int vecs = rows * (kKChunk / 8);
+  for (int v = threadIdx.x; v < vecs; v += kGemmThreads) {
+    const int r = v / (kKChunk / 8), kc = v - (v / (kKChunk / 8)) * (kKChunk / 8);
+    const int gr = r0 + r, gk = k0 + kc * 8;
+    uint4 val = make_uint4(0u, 0u, 0u, 0u);
+    if (gr < nrows && gk < K) val = *reinterpret_cast<const uint4*>(src + (long long)gr * ld + gk);
+    *reinterpret_cast<uint4*>(dst + ((r >> 3) * (kKChunk / 8) + kc) * kCoreBytes + (r & 7) * 16) = val;
+  }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kGemmThreads) gemm_tn_kernel(const __grid_constant__ GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + kATileBytes;
+  __shared__ uint64_t bar;
+  __shared__ uint32_t s_taddr;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kMTile;
+  const int N = g.N, Nt = (g.N + 15) / 16 * 16;
+  const uint32_t ncols = Nt <= 32 ? 32u : (Nt <= 64 ? 64u : (Nt <= 128 ? 128u : 256u));
+  if (warp == 0) {
+    tc::tmem_alloc(&s_taddr, ncols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    s_ok = 1;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = s_taddr;
+  const uint32_t idesc = tc::idesc_bf16_f32(kMTile, Nt);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int k0 = 0; k0 < g.K && ok; k0 += kKChunk) {
+    stage_tile(sA, g.A, g.lda, m0, kMTile, g.M, k0, g.K);
+    stage_tile(sB, g.B, g.ldb, 0, Nt, N, k0, g.K);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+      for (int kk = 0; kk < kKChunk / 16; kk++) {
+        // K step of 16 = two core matrices along K
+        const uint64_t ad = tc::smem_desc(a0 + kk * 2 * kLboBytes, kLboBytes, kSboBytes);
+        const uint64_t bd = tc::smem_desc(b0 + kk * 2 * kLboBytes, kLboBytes, kSboBytes);
+        tc::mma_bf16(taddr, ad, bd, idesc, (k0 > 0 || kk > 0) ? 1u : 0u);
+      }
+      tc::mma_commit(&bar);
+    }
+    // the MMAs have read the tiles (and written D) once the phase completes
+    ok = tc::mbar_wait(&bar, phase);
+    phase ^= 1;
+    tc::fence_after_sync();
+    if (!__syncthreads_and(ok)) ok = false;
+  }
+  if (ok) {
+    // epilogue: warp w holds rows m0 + 32 w + lane (tensor-memory lanes)
+    const int row = m0 + warp * 32 + lane;
+    const bool live = row < g.M;
+    for (int c0 = 0; c0 < Nt; c0 += 16) {
+      uint32_t r[16];
+      tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      tc::tmem_wait_ld();
+      if (!live) continue;
+#pragma unroll
+      for (int e = 0; e < 16; e++) {
+        const int col = c0 + e;
+        if (col >= N) break;
+        float v = __uint_as_float(r[e]);
+        if (EPI == kEpiF32) {
+          if (g.bias) v += g.bias[col];
+          g.C[(long long)row * g.ldc + col] = v;
+        } else if (EPI == kEpiBiasGelu) {
+          const float z = v + (g.bias ? g.bias[col] : 0.f);
+          g.C[(long long)row * g.ldc + col] = z;
+          const uint16_t h = row < g.m_valid ? f32_to_bf16(gelu(z)) : (uint16_t)0;
+          g.H[(long long)row * g.ldh + col] = h;
+          if (g.Ht) g.Ht[(long long)col * g.ldht + row] = h;
+        } else {  // kEpiGeluBack
+          const float d = row < g.m_valid ? v * gelu_grad(g.Zin[(long long)row * g.ldz + col]) : 0.f;
+          const uint16_t h = f32_to_bf16(d);
+          g.H[(long long)row * g.ldh + col] = h;
+          if (g.Ht) g.Ht[(long long)col * g.ldht + row] = h;
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(g.err, 1);
+    // a second bounded wait for MMAs still in flight before the memory is freed
+    tc::mbar_wait(&bar, phase ^ 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(taddr, ncols);
+  }
+}
+
+template <int EPI>
+cudaError_t launch_gemm_epi(const GemmArgs& g, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(gemm_tn_kernel<EPI>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  if (e != cudaSuccess) return e;
+  const int grid = (g.M + kMTile - 1) / kMTile;
+  gemm_tn_kernel<EPI><<<grid, kGemmThreads, kGemmSmem, s>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Shape rules checked on the host before any launch.
+const char* gemm_shape_error(const GemmArgs& g) {
+  if (g.M < 1 || g.N < 1 || g.K < 1) return "M, N and K must be >= 1";
+  if (g.N > kNMax) return "N must be <= 256";
+  if (g.K % 16) return "K must be a multiple of 16";
+  if (g.lda < g.K || g.ldb < g.K || g.lda % 8 || g.ldb % 8)
+    return "lda and ldb must be >= K and multiples of 8 (16-byte rows)";
+  if (((uintptr_t)g.A | (uintptr_t)g.B) & 15) return "A and B must be 16-byte aligned";
+  return nullptr;
+}
+
+cudaError_t launch_gemm(const GemmArgs& g, int epi, cudaStream_t s) {
+  if (epi == kEpiF32) return launch_gemm_epi<kEpiF32>(g, s);
+  if (epi == kEpiBiasGelu) return launch_gemm_epi<kEpiBiasGelu>(g, s);
+  return launch_gemm_epi<kEpiGeluBack>(g, s);
+}
+
+}  // namespace fk
+
+extern "C" fk_status fk_gemm_bf16_tn(const void* A, int64_t lda, const void* B, int64_t ldb,
+                                     float* C, int64_t ldc, int32_t M, int32_t N, int32_t K,
+                                     int32_t* err_dev, void* cuda_stream) {
+  fk::GemmArgs g{};
+  g.A = static_cast<const uint16_t*>(A);
+  g.B = static_cast<const uint16_t*>(B);
+  g.lda = lda;
+  g.ldb = ldb;
+  g.C = C;
+  g.ldc = ldc;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.m_valid = M;
+  g.err = err_dev;
+  if (!A || !B || !C || !err_dev) {
+    fk::set_thread_error("fk_gemm_bf16_tn: A, B, C and err must be device pointers");
+    return FK_EINVAL;
+  }
+  if (const char* why = fk::gemm_shape_error(g)) {
+    fk::set_thread_error((std::string("fk_gemm_bf16_tn: ") + why).c_str());
+    return FK_EINVAL;
+  }
+  if (ldc < N) {
+    fk::set_thread_error("fk_gemm_bf16_tn: ldc must be >= N");
+    return FK_EINVAL;
+  }
+  const cudaError_t e = fk::launch_gemm(g, fk::kEpiF32, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) {
+    fk::set_thread_error((std::string("fk_gemm_bf16_tn: ") + cudaGetErrorString(e)).c_str());
+    return FK_ECUDA;
+  }
+  return FK_OK;
+}

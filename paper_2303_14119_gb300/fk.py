@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
         "fk_batch_info": [P, dp],
         "fk_batch_set_kernel_timing": [P, I],
         "fk_batch_kernel_timing": [P, i64p, dp],
+        "fk_gemm_bf16_tn": [P, I64, P, I64, P, I64, C.c_int32, C.c_int32, C.c_int32, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -331,6 +332,16 @@ class Grid:
 
     def kernel_timing(self):
         return fk_kernel_timing(self.h)
+
+
+# --- tensor-core dense layer (include/fk_mlp.h) ---------------------------
+def fk_gemm_bf16_tn(A_ptr, lda, B_ptr, ldb, C_ptr, ldc, M, N, K, err_ptr, stream=None):
+    """C = A * B^T on the tensor cores; every pointer a raw device address
+    (e.g. ``tensor.data_ptr()``), A and B bf16, C FP32, err an int32."""
+    _check(load().fk_gemm_bf16_tn(C.c_void_p(A_ptr), int(lda), C.c_void_p(B_ptr), int(ldb),
+                                  C.c_void_p(C_ptr), int(ldc), int(M), int(N), int(K),
+                                  C.c_void_p(err_ptr), C.c_void_p(stream) if stream else None),
+           "fk_gemm_bf16_tn")
 
 
 # --- batches ---------------------------------------------------------------

@@ -1,0 +1,86 @@
+"""The surrogate's tensor-core dense layer (tcgen05) against exact products.
+
+bf16 x bf16 products are exact in FP32 and FP64; the kernel accumulates in
+FP32, so against an FP64 sum of the same bf16 values the error is FP32
+accumulation rounding: |err| <= K * 2^-24 * sum |a b| per element (a loose
+bound; the test uses it directly).  Small-integer inputs are exact.
+"""
+import numpy as np
+import pytest
+
+from paper_2303_14119_gb300 import fk
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fk.load()
+
+
+def gemm(A, B, N=None):
+    """A [M][K], B [N][K] bf16 CUDA tensors -> FP32 [M][N] via the kernel."""
+    M, K = A.shape
+    N = B.shape[0] if N is None else N
+    Cm = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    fk.fk_gemm_bf16_tn(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), Cm.data_ptr(),
+                       Cm.stride(0), M, N, K, err.data_ptr(),
+                       torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    return Cm.cpu()
+
+
+def test_tiny_integer_product_is_exact():
+    g = torch.Generator().manual_seed(1)
+    A = torch.randint(-4, 5, (128, 16), generator=g).to(torch.bfloat16)
+    B = torch.randint(-4, 5, (16, 16), generator=g).to(torch.bfloat16)
+    C = gemm(A.cuda(), B.cuda())
+    ref = A.double() @ B.double().T
+    assert torch.equal(C.double(), ref)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 16, 64), (300, 80, 208), (4096, 256, 256),
+                                   (256, 16, 4096), (1, 256, 16), (200, 65, 32)])
+def test_random_products_within_fp32_accumulation_bound(M, N, K):
+    g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
+    A = (torch.randn(M, K, generator=g)).to(torch.bfloat16)
+    B = (torch.randn(N, K, generator=g)).to(torch.bfloat16)
+    C = gemm(A.cuda(), B.cuda())
+    ref = A.double() @ B.double().T
+    bound = K * 2.0 ** -24 * (A.double().abs() @ B.double().abs().T) + 1e-30
+    assert torch.all((C.double() - ref).abs() <= bound)
+    # and far tighter than bf16 rounding of the output would be
+    assert (C.double() - ref).abs().max() < 1e-3 * ref.abs().max()
+
+
+def test_strided_operands_and_columns():
+    g = torch.Generator().manual_seed(5)
+    big_a = torch.randn(150, 96, generator=g).to(torch.bfloat16).cuda()
+    big_b = torch.randn(40, 104, generator=g).to(torch.bfloat16).cuda()
+    A = big_a[:, :48]   # lda 96, K = 48
+    B = big_b[:, :48]   # ldb 104
+    C = gemm(A, B)
+    ref = A.cpu().double() @ B.cpu().double().T
+    assert (C.double() - ref).abs().max() <= 48 * 2.0 ** -24 * (A.cpu().double().abs() @ B.cpu().double().abs().T).max()
+
+
+def test_bad_shapes_rejected_on_host():
+    A = torch.zeros(128, 24, dtype=torch.bfloat16, device="cuda")
+    B = torch.zeros(16, 24, dtype=torch.bfloat16, device="cuda")
+    C = torch.zeros(128, 16, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lib = fk.load()
+    import ctypes as Ct
+    args = lambda M, N, K, lda=24, ldb=24: (Ct.c_void_p(A.data_ptr()), lda, Ct.c_void_p(B.data_ptr()), ldb,
+                                            Ct.c_void_p(C.data_ptr()), 16, M, N, K,
+                                            Ct.c_void_p(err.data_ptr()), None)
+    assert lib.fk_gemm_bf16_tn(*args(128, 16, 24)) == fk.FK_EINVAL   # K not a multiple of 16
+    assert lib.fk_gemm_bf16_tn(*args(128, 300, 16)) == fk.FK_EINVAL  # N > 256
+    assert lib.fk_gemm_bf16_tn(*args(128, 16, 16, lda=12)) == fk.FK_EINVAL
+    assert lib.fk_gemm_bf16_tn(*args(0, 16, 16)) == fk.FK_EINVAL
