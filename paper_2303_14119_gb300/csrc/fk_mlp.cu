@@ -162,7 +162,147 @@ cudaError_t launch_gemm_epi(const GemmArgs& g, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+constexpr int kEwThreads = 256;
+
+__global__ void gather_kernel(const float* __restrict__ x_src, const float* __restrict__ t_src,
+                              const int* __restrict__ idx, int n, int bp, int n_in, int in_p,
+                              int n_out, int out_p, uint16_t* X, uint16_t* Xt, float* T) {
+  const long long e = (long long)blockIdx.x * kEwThreads + threadIdx.x;
+  if (e < (long long)bp * in_p) {
+    const int r = (int)(e / in_p), c = (int)(e - (e / in_p) * in_p);
+    const float v = (r < n && c < n_in) ? x_src[(long long)idx[r] * n_in + c] : 0.f;
+    const uint16_t h = f32_to_bf16(v);
+    X[(long long)r * in_p + c] = h;
+    Xt[(long long)c * bp + r] = h;
+  }
+  if (t_src && e < (long long)bp * out_p) {
+    const int r = (int)(e / out_p), c = (int)(e - (e / out_p) * out_p);
+    T[e] = (r < n && c < n_out) ? t_src[(long long)idx[r] * n_out + c] : 0.f;
+  }
+}
+
+__global__ void loss_grad_kernel(const float* __restrict__ Y, const float* __restrict__ T,
+                                 const float* __restrict__ w, int n, int bp, int out_p,
+                                 double inv_n, uint16_t* dY, uint16_t* dYt, double* loss_rows) {
+  const long long e = (long long)blockIdx.x * kEwThreads + threadIdx.x;
+  if (e < (long long)bp * out_p) {
+    const int r = (int)(e / out_p), c = (int)(e - (e / out_p) * out_p);
+    float d = 0.f;
+    if (r < n) d = (float)(2.0 * (double)w[c] * ((double)Y[e] - (double)T[e]) * inv_n);
+    const uint16_t h = f32_to_bf16(d);
+    dY[e] = h;
+    dYt[(long long)c * bp + r] = h;
+  }
+  if (e < n) {  // one thread per sample row: its weighted squared error
+    double acc = 0.0;
+    for (int c = 0; c < out_p; c++) {
+      const double dd = (double)Y[e * out_p + c] - (double)T[e * out_p + c];
+      acc += (double)w[c] * dd * dd;
+    }
+    loss_rows[e] = acc;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T block_reduce_sum(T v, T* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  T r = 0;
+  if (w == 0) {
+    r = l < (int)(blockDim.x >> 5) ? sh[l] : (T)0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  return r;  // thread 0
+}
+
+__global__ void row_sums_kernel(const uint16_t* __restrict__ M, long long ld, int n, float* out) {
+  __shared__ float sh[32];
+  const uint16_t* row = M + (long long)blockIdx.x * ld;
+  float acc = 0.f;
+  for (int c = threadIdx.x; c < n; c += kEwThreads) acc += __uint_as_float((uint32_t)row[c] << 16);
+  acc = block_reduce_sum(acc, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = acc;
+}
+
+__global__ void loss_reduce_kernel(const double* __restrict__ rows, int n, double scale,
+                                   double* acc) {
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (int r = threadIdx.x; r < n; r += kEwThreads) v += rows[r];
+  v = block_reduce_sum(v, sh);
+  if (threadIdx.x == 0) *acc += scale * v;
+}
+
+__global__ void adam_kernel(float* p, const float* __restrict__ g, float* m, float* v,
+                            long long count, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+  const long long e = (long long)blockIdx.x * kEwThreads + threadIdx.x;
+  if (e >= count) return;
+  const float gg = g[e];
+  const float mm = b1 * m[e] + (1.f - b1) * gg;
+  const float vv = b2 * v[e] + (1.f - b2) * gg * gg;
+  m[e] = mm;
+  v[e] = vv;
+  p[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+
+__global__ void pack_weights_kernel(const float* __restrict__ W, int N, int K, uint16_t* Wb,
+                                    uint16_t* Wt) {
+  const long long e = (long long)blockIdx.x * kEwThreads + threadIdx.x;
+  if (e >= (long long)N * K) return;
+  const int r = (int)(e / K), c = (int)(e - (e / K) * K);
+  const uint16_t h = f32_to_bf16(W[e]);
+  Wb[e] = h;
+  Wt[(long long)c * N + r] = h;
+}
+
+inline int ew_blocks(long long count) { return (int)((count + kEwThreads - 1) / kEwThreads); }
+
 }  // namespace
+
+cudaError_t launch_gather(const float* x_src, const float* t_src, const int* idx, int n, int bp,
+                          int n_in, int in_p, int n_out, int out_p, uint16_t* X, uint16_t* Xt,
+                          float* T, cudaStream_t s) {
+  const long long cnt = (long long)bp * (in_p > out_p ? in_p : out_p);
+  gather_kernel<<<ew_blocks(cnt), kEwThreads, 0, s>>>(x_src, t_src, idx, n, bp, n_in, in_p,
+                                                      n_out, out_p, X, Xt, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_grad(const float* Y, const float* T, const float* w, int n, int bp,
+                             int out_p, double inv_n, uint16_t* dY, uint16_t* dYt,
+                             double* loss_rows, cudaStream_t s) {
+  loss_grad_kernel<<<ew_blocks((long long)bp * out_p), kEwThreads, 0, s>>>(
+      Y, T, w, n, bp, out_p, inv_n, dY, dYt, loss_rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_sums(const uint16_t* M, long long ld, int rows, int n, float* out,
+                            cudaStream_t s) {
+  row_sums_kernel<<<rows, kEwThreads, 0, s>>>(M, ld, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_reduce(const double* loss_rows, int n, double scale, double* acc,
+                               cudaStream_t s) {
+  loss_reduce_kernel<<<1, kEwThreads, 0, s>>>(loss_rows, n, scale, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long count, float lr,
+                        float b1, float b2, float eps, int t, cudaStream_t s) {
+  const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+  adam_kernel<<<ew_blocks(count), kEwThreads, 0, s>>>(p, g, m, v, count, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_weights(const float* W, int N, int K, uint16_t* Wb, uint16_t* Wt,
+                                cudaStream_t s) {
+  pack_weights_kernel<<<ew_blocks((long long)N * K), kEwThreads, 0, s>>>(W, N, K, Wb, Wt);
+  return cudaGetLastError();
+}
 
 // Shape rules checked on the host before any launch.
 const char* gemm_shape_error(const GemmArgs& g) {

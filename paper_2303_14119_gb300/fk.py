@@ -35,6 +35,11 @@ class fk_grid_desc(C.Structure):
                 ("device", C.c_int32), ("reserved", C.c_int32)]
 
 
+class fk_mlp_desc(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("width", C.c_int32), ("depth", C.c_int32),
+                ("n_out", C.c_int32), ("max_batch", C.c_int32), ("device", C.c_int32)]
+
+
 class FkError(RuntimeError):
     def __init__(self, status, what, message):
         self.status = status
@@ -61,6 +66,7 @@ def load(build_if_missing: bool = True):
     lib = C.CDLL(_build.LIB)
     P, D, I, I64 = C.c_void_p, C.c_double, C.c_int, C.c_int64
     dp = C.POINTER(C.c_double)
+    fp = C.POINTER(C.c_float)
     i64p = C.POINTER(C.c_int64)
     sig = {
         "fk_create_grid": [C.POINTER(fk_grid_desc), P, C.POINTER(P)],
@@ -93,6 +99,14 @@ def load(build_if_missing: bool = True):
         "fk_batch_set_kernel_timing": [P, I],
         "fk_batch_kernel_timing": [P, i64p, dp],
         "fk_gemm_bf16_tn": [P, I64, P, I64, P, I64, C.c_int32, C.c_int32, C.c_int32, P, P],
+        "fk_mlp_create": [C.POINTER(fk_mlp_desc), P, C.POINTER(P)],
+        "fk_mlp_destroy": [P],
+        "fk_mlp_param_count": [P, i64p],
+        "fk_mlp_set_params": [P, fp],
+        "fk_mlp_get_params": [P, fp],
+        "fk_mlp_forward": [P, fp, I64, fp],
+        "fk_mlp_loss_grad": [P, fp, fp, fp, I64, dp, fp],
+        "fk_mlp_train": [P, fp, fp, fp, I64, C.c_int32, C.c_int32, C.c_float, C.c_uint64, dp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -102,6 +116,8 @@ def load(build_if_missing: bool = True):
     lib.fk_last_error.argtypes = [P]
     lib.fk_batch_last_error.restype = C.c_char_p
     lib.fk_batch_last_error.argtypes = [P]
+    lib.fk_mlp_last_error.restype = C.c_char_p
+    lib.fk_mlp_last_error.argtypes = [P]
     _lib = lib
     return lib
 
@@ -342,6 +358,125 @@ def fk_gemm_bf16_tn(A_ptr, lda, B_ptr, ldb, C_ptr, ldc, M, N, K, err_ptr, stream
                                   C.c_void_p(C_ptr), int(ldc), int(M), int(N), int(K),
                                   C.c_void_p(err_ptr), C.c_void_p(stream) if stream else None),
            "fk_gemm_bf16_tn")
+
+
+# --- the surrogate network (include/fk_mlp.h) ------------------------------
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _f32(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if n is not None and a.size != n:
+        raise ValueError("expected %d elements, got %d" % (n, a.size))
+    return a
+
+
+def _mcheck(status, what, handle=None):
+    if status != FK_OK:
+        msg = load().fk_mlp_last_error(handle).decode(errors="replace")
+        raise FkError(status, what, msg)
+
+
+def fk_mlp_create(n_in, width, depth, n_out, max_batch, device=0, stream=None):
+    d = fk_mlp_desc(int(n_in), int(width), int(depth), int(n_out), int(max_batch), int(device))
+    h = C.c_void_p()
+    st = load().fk_mlp_create(C.byref(d), C.c_void_p(stream) if stream else None, C.byref(h))
+    _mcheck(st, "fk_mlp_create")
+    return h.value
+
+
+def fk_mlp_destroy(h):
+    _mcheck(load().fk_mlp_destroy(h), "fk_mlp_destroy", h)
+
+
+def fk_mlp_param_count(h):
+    n = C.c_int64()
+    _mcheck(load().fk_mlp_param_count(h, C.byref(n)), "fk_mlp_param_count", h)
+    return n.value
+
+
+def fk_mlp_set_params(h, params):
+    p = _f32(params, fk_mlp_param_count(h))
+    _mcheck(load().fk_mlp_set_params(h, _fp(p)), "fk_mlp_set_params", h)
+
+
+def fk_mlp_get_params(h):
+    p = np.empty(fk_mlp_param_count(h), dtype=np.float32)
+    _mcheck(load().fk_mlp_get_params(h, _fp(p)), "fk_mlp_get_params", h)
+    return p
+
+
+def fk_mlp_forward(h, x, n_out):
+    x = _f32(x)
+    n = x.shape[0]
+    y = np.empty((n, n_out), dtype=np.float32)
+    _mcheck(load().fk_mlp_forward(h, _fp(x), int(n), _fp(y)), "fk_mlp_forward", h)
+    return y
+
+
+def fk_mlp_loss_grad(h, x, t, w=None, grad=True):
+    x, t = _f32(x), _f32(t)
+    wv = _f32(w) if w is not None else None
+    loss = np.empty(1)
+    g = np.empty(fk_mlp_param_count(h), dtype=np.float32) if grad else None
+    _mcheck(load().fk_mlp_loss_grad(h, _fp(x), _fp(t), _fp(wv) if wv is not None else None,
+                                    int(x.shape[0]), _dp(loss), _fp(g) if grad else None),
+            "fk_mlp_loss_grad", h)
+    return float(loss[0]), g
+
+
+def fk_mlp_train(h, x, t, w=None, batch=256, epochs=1, lr=1e-3, seed=0):
+    x, t = _f32(x), _f32(t)
+    wv = _f32(w) if w is not None else None
+    el = np.empty(max(int(epochs), 1))
+    _mcheck(load().fk_mlp_train(h, _fp(x), _fp(t), _fp(wv) if wv is not None else None,
+                                int(x.shape[0]), int(batch), int(epochs), float(lr),
+                                int(seed) & 0xFFFFFFFFFFFFFFFF, _dp(el)), "fk_mlp_train", h)
+    return el[:int(epochs)]
+
+
+def fk_mlp_last_error(h=None):
+    return load().fk_mlp_last_error(h).decode(errors="replace")
+
+
+class Mlp:
+    """Owning handle around one ``fk_mlp``."""
+
+    def __init__(self, n_in, width, depth, n_out, max_batch, device=0, stream=None):
+        self.h = fk_mlp_create(n_in, width, depth, n_out, max_batch, device, stream)
+        self.n_in, self.width, self.depth, self.n_out = n_in, width, depth, n_out
+
+    def close(self):
+        if getattr(self, "h", None):
+            fk_mlp_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def param_count(self):
+        return fk_mlp_param_count(self.h)
+
+    def set_params(self, p):
+        fk_mlp_set_params(self.h, p)
+
+    def get_params(self):
+        return fk_mlp_get_params(self.h)
+
+    def forward(self, x):
+        return fk_mlp_forward(self.h, x, self.n_out)
+
+    def loss_grad(self, x, t, w=None, grad=True):
+        return fk_mlp_loss_grad(self.h, x, t, w, grad)
+
+    def train(self, x, t, w=None, batch=256, epochs=1, lr=1e-3, seed=0):
+        return fk_mlp_train(self.h, x, t, w, batch, epochs, lr, seed)
 
 
 # --- batches ---------------------------------------------------------------

@@ -84,3 +84,106 @@ def test_bad_shapes_rejected_on_host():
     assert lib.fk_gemm_bf16_tn(*args(128, 300, 16)) == fk.FK_EINVAL  # N > 256
     assert lib.fk_gemm_bf16_tn(*args(128, 16, 16, lda=12)) == fk.FK_EINVAL
     assert lib.fk_gemm_bf16_tn(*args(0, 16, 16)) == fk.FK_EINVAL
+
+
+# ------------------------------------------------------------ the network
+from oracle.mlp_oracle import MLPOracle  # noqa: E402
+
+
+def init_params(o, seed):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for out_, in_ in o.shapes:
+        parts.append(rng.normal(0.0, 1.0 / np.sqrt(in_), out_ * in_))
+        parts.append(rng.normal(0.0, 0.05, out_))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+SURROGATE = (6, 256, 3, 65)  # inputs, width, hidden layers, outputs
+
+
+def test_param_layout_round_trip_and_count():
+    o = MLPOracle(*SURROGATE)
+    with fk.Mlp(*SURROGATE, max_batch=256) as m:
+        assert m.param_count() == o.param_count()
+        p = init_params(o, 1)
+        m.set_params(p)
+        assert np.array_equal(m.get_params(), p)
+
+
+@pytest.mark.parametrize("n", [1, 130, 300])
+def test_forward_matches_oracle(n):
+    o = MLPOracle(*SURROGATE)
+    p = init_params(o, 2)
+    rng = np.random.default_rng(n)
+    X = rng.normal(size=(n, 6)).astype(np.float32)
+    with fk.Mlp(*SURROGATE, max_batch=512) as m:
+        m.set_params(p)
+        Y = m.forward(X)
+    Yo, _ = o.forward(p.astype(np.float64), X.astype(np.float64), bf16=True)
+    assert rel_l2(Y, Yo) <= 1e-3
+    # the bf16 rounding is real: without it the oracle is further away
+    Y64, _ = o.forward(p.astype(np.float64), X.astype(np.float64), bf16=False)
+    assert rel_l2(Y, Y64) > rel_l2(Y, Yo)
+
+
+def test_forward_in_chunks_equals_one_call():
+    o = MLPOracle(*SURROGATE)
+    p = init_params(o, 3)
+    X = np.random.default_rng(9).normal(size=(333, 6)).astype(np.float32)
+    with fk.Mlp(*SURROGATE, max_batch=128) as a, fk.Mlp(*SURROGATE, max_batch=512) as b:
+        a.set_params(p)
+        b.set_params(p)
+        assert np.array_equal(a.forward(X), b.forward(X))
+
+
+@pytest.mark.parametrize("n", [7, 256, 1000])
+def test_gradient_matches_oracle(n):
+    o = MLPOracle(*SURROGATE)
+    p = init_params(o, 4)
+    rng = np.random.default_rng(100 + n)
+    X = rng.normal(size=(n, 6)).astype(np.float32)
+    T = rng.normal(size=(n, 65)).astype(np.float32)
+    w = rng.uniform(0.5, 2.0, 65).astype(np.float32)
+    with fk.Mlp(*SURROGATE, max_batch=1024) as m:
+        m.set_params(p)
+        loss, g = m.loss_grad(X, T, w)
+    lo, go = o.loss_grad(p.astype(np.float64), X.astype(np.float64), T.astype(np.float64),
+                         w.astype(np.float64), bf16=True)
+    assert abs(loss - lo) <= 1e-4 * lo
+    pos = 0
+    for out_, in_ in o.shapes:
+        for size in (out_ * in_, out_):
+            seg, ref = g[pos:pos + size], go[pos:pos + size]
+            assert rel_l2(seg, ref) <= 5e-3, (pos, size, rel_l2(seg, ref))
+            pos += size
+    cos = float(np.dot(g, go) / (np.linalg.norm(g) * np.linalg.norm(go)))
+    assert cos >= 0.99999
+
+
+def test_training_reduces_loss_and_is_deterministic():
+    o = MLPOracle(6, 64, 2, 5)
+    p = init_params(o, 5)
+    rng = np.random.default_rng(11)
+    X = rng.uniform(-1, 1, size=(2048, 6)).astype(np.float32)
+    A = rng.normal(size=(6, 5))
+    T = np.sin(X @ A).astype(np.float32)
+    runs = []
+    for _ in range(2):
+        with fk.Mlp(6, 64, 2, 5, max_batch=256) as m:
+            m.set_params(p)
+            hist = m.train(X, T, batch=128, epochs=60, lr=3e-3, seed=7)
+            runs.append((hist, m.get_params()))
+    hist = runs[0][0]
+    assert hist[-1] < 0.05 * hist[0]
+    assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][0], runs[1][0])
+    # the trained network's loss, recomputed by the oracle, agrees
+    with fk.Mlp(6, 64, 2, 5, max_batch=2048) as m:
+        m.set_params(runs[0][1])
+        loss, _ = m.loss_grad(X, T, grad=False)
+    lo = o.loss(runs[0][1].astype(np.float64), X.astype(np.float64), T.astype(np.float64), bf16=True)
+    assert abs(loss - lo) <= 1e-3 * lo
