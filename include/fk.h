@@ -266,6 +266,13 @@ fk_status fk_batch_step(fk_batch *batch, int64_t n);
  * status of the first grid that is not (its message in fk_batch_last_error). */
 fk_status fk_batch_sync(fk_batch *batch, int32_t *status);
 
+/* Per-grid scalars of the current states after the batch's enqueued work
+ * (one synchronisation for all grids): sigma[i] (C/m^2), step[i], the first
+ * saturated step sat_step[i] (-1 if none) and the sticky status[i]; any
+ * array may be NULL.  Frozen grids report their last valid state. */
+fk_status fk_batch_scalars(fk_batch *batch, double *sigma, int64_t *step, int64_t *sat_step,
+                           int32_t *status);
+
 /* Autotuner: picks the x-chunk length (planes per work unit) of every size
  * bucket of the batch -- grids grouped by plane size and nx, each a power of
  * two -- by timing real steps: one trial of steps_per_trial >= 1 batch steps

@@ -427,6 +427,24 @@ fk_status fk_batch_sync(fk_batch* b, int32_t* status) {
   return first;
 }
 
+fk_status fk_batch_scalars(fk_batch* b, double* sigma, int64_t* step, int64_t* sat_step,
+                           int32_t* status) {
+  if (!b) return FK_EINVAL;
+  BK_CUDA(b, cudaSetDevice(b->dev));
+  std::vector<DevState> st(b->n);
+  for (int i = 0; i < b->n; i++)
+    BK_CUDA(b, cudaMemcpyAsync(&st[i], b->grids[i]->d_st, sizeof(DevState),
+                               cudaMemcpyDeviceToHost, b->stream));
+  BK_CUDA(b, cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < b->n; i++) {
+    if (sigma) sigma[i] = st[i].sigma;
+    if (step) step[i] = st[i].step;
+    if (sat_step) sat_step[i] = st[i].sat_step;
+    if (status) status[i] = flags_status(b->grids[i], st[i].flags);
+  }
+  return FK_OK;
+}
+
 fk_status fk_batch_get_chunks(const fk_batch* b, int32_t* chunk_len) {
   if (!b || !chunk_len) return FK_EINVAL;
   for (int i = 0; i < b->n; i++) chunk_len[i] = b->chunk_len[i];

@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
         "fk_batch_get_chunks": [P, C.POINTER(C.c_int32)],
         "fk_batch_set_chunks": [P, C.POINTER(C.c_int32)],
         "fk_batch_info": [P, dp],
+        "fk_batch_scalars": [P, dp, i64p, i64p, C.POINTER(C.c_int32)],
         "fk_batch_set_kernel_timing": [P, I],
         "fk_batch_kernel_timing": [P, i64p, dp],
         "fk_gemm_bf16_tn": [P, I64, P, I64, P, I64, C.c_int32, C.c_int32, C.c_int32, P, P],
@@ -517,6 +518,19 @@ def fk_batch_sync(b, n):
     return list(out)
 
 
+def fk_batch_scalars(b, n):
+    """(sigma, step, sat_step, status) arrays of the batch's n grids."""
+    sig = np.empty(n)
+    st = np.empty(n, dtype=np.int64)
+    sat = np.empty(n, dtype=np.int64)
+    status = np.empty(n, dtype=np.int32)
+    _bcheck(load().fk_batch_scalars(b, _dp(sig), st.ctypes.data_as(C.POINTER(C.c_int64)),
+                                    sat.ctypes.data_as(C.POINTER(C.c_int64)),
+                                    status.ctypes.data_as(C.POINTER(C.c_int32))),
+            "fk_batch_scalars", b)
+    return sig, st, sat, status
+
+
 def fk_batch_autotune(b, steps_per_trial=2):
     taken = C.c_int64()
     _bcheck(load().fk_batch_autotune(b, int(steps_per_trial), C.byref(taken)),
@@ -588,6 +602,9 @@ class Batch:
 
     def autotune(self, steps_per_trial=2):
         return fk_batch_autotune(self.h, steps_per_trial)
+
+    def scalars(self):
+        return fk_batch_scalars(self.h, len(self.grids))
 
     def chunks(self):
         return fk_batch_get_chunks(self.h, len(self.grids))

@@ -106,3 +106,30 @@ def sweep_instances(n: int = 256, seed: int = 2023):
                         A_max=250.0 + 350.0 * float(u[q, 4]),
                         T_se=1.0 + 4.0 * float(u[q, 5]), seed=seed + 1 + q))
     return out
+
+
+# Surrogate training runs: the sweep's parameter draws plus the two inputs
+# the surrogate also takes, the injected current J (log-uniform; strong
+# enough that the surface charge moves within the runs' horizon) and the
+# gap h_max (uniform), on the coarse grid of the small workload.
+SURROGATE_J = (1e5, 1e7)        # A/m^2
+SURROGATE_H = (16e-6, 24e-6)    # m
+_SURROGATE_OFFSET = 1 << 61
+
+
+def surrogate_runs(n: int, seed: int):
+    """n run descriptions drawn from one seed: E_y log-uniform in
+    [3e5, 5e6] V/m, delta_max in [2, 4], A_max in [250, 600] eV, T_se in
+    [1, 5] eV (as sweep_instances), J log-uniform in SURROGATE_J, h_max
+    uniform in SURROGATE_H; grid 64 x 48 x 48."""
+    u = uniform(seed, 6 * n, offset=_SURROGATE_OFFSET).reshape(n, 6)
+    out = []
+    for q in range(n):
+        e = float(np.exp(np.log(3e5) + u[q, 0] * (np.log(5e6) - np.log(3e5))))
+        J = float(np.exp(np.log(SURROGATE_J[0]) + u[q, 4] * (np.log(SURROGATE_J[1]) - np.log(SURROGATE_J[0]))))
+        out.append(dict(BASE, nx=64, nv1=48, nv2=48, Ey=-e,
+                        delta_max=2.0 + 2.0 * float(u[q, 1]),
+                        A_max=250.0 + 350.0 * float(u[q, 2]),
+                        T_se=1.0 + 4.0 * float(u[q, 3]), J=J,
+                        h_max=SURROGATE_H[0] + (SURROGATE_H[1] - SURROGATE_H[0]) * float(u[q, 5])))
+    return out

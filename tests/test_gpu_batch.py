@@ -226,3 +226,14 @@ def test_batch_kernel_timing():
         b.set_kernel_timing(False)
         b.step(32)
         assert b.sync() == [fk.FK_OK, fk.FK_OK]
+
+
+def test_batch_scalars_equal_the_grid_getters():
+    _, batched = twins(fk.FK_F32, SHAPES[:3])
+    with fk.Batch(batched) as b:
+        b.step(37)
+        sig, step, sat, status = b.scalars()
+        for q, g in enumerate(batched):
+            assert sig[q] == g.surface_charge()
+            assert (step[q], sat[q]) == g.step_count()
+            assert status[q] == fk.FK_OK
