@@ -119,6 +119,20 @@ fk_status fk_set_see(fk_grid *grid, double delta_max, double A_max_eV, double k_
  * centre lies in the band. */
 fk_status fk_set_source(fk_grid *grid, double J, double x_lo, double x_hi, double T_fe_eV);
 
+/* Fowler-Nordheim field emission, Eq. 6: the current density J (A/m^2) at
+ * the emitter field E (V/m, > 0) for a work function e phi (phi in V, > 0),
+ * without field enhancement or image-charge correction.  *log_J receives
+ * ln J (finite even where J underflows), *J = exp(ln J) (0 on underflow);
+ * either may be NULL.  Host-side, needs no grid.  At the paper's E = |E_y|
+ * of a few MV/m the exponent is about -1e4, so J is exactly 0 in FP64. */
+fk_status fk_fowler_nordheim(double E, double phi_V, double *log_J, double *J);
+
+/* fk_set_source with J from Eq. 6 at the field E_ctj (V/m) and work function
+ * phi (V): the source of Eq. 7 fed by field emission at the cathode triple
+ * junction.  A J that underflows switches the source off. */
+fk_status fk_set_source_fn(fk_grid *grid, double E_ctj, double phi_V, double x_lo, double x_hi,
+                           double T_fe_eV);
+
 /* Convergence test of Sec. 2 (paragraph after Eq. 18): the run is saturated
  * at the first step n >= window with |q_n - q_{n-window}| <= rel_tol |q_n|
  * for q = sigma, Gamma_pe and Gamma_see.  Defaults: window 10000, rel_tol

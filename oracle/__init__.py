@@ -80,6 +80,7 @@ def _load():
         "oracle_first_crossover": (D, [D, D, D]),
         "oracle_sigma_eq20": (D, [D, D, D]),
         "oracle_time_of_flight": (D, [D, D]),
+        "oracle_fn_log_current": (D, [D, D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -120,6 +121,11 @@ def sigma_eq20(Ey, A0_eV, A1_eV):
 
 def time_of_flight(A0_eV, ax):
     return _load().oracle_time_of_flight(A0_eV, ax)
+
+
+def fn_log_current(E, phi_V):
+    """ln of the Eq. 6 Fowler-Nordheim current density (A/m^2)."""
+    return _load().oracle_fn_log_current(E, phi_V)
 
 
 class OracleError(RuntimeError):

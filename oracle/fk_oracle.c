@@ -57,6 +57,7 @@
 #define OR_ME 9.1093837015e-31   /* electron mass, kg */
 #define OR_EPS0 8.8541878128e-12 /* vacuum permittivity, F/m */
 #define OR_PI 3.14159265358979323846
+#define OR_H 6.62607015e-34      /* Planck constant, J s (exact in SI) */
 
 enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2, OR_ECFL = 4 };
 
@@ -582,6 +583,17 @@ double oracle_first_crossover(double delta_max, double A_max_eV, double k_s) {
     if (oracle_seey(mid, 0.0, delta_max, A_max_eV, k_s) < 1.0) lo = mid; else hi = mid;
   }
   return 0.5 * (lo + hi);
+}
+
+/* Eq. 6, the Fowler-Nordheim current density J (A/m^2) at the field E
+ * (V/m) for a work function e phi (phi in V), returned as ln J so that the
+ * exponent -B/E (about -1.1e4 at 5 MV/m) does not underflow:
+ *   J = e^3 E^2 / (8 pi h W) exp(-8 pi sqrt(2 m_e W^3) / (3 e h E)),  W = e phi. */
+double oracle_fn_log_current(double E, double phi_V) {
+  const double W = OR_QE * phi_V;
+  const double pre = OR_QE * OR_QE * OR_QE / (8.0 * OR_PI * OR_H * W);
+  const double B = 8.0 * OR_PI * sqrt(2.0 * OR_ME * W * W * W) / (3.0 * OR_QE * OR_H);
+  return log(pre) + 2.0 * log(E) - B / E;
 }
 
 /* Eq. 20: saturated surface charge of the SEEA theory, A0, A1 in eV. */

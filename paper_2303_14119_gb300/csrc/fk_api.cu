@@ -488,6 +488,30 @@ fk_status fk_set_source(fk_grid* g, double J, double x_lo, double x_hi, double T
   return refresh(g, true);
 }
 
+fk_status fk_fowler_nordheim(double E, double phi_V, double* log_J, double* J) {
+  if (!(E > 0.0) || !(phi_V > 0.0) || !isfinite(E) || !isfinite(phi_V))
+    return fail(nullptr, FK_EINVAL, "fk_fowler_nordheim: need E > 0 and phi > 0, finite");
+  // Eq. 6 with the work function W = e phi (J) and Planck's constant
+  // h = 6.62607015e-34 J s; ln J keeps the exponent from underflowing
+  const double h = 6.62607015e-34;
+  const double W = kQe * phi_V;
+  const double ln_pre = log(kQe * kQe * kQe / (8.0 * kPi * h * W));
+  const double B = 8.0 * kPi * sqrt(2.0 * kMe * W * W * W) / (3.0 * kQe * h);
+  const double lj = ln_pre + 2.0 * log(E) - B / E;
+  if (log_J) *log_J = lj;
+  if (J) *J = exp(lj);  // 0 when it underflows
+  return FK_OK;
+}
+
+fk_status fk_set_source_fn(fk_grid* g, double E_ctj, double phi_V, double x_lo, double x_hi,
+                           double T_fe_eV) {
+  if (!g) return FK_EINVAL;
+  double J = 0.0;
+  if (fk_fowler_nordheim(E_ctj, phi_V, nullptr, &J) != FK_OK)
+    return fail(g, FK_EINVAL, "need E_ctj > 0 and phi > 0");
+  return fk_set_source(g, J, x_lo, x_hi, T_fe_eV);
+}
+
 fk_status fk_set_convergence(fk_grid* g, int64_t window, double rel_tol) {
   if (!g) return FK_EINVAL;
   FK_NOT_IN_BATCH(g);

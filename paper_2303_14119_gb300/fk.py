@@ -75,6 +75,8 @@ def load(build_if_missing: bool = True):
         "fk_set_see": [P, D, D, D, D, I],
         "fk_set_source": [P, D, D, D, D],
         "fk_set_convergence": [P, I64, D],
+        "fk_fowler_nordheim": [D, D, dp, dp],
+        "fk_set_source_fn": [P, D, D, D, D, D],
         "fk_step": [P, I64],
         "fk_sync": [P],
         "fk_moments": [P, dp, dp, dp, dp],
@@ -169,6 +171,19 @@ def fk_set_see(g, delta_max, A_max_eV, k_s=1.0, T_se_eV=2.0, enabled=True):
 def fk_set_source(g, J, x_lo, x_hi, T_fe_eV):
     _check(load().fk_set_source(g, float(J), float(x_lo), float(x_hi), float(T_fe_eV)),
            "fk_set_source", g)
+
+
+def fk_fowler_nordheim(E, phi_V):
+    """(ln J, J) of Eq. 6 in A/m^2."""
+    lj, j = np.empty(1), np.empty(1)
+    _check(load().fk_fowler_nordheim(float(E), float(phi_V), _dp(lj), _dp(j)),
+           "fk_fowler_nordheim")
+    return float(lj[0]), float(j[0])
+
+
+def fk_set_source_fn(g, E_ctj, phi_V, x_lo, x_hi, T_fe_eV):
+    _check(load().fk_set_source_fn(g, float(E_ctj), float(phi_V), float(x_lo), float(x_hi),
+                                   float(T_fe_eV)), "fk_set_source_fn", g)
 
 
 def fk_set_convergence(g, window, rel_tol):
@@ -303,6 +318,9 @@ class Grid:
 
     def set_source(self, J, x_lo, x_hi, T_fe_eV):
         fk_set_source(self.h, J, x_lo, x_hi, T_fe_eV)
+
+    def set_source_fn(self, E_ctj, phi_V, x_lo, x_hi, T_fe_eV):
+        fk_set_source_fn(self.h, E_ctj, phi_V, x_lo, x_hi, T_fe_eV)
 
     def set_convergence(self, window, rel_tol):
         fk_set_convergence(self.h, window, rel_tol)

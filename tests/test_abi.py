@@ -94,3 +94,20 @@ def test_batch_calls_reject_null_handles():
     assert lib.fk_batch_info(None, C.byref(d)) == fk.FK_EINVAL
     assert lib.fk_batch_kernel_timing(None, C.byref(n), C.byref(d)) == fk.FK_EINVAL
     assert lib.fk_batch_destroy(None) == fk.FK_OK
+
+
+def test_fowler_nordheim_host_function_matches_the_oracle():
+    import math
+    import oracle
+    for E in (1e6, 5e6, 3e9, 1e10):
+        for phi in (2.5, 4.08, 4.5):
+            lj, j = fk.fk_fowler_nordheim(E, phi)
+            ref = oracle.fn_log_current(E, phi)
+            assert abs(lj - ref) <= 1e-12 * abs(ref)
+            assert j == (math.exp(lj))
+    assert fk.fk_fowler_nordheim(5e6, 4.08)[1] == 0.0
+    lib = fk.load()
+    import ctypes as Ct
+    d = Ct.c_double()
+    assert lib.fk_fowler_nordheim(0.0, 4.0, Ct.byref(d), None) == fk.FK_EINVAL
+    assert lib.fk_fowler_nordheim(1e9, -1.0, None, None) == fk.FK_EINVAL

@@ -522,3 +522,24 @@ def test_sigma_eq20_from_cosine_averaged_kinematics():
 
         sig = optimize.brentq(residual, 1e-9, 1.0, xtol=1e-20, rtol=1e-14)
         assert oracle.sigma_eq20(Ey, A0, A1) == pytest.approx(sig, rel=1e-9)
+
+
+def test_fowler_nordheim_matches_the_published_fn_constants():
+    """Eq. 6 with W = e phi equals a E^2 / phi exp(-b phi^1.5 / E) with the
+    first and second Fowler-Nordheim constants a = 1.541434e-6 A eV V^-2 and
+    b = 6.830890e9 eV^-1.5 V m^-1 (Forbes and Deane, Proc. R. Soc. A 2007)."""
+    a, b = 1.541434e-6, 6.830890e9
+    for E in (1e6, 5e6, 1e9, 5e9, 2e10):
+        for phi in (2.0, 4.08, 4.5, 5.5):
+            ref = math.log(a) + 2 * math.log(E) - math.log(phi) - b * phi ** 1.5 / E
+            got = oracle.fn_log_current(E, phi)
+            assert abs(got - ref) <= 2e-6 * abs(b * phi ** 1.5 / E) + 1e-6, (E, phi, got, ref)
+
+
+def test_fowler_nordheim_underflows_at_the_papers_field():
+    """With E_CTJ = |E_y| = 5 MV/m and phi = 4.08 V the exponent is about
+    -1.13e4: J = exp(ln J) is exactly 0 in FP64 (the reason a constant J
+    stands in for Eq. 6)."""
+    lj = oracle.fn_log_current(5e6, 4.08)
+    assert -11300 < lj < -11200
+    assert math.exp(lj) == 0.0
