@@ -81,6 +81,8 @@ def _load():
         "oracle_sigma_eq20": (D, [D, D, D]),
         "oracle_time_of_flight": (D, [D, D]),
         "oracle_fn_log_current": (D, [D, D]),
+        "oracle_nu_ee": (D, [D, D, D]),
+        "oracle_set_collisions": (I, [P, D, D, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -121,6 +123,11 @@ def sigma_eq20(Ey, A0_eV, A1_eV):
 
 def time_of_flight(A0_eV, ax):
     return _load().oracle_time_of_flight(A0_eV, ax)
+
+
+def nu_ee(n, T_e_eV, ln_lambda=10.0):
+    """Eq. 4: electron-electron collision frequency (1/s)."""
+    return _load().oracle_nu_ee(n, T_e_eV, ln_lambda)
 
 
 def fn_log_current(E, phi_V):
@@ -167,6 +174,10 @@ class Oracle:
     def set_source(self, J, x_lo, x_hi, T_fe_eV):
         self._chk(self._lib.oracle_set_source(self._h, float(J), float(x_lo), float(x_hi),
                                               float(T_fe_eV)), "set_source")
+
+    def set_collisions(self, T_e_eV=2.0, ln_lambda=10.0, enabled=True):
+        self._chk(self._lib.oracle_set_collisions(self._h, float(T_e_eV), float(ln_lambda),
+                                                  int(bool(enabled))), "set_collisions")
 
     def set_convergence(self, window, tol):
         self._chk(self._lib.oracle_set_convergence(self._h, int(window), float(tol)),

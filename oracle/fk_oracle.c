@@ -45,7 +45,15 @@
  *      counted as a loss in the ledger;
  *   R10 the convergence test compares each history row with the row
  *      `window` steps earlier (relative change <= tol for sigma, Gamma_pe
- *      and Gamma_see).
+ *      and Gamma_see);
+ *   R11 the electron-electron BGK term of Eqs. 3-5 (off unless switched on)
+ *      uses the electron temperature T_e as a fixed parameter (listed with
+ *      the default parameters of Sec. 2, 2 eV) and n_e(x) of f^n, so that
+ *      nu_ee(x) = n_e e^4 ln(Lambda) / (12 pi^1.5 eps0^2 sqrt(m_e) T_e^1.5);
+ *      the equilibrium of Eq. 5 (no drift) is renormalised on the grid to
+ *      unit density, so the term changes no plane's density; it enters the
+ *      same forward-Euler step as the advection (R1), and the Courant sum
+ *      includes dt nu_ee.
  */
 #include <math.h>
 #include <stdint.h>
@@ -83,6 +91,10 @@ typedef struct {
   double J, x_lo, x_hi, T_fe;
   int n_band;
   double *g_fe; /* source velocity shape of Eq. 7 */
+  /* electron-electron collisions, Eqs. 3-5 (R11) */
+  int collisions;
+  double T_e, ln_lambda;
+  double *g_e0; /* equilibrium of Eq. 5, unit density on the grid */
   /* state */
   double sigma;
   int64_t step;
@@ -187,6 +199,37 @@ static void build_gfe(or_state *s) {
   for (int i = 0; i < s->nv1; i++)
     for (int j = 0; j < s->nv2; j++)
       s->g_fe[vcell(s, i, j)] = norm > 0.0 ? s->g_fe[vcell(s, i, j)] / norm : 0.0;
+}
+
+/* Equilibrium VDF of Eq. 5 at T_e, renormalised on the grid to unit
+ * density (R11). */
+static void build_ge0(or_state *s) {
+  double T = s->T_e * OR_QE;
+  double norm = 0.0;
+  for (int i = 0; i < s->nv1; i++)
+    for (int j = 0; j < s->nv2; j++) {
+      double g = OR_ME / (2.0 * OR_PI * T) *
+                 exp(-(OR_ME * s->v1[i] * s->v1[i] + OR_ME * s->v2[j] * s->v2[j]) / (2.0 * T));
+      s->g_e0[vcell(s, i, j)] = g;
+      norm += g * s->dv1 * s->dv2;
+    }
+  for (int i = 0; i < s->nv1; i++)
+    for (int j = 0; j < s->nv2; j++)
+      s->g_e0[vcell(s, i, j)] = norm > 0.0 ? s->g_e0[vcell(s, i, j)] / norm : 0.0;
+}
+
+/* Eq. 4: electron-electron collision frequency (1/s) at density n (m^-3),
+ * temperature T_e (eV) and Coulomb logarithm ln_lambda. */
+double oracle_nu_ee(double n, double T_e_eV, double ln_lambda) {
+  const double T = T_e_eV * OR_QE;
+  return n * pow(OR_QE, 4) * ln_lambda /
+         (12.0 * pow(OR_PI, 1.5) * OR_EPS0 * OR_EPS0 * sqrt(OR_ME) * pow(T, 1.5));
+}
+
+/* BGK relaxation rate of plane k of the current state (0 when off). */
+static double nu_plane(const or_state *s, int k) {
+  if (!s->collisions || !(s->ne[k] > 0.0)) return 0.0;
+  return oracle_nu_ee(s->ne[k], s->T_e, s->ln_lambda);
 }
 
 static int in_band(const or_state *s, int k) {
@@ -359,7 +402,7 @@ void oracle_destroy(or_state *s) {
   if (!s) return;
   free(s->x); free(s->v1); free(s->v2);
   free(s->f); free(s->f_next);
-  free(s->delta); free(s->g_se); free(s->g_fe);
+  free(s->delta); free(s->g_se); free(s->g_fe); free(s->g_e0);
   free(s->ne); free(s->Ex); free(s->a1);
   free(s->hist);
   free(s);
@@ -392,11 +435,12 @@ or_state *oracle_create(int nx, int nv1, int nv2, double h_max, double v1_min,
   s->delta = (double *)calloc(nv, sizeof(double));
   s->g_se = (double *)calloc(nv, sizeof(double));
   s->g_fe = (double *)calloc(nv, sizeof(double));
+  s->g_e0 = (double *)calloc(nv, sizeof(double));
   s->ne = (double *)calloc(nx, sizeof(double));
   s->Ex = (double *)calloc(nx, sizeof(double));
   s->a1 = (double *)calloc(nx, sizeof(double));
   if (!s->x || !s->v1 || !s->v2 || !s->f || !s->f_next || !s->delta || !s->g_se ||
-      !s->g_fe || !s->ne || !s->Ex || !s->a1) {
+      !s->g_fe || !s->g_e0 || !s->ne || !s->Ex || !s->a1) {
     oracle_destroy(s);
     return NULL;
   }
@@ -407,6 +451,8 @@ or_state *oracle_create(int nx, int nv1, int nv2, double h_max, double v1_min,
   s->self_consistent = 1;
   s->delta_max = 0.0; s->A_max = 1.0; s->k_s = 1.0; s->T_se = 1.0;
   s->T_fe = 1.0;
+  s->T_e = 2.0; s->ln_lambda = 10.0; /* Sec. 2 defaults; collisions off */
+  build_ge0(s);
   s->sat_window = 10000;
   s->sat_tol = 1e-3;
   if (reset_run(s) != OR_OK) { oracle_destroy(s); return NULL; }
@@ -442,6 +488,16 @@ int oracle_set_source(or_state *s, double J, double x_lo, double x_hi, double T_
   return refresh(s);
 }
 
+/* Electron-electron collisions of Eqs. 3-5 (R11). */
+int oracle_set_collisions(or_state *s, double T_e_eV, double ln_lambda, int enabled) {
+  if (!(T_e_eV > 0.0) || !(ln_lambda >= 0.0)) return OR_EINVAL;
+  s->T_e = T_e_eV;
+  s->ln_lambda = ln_lambda;
+  s->collisions = enabled ? 1 : 0;
+  build_ge0(s);
+  return refresh(s);
+}
+
 int oracle_set_convergence(or_state *s, int64_t window, double tol) {
   if (window < 1 || !(tol >= 0.0)) return OR_EINVAL;
   s->sat_window = window;
@@ -461,23 +517,29 @@ double oracle_courant_sum(const or_state *s) {
   double cx = 0.0, c1 = 0.0;
   for (int i = 0; i < s->nv1; i++) cx = fmax(cx, fabs(s->v1[i]) * s->dt / s->dx);
   for (int k = 0; k < s->nx; k++) c1 = fmax(c1, fabs(s->a1[k]) * s->dt / s->dv1);
-  return cx + c1 + fabs(s->a2) * s->dt / s->dv2;
+  double cb = 0.0;
+  for (int k = 0; k < s->nx; k++) cb = fmax(cb, nu_plane(s, k) * s->dt);
+  return cx + c1 + fabs(s->a2) * s->dt / s->dv2 + cb;
 }
 
 /* Steps 3-5 for one time step (R1, R4). */
 static int one_step(or_state *s) {
   if (oracle_courant_sum(s) > 1.0 + 1e-12) return OR_ECFL;
   const double dt = s->dt;
-  for (int k = 0; k < s->nx; k++)
+  for (int k = 0; k < s->nx; k++) {
+    const double nu = nu_plane(s, k);
     for (int i = 0; i < s->nv1; i++)
       for (int j = 0; j < s->nv2; j++) {
         double dFx = flux_x(s, k + 1, i, j) - flux_x(s, k, i, j);
         double dFv1 = flux_v1(s, k, i + 1, j) - flux_v1(s, k, i, j);
         double dFv2 = flux_v2(s, k, i, j + 1) - flux_v2(s, k, i, j);
+        /* Eq. 3: nu_ee (n_e f_e0 - f), from f^n */
+        double coll = nu * (s->ne[k] * s->g_e0[vcell(s, i, j)] - s->f[cell(s, k, i, j)]);
         s->f_next[cell(s, k, i, j)] = s->f[cell(s, k, i, j)] - dt / s->dx * dFx -
                                       dt / s->dv1 * dFv1 - dt / s->dv2 * dFv2 +
-                                      dt * source(s, k, i, j);
+                                      dt * source(s, k, i, j) + dt * coll;
       }
+  }
   /* ledger: fluxes of state n times dt */
   double inj = 0.0;
   for (int k = 0; k < s->nx; k++)

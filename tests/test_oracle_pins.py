@@ -15,6 +15,7 @@ import pytest
 from scipy import integrate, linalg, optimize, stats
 
 import oracle
+from paper_2303_14119_gb300 import synth
 from oracle import EPS0, ME, QE, Oracle
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -543,3 +544,83 @@ def test_fowler_nordheim_underflows_at_the_papers_field():
     lj = oracle.fn_log_current(5e6, 4.08)
     assert -11300 < lj < -11200
     assert math.exp(lj) == 0.0
+
+
+# ---- electron-electron BGK collisions (Eqs. 3-5)
+def nrl_nu(n_m3, T_eV, ln_lambda):
+    """The NRL Plasma Formulary's electron collision rate
+    nu_e = 2.91e-6 n[cm^-3] lnL T_e[eV]^-1.5 / s; Eq. 4 is that rate divided
+    by sqrt(2)."""
+    return 2.91e-6 * (n_m3 * 1e-6) * ln_lambda * T_eV ** -1.5 / math.sqrt(2.0)
+
+
+def test_nu_ee_matches_the_published_rate():
+    for n in (1e12, 1e16, 3e19):
+        for T in (0.5, 2.0, 40.0):
+            for L in (5.0, 10.0):
+                assert oracle.nu_ee(n, T, L) == pytest.approx(nrl_nu(n, T, L), rel=5e-3)
+
+
+def maxwellian(v1, v2, T_eV, dv1, dv2):
+    """Eq. 5 on the grid (no drift), scaled to unit density by its own sum."""
+    T = T_eV * QE
+    g = np.exp(-ME * (v1[:, None] ** 2 + v2[None, :] ** 2) / (2 * T))
+    return g / (g.sum() * dv1 * dv2)
+
+
+def bgk_pair(shape, f0, sigma, lnL, T_e=2.0):
+    """One step with collisions and one without, from the same state."""
+    nx, nv1, nv2 = shape
+    out = []
+    for on in (True, False):
+        o = oracle.Oracle(nx, nv1, nv2, 20e-6, -6e7, 6e7, -3e7, 3e7, cfl=0.3)
+        o.set_fields(-1e6)
+        o.set_collisions(T_e, lnL, on)
+        o.set_state(f0, sigma)
+        assert o.courant_sum() <= 1.0
+        ne_before, _, _, _ = o.moments()
+        o.step(1)
+        out.append((o.get_f(), o.moments()[0], ne_before, o.info()))
+        o.close()
+    return out
+
+
+def grid_v(shape):
+    nx, nv1, nv2 = shape
+    dv1, dv2 = 12e7 / nv1, 6e7 / nv2
+    v1 = -6e7 + (np.arange(nv1) + 0.5) * dv1
+    v2 = -3e7 + (np.arange(nv2) + 0.5) * dv2
+    return v1, v2, dv1, dv2
+
+
+def test_bgk_keeps_every_plane_density():
+    shape = (6, 20, 18)
+    f0 = synth.random_f(shape, 3, 1e-2)
+    (f_on, n_on, nb, info), (f_off, n_off, _, _) = bgk_pair(shape, f0, 0.0, lnL=1e10)
+    dt = info["dt"]
+    # the collision term is large enough to matter
+    assert nrl_nu(nb.max(), 2.0, 1e10) * dt > 1e-3
+    assert np.abs(f_on - f_off).max() > 1e-3 * np.abs(f_off).max()
+    # but it moves no density between planes or out of them
+    assert np.allclose(n_on, n_off, rtol=1e-12, atol=0)
+
+
+def test_bgk_leaves_the_equilibrium_unchanged_and_relaxes_others():
+    shape = (5, 24, 22)
+    v1, v2, dv1, dv2 = grid_v(shape)
+    M = maxwellian(v1, v2, 2.0, dv1, dv2)
+    amp = np.array([1.0, 2.0, 0.5, 3.0, 1.5])[:, None, None] * 1e13
+    f_eq = amp * M[None]
+    (f_on, _, nb, info), (f_off, _, _, _) = bgk_pair(shape, f_eq, 0.0, lnL=1e9)
+    scale = np.abs(f_off).max()
+    assert np.abs(f_on - f_off).max() <= 1e-12 * scale
+    # a Maxwellian at another temperature relaxes toward M at T_e, by
+    # dt nu (n M - f) in one forward-Euler step
+    M8 = maxwellian(v1, v2, 8.0, dv1, dv2)
+    f_hot = amp * M8[None]
+    (f_on, _, nb, info), (f_off, _, _, _) = bgk_pair(shape, f_hot, 0.0, lnL=1e9)
+    dt = info["dt"]
+    for k in range(shape[0]):
+        expect = dt * nrl_nu(nb[k], 2.0, 1e9) * (nb[k] * M - f_hot[k])
+        got = f_on[k] - f_off[k]
+        assert np.abs(got - expect).max() <= 6e-3 * np.abs(expect).max()
