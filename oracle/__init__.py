@@ -83,6 +83,7 @@ def _load():
         "oracle_fn_log_current": (D, [D, D]),
         "oracle_nu_ee": (D, [D, D, D]),
         "oracle_set_collisions": (I, [P, D, D, I]),
+        "oracle_set_reflection": (I, [P, D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -178,6 +179,9 @@ class Oracle:
     def set_collisions(self, T_e_eV=2.0, ln_lambda=10.0, enabled=True):
         self._chk(self._lib.oracle_set_collisions(self._h, float(T_e_eV), float(ln_lambda),
                                                   int(bool(enabled))), "set_collisions")
+
+    def set_reflection(self, R_f):
+        self._chk(self._lib.oracle_set_reflection(self._h, float(R_f)), "set_reflection")
 
     def set_convergence(self, window, tol):
         self._chk(self._lib.oracle_set_convergence(self._h, int(window), float(tol)),

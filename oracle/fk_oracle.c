@@ -53,7 +53,13 @@
  *      the equilibrium of Eq. 5 (no drift) is renormalised on the grid to
  *      unit density, so the term changes no plane's density; it enters the
  *      same forward-Euler step as the advection (R1), and the Courant sum
- *      includes dt nu_ee.
+ *      includes dt nu_ee;
+ *   R12 electron reflection at the dielectric (Sec. 2, after Eq. 17, off
+ *      unless set): a fraction R_f of each incident flux element
+ *      dGamma_pe(i, j) returns specularly at (-v1_i, v2_j) -- the mirror cell
+ *      of a v1 grid symmetric about 0 -- and only the rest, (1 - R_f), is
+ *      absorbed and induces SEE with yield delta(i, j); the surface charge
+ *      changes by e dt (1 - R_f) sum (delta - 1) dGamma_pe.
  */
 #include <math.h>
 #include <stdint.h>
@@ -95,6 +101,8 @@ typedef struct {
   int collisions;
   double T_e, ln_lambda;
   double *g_e0; /* equilibrium of Eq. 5, unit density on the grid */
+  /* electron reflection at the dielectric (R12) */
+  double refl;
   /* state */
   double sigma;
   int64_t step;
@@ -275,7 +283,8 @@ static void evaluate_wall(or_state *s) {
     for (int j = 0; j < s->nv2; j++) {
       double dG = -s->v1[i] * s->f[cell(s, 0, i, j)] * s->dv1 * s->dv2; /* Eq. 13 */
       gpe += dG;
-      if (s->see_enabled) gsee += s->delta[vcell(s, i, j)] * dG; /* Eqs. 12, 14 */
+      /* Eqs. 12, 14 on the absorbed part (R12) */
+      if (s->see_enabled) gsee += (1.0 - s->refl) * s->delta[vcell(s, i, j)] * dG;
     }
   }
   s->g_pe = gpe;
@@ -290,10 +299,13 @@ static void evaluate_wall(or_state *s) {
 static double flux_x(const or_state *s, int kf, int i, int j) {
   double v = s->v1[i];
   double lower, upper;
-  if (kf == 0) /* Eq. 15: inflow from the wall carries the SE distribution */
+  if (kf == 0) { /* Eq. 15: inflow from the wall carries the SE distribution */
     lower = s->g_see * s->g_se[vcell(s, i, j)];
-  else
+    /* R12: plus the specularly reflected part of the incident distribution */
+    if (s->refl > 0.0 && v > 0.0) lower += s->refl * s->f[cell(s, 0, s->nv1 - 1 - i, j)];
+  } else {
     lower = s->f[cell(s, kf - 1, i, j)];
+  }
   if (kf == s->nx) /* Eq. 17: nothing enters from the vacuum side */
     upper = 0.0;
   else
@@ -498,6 +510,15 @@ int oracle_set_collisions(or_state *s, double T_e_eV, double ln_lambda, int enab
   return refresh(s);
 }
 
+/* Electron reflection at the dielectric (R12); R_f > 0 needs a v1 grid
+ * symmetric about 0. */
+int oracle_set_reflection(or_state *s, double R_f) {
+  if (!(R_f >= 0.0 && R_f <= 1.0)) return OR_EINVAL;
+  if (R_f > 0.0 && fabs(s->v1_min + s->v1_max) > 1e-12 * fabs(s->v1_max)) return OR_EINVAL;
+  s->refl = R_f;
+  return refresh(s);
+}
+
 int oracle_set_convergence(or_state *s, int64_t window, double tol) {
   if (window < 1 || !(tol >= 0.0)) return OR_EINVAL;
   s->sat_window = window;
@@ -558,7 +579,7 @@ static int one_step(or_state *s) {
     for (int j = 0; j < s->nv2; j++) {
       double dG = -s->v1[i] * s->f[cell(s, 0, i, j)] * s->dv1 * s->dv2;
       double d = s->see_enabled ? s->delta[vcell(s, i, j)] : 0.0;
-      dsig += (d - 1.0) * dG;
+      dsig += (1.0 - s->refl) * (d - 1.0) * dG; /* R12: reflected electrons deposit nothing */
     }
   }
   s->sigma += OR_QE * dt * dsig;

@@ -624,3 +624,49 @@ def test_bgk_leaves_the_equilibrium_unchanged_and_relaxes_others():
         expect = dt * nrl_nu(nb[k], 2.0, 1e9) * (nb[k] * M - f_hot[k])
         got = f_on[k] - f_off[k]
         assert np.abs(got - expect).max() <= 6e-3 * np.abs(expect).max()
+
+
+# ---- electron reflection at the dielectric (R_f, Sec. 2 after Eq. 17)
+def test_reflection_ledger_and_charge():
+    """With R_f the wall returns R_f of each incident flux element at the
+    mirrored velocity: the wall inflow equals the secondaries plus R_f times
+    the primary flux, the electron ledger still closes, and only the absorbed
+    part (1 - R_f) charges the surface."""
+    Rf = 0.35
+    o, f0, sigma, p = _strong_case(14, 12, 10, seed=8)
+    o.set_reflection(Rf)
+    o.set_state(f0, sigma)
+    o.step(50)
+    L = o.ledger()
+    rhs = L["emit"] - L["pe"] - L["vac"] - L["lv"] + L["inj"]
+    scale = max(abs(L["emit"]), abs(L["pe"]), abs(L["vac"]), abs(L["lv"]), abs(L["inj"]), L["N"])
+    assert abs((L["N"] - L["N0"]) - rhs) < 1e-12 * scale
+    assert L["emit"] == pytest.approx(L["see"] + Rf * L["pe"], rel=1e-12)
+    dsig = o.surface_charge() - L["sigma0"]
+    assert dsig / QE == pytest.approx(L["see"] - (1 - Rf) * L["pe"], rel=1e-11)
+
+
+def test_full_reflection_leaves_the_charge_and_zero_reflection_changes_nothing():
+    o, f0, sigma, p = _strong_case(10, 12, 8, seed=9)
+    o.set_reflection(1.0)
+    o.set_state(f0, sigma)
+    o.step(20)
+    assert o.surface_charge() == sigma
+    L = o.ledger()
+    assert L["see"] == 0.0 and L["emit"] == pytest.approx(L["pe"], rel=1e-12)
+    a, _, _, _ = _strong_case(10, 12, 8, seed=9)
+    b, _, _, _ = _strong_case(10, 12, 8, seed=9)
+    b.set_reflection(0.0)
+    for x in (a, b):
+        x.set_state(f0, sigma)
+        x.step(7)
+    assert np.array_equal(a.get_f(), b.get_f())
+
+
+def test_reflection_needs_a_symmetric_v1_grid():
+    o = Oracle(8, 6, 6, 20e-6, -5e7, 6e7, -3e7, 3e7)
+    with pytest.raises(oracle.OracleError):
+        o.set_reflection(0.5)
+    o.set_reflection(0.0)
+    with pytest.raises(oracle.OracleError):
+        Oracle(8, 6, 6, 20e-6, -6e7, 6e7, -3e7, 3e7).set_reflection(1.5)
