@@ -133,6 +133,27 @@ fk_status fk_fowler_nordheim(double E, double phi_V, double *log_J, double *J);
 fk_status fk_set_source_fn(fk_grid *grid, double E_ctj, double phi_V, double x_lo, double x_hi,
                            double T_fe_eV);
 
+/* Electron-electron Coulomb collisions, Eqs. 3-5: the BGK term
+ * nu_ee(x) (n_e(x) f_e0 - f) with nu_ee from Eq. 4 at the electron
+ * temperature T_e (eV, > 0; the paper's default is 2 eV) and Coulomb
+ * logarithm ln_lambda (>= 0; the paper's value is 10), n_e(x) the density of
+ * the state being stepped, and f_e0 the equilibrium of Eq. 5 (Maxwellian at
+ * T_e, no drift) normalised on the grid so that the term moves no density.
+ * It enters the same forward-Euler step as the advection; dt nu_ee counts
+ * toward the Courant bound (FK_ECFL).  enabled = 0 (the default) switches
+ * it off. */
+fk_status fk_set_collisions(fk_grid *grid, double T_e_eV, double ln_lambda, int enabled);
+
+/* Electron reflection at the dielectric (Sec. 2, text after Eq. 17): a
+ * fraction R_f (0..1) of each incident primary flux element dGamma_pe(i, j)
+ * returns specularly at (-v1_i, v2_j); only the rest, (1 - R_f), is absorbed
+ * and emits secondaries with yield delta(i, j) (Eqs. 12-14), so Gamma_see
+ * and the charging of Eq. 18 scale with (1 - R_f), and the ledger's emitted
+ * term counts secondaries plus reflected electrons.  R_f > 0 needs a v1 grid
+ * symmetric about 0 (each cell's mirror is a cell); FK_EINVAL otherwise.
+ * Default 0. */
+fk_status fk_set_reflection(fk_grid *grid, double R_f);
+
 /* Convergence test of Sec. 2 (paragraph after Eq. 18): the run is saturated
  * at the first step n >= window with |q_n - q_{n-window}| <= rel_tol |q_n|
  * for q = sigma, Gamma_pe and Gamma_see.  Defaults: window 10000, rel_tol
@@ -249,7 +270,8 @@ fk_status fk_density_moment_noalloc(const double *f_dev, int32_t nx, int32_t nv1
  * Ownership and state rules:
  *  - The batch borrows the grids; the caller keeps ownership.  While a grid
  *    belongs to a batch, every call that changes it (fk_step, the setters,
- *    fk_set_f, fk_set_surface_charge, fk_set_kernel_timing and
+ *    fk_set_f, fk_set_surface_charge, fk_set_collisions, fk_set_reflection,
+ *    fk_set_kernel_timing and
  *    fk_destroy_grid) returns FK_ESTATE; the getters work and see every
  *    batch step enqueued before them.  fk_batch_destroy releases the grids.
  *  - A grid that meets a sticky device error (FK_ECFL, FK_ENUMERIC,

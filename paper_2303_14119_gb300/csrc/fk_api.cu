@@ -79,6 +79,8 @@ StepArgs fk::make_args(fk_grid* g, int cur) {
   a.geom = g->geom;
   a.prm = g->d_prm;
   a.st = g->d_st;
+  a.bgk = g->d_bgk;
+  a.bgk32 = g->d_bgk32;
   a.tab = g->tab;
   a.part = g->part;
   return a;
@@ -125,7 +127,8 @@ cudaError_t enqueue_step(fk_grid* g, int cur, cudaStream_t s, cudaEvent_t ev0, c
   cudaError_t e = cudaSuccess;
   if (ev0) e = cudaEventRecord(ev0, s);
   if (e == cudaSuccess)
-    e = g->use_stream ? launch_step_stream(a, g->prec, s) : launch_step(a, g->prec, 0, s);
+    e = g->use_stream ? launch_step_stream(a, g->prec, g->prm.collisions != 0, s)
+                      : launch_step(a, g->prec, 0, s);
   if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
   if (e == cudaSuccess)
     e = launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, g->fin, kModeStep, s);
@@ -156,7 +159,7 @@ fk_status rebuild_tables(fk_grid* g) {
   const double j_over_ew = (g->J > 0.0 && W > 0.0) ? g->J / kQe / W : 0.0;
   FK_CUDA(g, launch_tables(g->tab, g->nv1, g->nv2, g->pitch, g->desc.v1_min, g->desc.v2_min,
                            g->dv1, g->dv2, g->dt, g->dx, g->delta_max, g->A_max, g->k_s,
-                           g->T_se, g->T_fe, j_over_ew, g->stream));
+                           g->T_se, g->T_fe, j_over_ew, g->T_e, g->stream));
   return FK_OK;
 }
 
@@ -178,7 +181,8 @@ void free_grid(fk_grid* g) {
     if (g->graph[p]) cudaGraphExecDestroy(g->graph[p]);
   void* ptrs[] = {g->d_prm, g->d_st, g->d_f[0], g->d_f[1], g->tab.v1, g->tab.cx,
                   g->tab.cx32, g->tab.delta, g->tab.gse, g->tab.src, g->tab.src32,
-                  g->tab.gfe_raw, g->tab.srow32, g->tab.scol32, g->tab.tsum, g->part.n, g->part.lv,
+                  g->tab.gfe_raw, g->tab.srow32, g->tab.scol32, g->tab.tsum, g->tab.m1, g->tab.m2,
+                  g->tab.m1_32, g->tab.m2_32, g->d_bgk, g->d_bgk32, g->part.n, g->part.lv,
                   g->part.pe, g->part.see,
                   g->part.vac, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist,
                   g->d_stage, g->fin.pre, g->fin.bsum, g->fin.blv, g->fin.counter};
@@ -331,6 +335,9 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   p.hist_cap = d.history_capacity > 0 ? d.history_capacity : 65536;
   p.self_consistent = 1;
   p.see_enabled = 0;
+  p.collisions = 0;
+  p.bgk_c = 0.0;
+  p.refl = 0.0;
   p.band_lo = p.band_hi = 0;
   if (p.sat_window >= p.hist_cap) p.sat_window = p.hist_cap - 1;
   if (cx_max > 1.0 + 1e-12) {
@@ -383,6 +390,14 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   CREATE_CUDA(dalloc(&g->tab.srow32, d.nv1 * sizeof(float)));
   CREATE_CUDA(dalloc(&g->tab.scol32, g->pitch * sizeof(float)));
   CREATE_CUDA(dalloc(&g->tab.tsum, tables_scratch_doubles() * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->tab.m1, d.nv1 * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->tab.m2, g->pitch * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->tab.m1_32, d.nv1 * sizeof(float)));
+  CREATE_CUDA(dalloc(&g->tab.m2_32, g->pitch * sizeof(float)));
+  CREATE_CUDA(dalloc(&g->d_bgk, 2 * (size_t)d.nx * sizeof(double)));
+  CREATE_CUDA(dalloc(&g->d_bgk32, 2 * (size_t)d.nx * sizeof(float)));
+  CREATE_CUDA(cudaMemsetAsync(g->d_bgk, 0, 2 * (size_t)d.nx * sizeof(double), g->stream));
+  CREATE_CUDA(cudaMemsetAsync(g->d_bgk32, 0, 2 * (size_t)d.nx * sizeof(float), g->stream));
   CREATE_CUDA(dalloc(&g->part.n, nparts * sizeof(double)));
   CREATE_CUDA(dalloc(&g->part.lv, nparts * sizeof(double)));
   CREATE_CUDA(dalloc(&g->part.pe, g->part.nu * sizeof(double)));
@@ -510,6 +525,46 @@ fk_status fk_set_source_fn(fk_grid* g, double E_ctj, double phi_V, double x_lo, 
   if (fk_fowler_nordheim(E_ctj, phi_V, nullptr, &J) != FK_OK)
     return fail(g, FK_EINVAL, "need E_ctj > 0 and phi > 0");
   return fk_set_source(g, J, x_lo, x_hi, T_fe_eV);
+}
+
+fk_status fk_set_collisions(fk_grid* g, double T_e_eV, double ln_lambda, int enabled) {
+  if (!g) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
+  if (!(T_e_eV > 0.0) || !(ln_lambda >= 0.0) || !isfinite(T_e_eV) || !isfinite(ln_lambda))
+    return fail(g, FK_EINVAL, "need T_e > 0 and ln(Lambda) >= 0, finite");
+  g->T_e = T_e_eV;
+  g->ln_lambda = ln_lambda;
+  // Eq. 4 without n_e, times dt: dt nu_ee(x) = bgk_c * n_e(x)
+  const double T = T_e_eV * kQe;
+  const double per_n = kQe * kQe * kQe * kQe * ln_lambda /
+                       (12.0 * pow(kPi, 1.5) * kEps0 * kEps0 * sqrt(kMe) * pow(T, 1.5));
+  g->prm.bgk_c = g->dt * per_n;
+  const int on = enabled ? 1 : 0;
+  if (on != g->prm.collisions) {
+    // the captured graphs hold the step kernel of the other variant
+    FK_CUDA(g, cudaStreamSynchronize(g->stream));
+    for (int q = 0; q < 2; q++)
+      if (g->graph[q]) {
+        cudaGraphExecDestroy(g->graph[q]);
+        g->graph[q] = nullptr;
+      }
+  }
+  g->prm.collisions = on;
+  if (!on) {
+    FK_CUDA(g, cudaMemsetAsync(g->d_bgk, 0, 2 * (size_t)g->nx * sizeof(double), g->stream));
+    FK_CUDA(g, cudaMemsetAsync(g->d_bgk32, 0, 2 * (size_t)g->nx * sizeof(float), g->stream));
+  }
+  return refresh(g, true);  // tables (equilibrium factors) and coefficients of the state
+}
+
+fk_status fk_set_reflection(fk_grid* g, double R_f) {
+  if (!g) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
+  if (!(R_f >= 0.0 && R_f <= 1.0)) return fail(g, FK_EINVAL, "need 0 <= R_f <= 1");
+  if (R_f > 0.0 && fabs(g->desc.v1_min + g->desc.v1_max) > 1e-12 * fabs(g->desc.v1_max))
+    return fail(g, FK_EINVAL, "reflection needs a v1 grid symmetric about 0");
+  g->prm.refl = R_f;
+  return refresh(g, false);  // the state's Gamma_see changes with R_f
 }
 
 fk_status fk_set_convergence(fk_grid* g, int64_t window, double rel_tol) {

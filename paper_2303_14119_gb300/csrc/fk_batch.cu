@@ -35,6 +35,7 @@ struct fk_batch {
   cudaStream_t cap_stream = nullptr;
   int prec = FK_F64;
   bool padded = false;  // some grid has row padding (pitch > nv2)
+  bool bgk = false;     // some grid has collisions on (the kernel variant with the term)
   int n = 0;
   std::vector<fk_grid*> grids;
   std::vector<int> cur0;       // buffer holding each grid's f at batch step 0
@@ -212,7 +213,8 @@ cudaError_t enqueue_batch_step(fk_batch* b, int p, cudaStream_t s, cudaEvent_t e
   cudaError_t e = cudaSuccess;
   if (ev0) e = cudaEventRecord(ev0, s);
   if (e == cudaSuccess)
-    e = launch_step_stream_batch(inst, b->d_units, b->n_units, b->prec, b->padded, b->smem, s);
+    e = launch_step_stream_batch(inst, b->d_units, b->n_units, b->prec, b->padded, b->bgk,
+                                 b->smem, s);
   if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
   if (e == cudaSuccess) e = launch_finalize_batch(inst, b->d_fblk, b->n_fblk, s);
   return e;
@@ -355,6 +357,7 @@ fk_status fk_batch_create(fk_grid* const* grids, int32_t n, void* cuda_stream, f
     fk_grid* g = gs[i];
     b->smem = std::max(b->smem, stream_smem_bytes(g->prec, g->geom.stage_elems, g->pitch));
     if (g->pitch != g->nv2) b->padded = true;
+    if (g->prm.collisions) b->bgk = true;
     b->cells += (double)g->nx * g->nv1 * g->nv2;
     for (int q = 0; q < finalize_blocks(g->nx); q++) fblk.push_back(make_int2(i, q));
     DevState st;

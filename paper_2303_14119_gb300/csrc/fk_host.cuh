@@ -38,6 +38,9 @@ struct fk_grid {
   double delta_max = 0, A_max = 1, k_s = 1, T_se = 1;
   int see_enabled = 0;
   double J = 0, x_lo = 0, x_hi = 0, T_fe = 1;
+  double T_e = 2.0, ln_lambda = 10.0;  // BGK collisions (off until switched on)
+  double *d_bgk = nullptr;             // [2][nx] per-plane collision coefficients
+  float* d_bgk32 = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   unsigned known_flags = 0;
   // kernel timing

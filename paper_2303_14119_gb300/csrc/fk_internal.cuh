@@ -39,6 +39,13 @@ struct Params {
   double ex_sigma, ex_n, c1_per_ex, dvv, lv_scale;
   long long sat_window;
   long long hist_cap;
+  // electron-electron BGK collisions (Eqs. 3-5): relaxation rate of plane k
+  // is nu_k = bgk_c n_k / dt, i.e. dt nu_k = bgk_c * n_k
+  double bgk_c;
+  // electron reflection at the dielectric: a fraction refl of each incident
+  // flux element returns at the mirrored v1 (symmetric v1 grid)
+  double refl;
+  int collisions;
   int self_consistent;
   int see_enabled;
   int band_lo, band_hi; // source planes [band_lo, band_hi)
@@ -82,6 +89,12 @@ struct Tables {
   float* srow32;  // [nv1] dt (J/e)/W times the normalised v1 factor
   float* scol32;  // [pitch] normalised v2 factor, zero for v2 <= 0 and padding
   double* tsum;   // [tables_scratch_doubles()] normalisation partials and norms
+  // equilibrium of Eq. 5 at T_e, separable and normalised per factor on the
+  // grid: f_e0(i, j) = m1[i] * m2[j] with sum_i m1 dv1 = sum_j m2 dv2 = 1
+  double* m1;     // [nv1]
+  double* m2;     // [pitch] (zero on padding)
+  float* m1_32;
+  float* m2_32;
 };
 
 // Work decomposition shared by the step kernels and the finalize kernel.
@@ -121,6 +134,10 @@ struct alignas(16) StepArgs {
   const float* c1_32;       // [nx] the same rounded to FP32
   const Params* prm;
   DevState* st;
+  // BGK coefficients of the state being stepped, written by the finalize
+  // kernel: bgk[k] = dt nu_k, bgk[nx + k] = dt nu_k n_k (zero when off)
+  double* bgk;      // [2][nx]
+  float* bgk32;     // [2][nx] the same rounded to FP32
   Tables tab;
   Partials part;
   Geom geom;
@@ -157,12 +174,12 @@ cudaError_t launch_tables(const Tables& t, int nv1, int nv2, int pitch,
                           double v1_min, double v2_min, double dv1, double dv2,
                           double dt, double dx, double delta_max, double A_max,
                           double k_s, double T_se, double T_fe, double J_over_eW,
-                          cudaStream_t s);
+                          double T_e, cudaStream_t s);
 int tables_scratch_doubles();
 // Direct-load step (and moments-only evaluation): one block per (plane, tile).
 cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cudaStream_t s);
 // Streaming step: one CTA per (tile, chunk), bulk-async staged planes.
-cudaError_t launch_step_stream(const StepArgs& a, int precision, cudaStream_t s);
+cudaError_t launch_step_stream(const StepArgs& a, int precision, bool bgk, cudaStream_t s);
 // Rows per tile of the streaming kernel for this precision and row pitch
 // so that two CTAs fit on an SM (0 if a row does not fit), its shared
 // memory per CTA, resident CTAs per SM.
@@ -173,7 +190,7 @@ int stream_ctas_per_sm(int precision, size_t smem_bytes);
 // tile + n_tiles * chunk of that grid); smem_bytes >= every grid's
 // stream_smem_bytes.  padded: some grid has pitch > nv2.
 cudaError_t launch_step_stream_batch(const BatchInst* inst, const int2* units, int n_units,
-                                     int precision, bool padded, size_t smem_bytes,
+                                     int precision, bool padded, bool bgk, size_t smem_bytes,
                                      cudaStream_t s);
 // Batched finalize (step mode): block b finalizes block blocks[b].y of grid
 // blocks[b].x; every grid's blocks 0 .. finalize_blocks(nx) - 1 appear once.

@@ -104,9 +104,10 @@ tables_cells_kernel(Tables t, int nv1, int nv2, int pitch, double v1_min, double
 
 __global__ void __launch_bounds__(kTabFoldThreads)
 tables_fold_kernel(Tables t, int nv1, int nv2, int pitch, double v1_min, double v2_min,
-                   double dv1, double dv2, double dt, double dx, double Tfe, double j_over_ew) {
+                   double dv1, double dv2, double dt, double dx, double Tfe, double j_over_ew,
+                   double Te) {
   __shared__ double sh[32];
-  __shared__ double norms[4];
+  __shared__ double norms[6];
   // block partials in block order (one per thread, kTabBlocks <= threads)
   const int b = threadIdx.x;
   double s_se = b < kTabBlocks ? t.tsum[2 * b] : 0.0;
@@ -157,6 +158,42 @@ tables_fold_kernel(Tables t, int nv1, int nv2, int pitch, double v1_min, double 
     }
     t.scol32[j] = (float)g;
   }
+  // factors of the BGK equilibrium of Eq. 5 at T_e (no drift), each
+  // normalised on the grid to unit integral
+  double e1 = 0.0, e2 = 0.0;
+  for (int i = threadIdx.x; i < nv1; i += blockDim.x) {
+    const double v1 = cell_centre(v1_min, i, dv1);
+    e1 += exp(-kMe * v1 * v1 / (2.0 * Te * kQe));
+  }
+  for (int j = threadIdx.x; j < nv2; j += blockDim.x) {
+    const double v2 = cell_centre(v2_min, j, dv2);
+    e2 += exp(-kMe * v2 * v2 / (2.0 * Te * kQe));
+  }
+  __syncthreads();
+  e1 = block_sum<kTabFoldThreads>(e1, sh);
+  __syncthreads();
+  e2 = block_sum<kTabFoldThreads>(e2, sh);
+  if (threadIdx.x == 0) {
+    norms[4] = e1 * dv1;
+    norms[5] = e2 * dv2;
+  }
+  __syncthreads();
+  const double ne1 = norms[4], ne2 = norms[5];
+  for (int i = threadIdx.x; i < nv1; i += blockDim.x) {
+    const double v1 = cell_centre(v1_min, i, dv1);
+    const double m = exp(-kMe * v1 * v1 / (2.0 * Te * kQe)) / ne1;
+    t.m1[i] = m;
+    t.m1_32[i] = (float)m;
+  }
+  for (int j = threadIdx.x; j < pitch; j += blockDim.x) {
+    double m = 0.0;
+    if (j < nv2) {
+      const double v2 = cell_centre(v2_min, j, dv2);
+      m = exp(-kMe * v2 * v2 / (2.0 * Te * kQe)) / ne2;
+    }
+    t.m2[j] = m;
+    t.m2_32[j] = (float)m;
+  }
 }
 
 __global__ void __launch_bounds__(kTabThreads)
@@ -175,11 +212,11 @@ int tables_scratch_doubles() { return 2 * kTabBlocks + 2; }
 cudaError_t launch_tables(const Tables& t, int nv1, int nv2, int pitch, double v1_min,
                           double v2_min, double dv1, double dv2, double dt, double dx,
                           double delta_max, double A_max, double k_s, double T_se,
-                          double T_fe, double j_over_ew, cudaStream_t s) {
+                          double T_fe, double j_over_ew, double T_e, cudaStream_t s) {
   tables_cells_kernel<<<kTabBlocks, kTabThreads, 0, s>>>(t, nv1, nv2, pitch, v1_min, v2_min, dv1,
                                                          dv2, delta_max, A_max, k_s, T_se, T_fe);
   tables_fold_kernel<<<1, kTabFoldThreads, 0, s>>>(t, nv1, nv2, pitch, v1_min, v2_min, dv1, dv2,
-                                                   dt, dx, T_fe, j_over_ew);
+                                                   dt, dx, T_fe, j_over_ew, T_e);
   tables_scale_kernel<<<kTabBlocks, kTabThreads, 0, s>>>(t, nv1 * pitch, dt, j_over_ew);
   return cudaGetLastError();
 }
@@ -250,6 +287,10 @@ step_direct_kernel(StepArgs a, int moments_only) {
   const T a1 = c1 < (T)0 ? -c1 : c1, a2 = c2 < (T)0 ? -c2 : c2;
   const double gsee = a.st->g_see;
   const bool band = k >= p.band_lo && k < p.band_hi;
+  // BGK relaxation of this plane (Eq. 3): dt nu_k and dt nu_k n_k
+  const bool coll = p.collisions != 0;
+  const T ca = coll ? (sizeof(T) == 8 ? (T)a.bgk[k] : (T)a.bgk32[k]) : (T)0;
+  const T cs = coll ? (sizeof(T) == 8 ? (T)a.bgk[nx + k] : (T)a.bgk32[nx + k]) : (T)0;
   const int ncell = (i1 - i0) * nv2;
   typename Acc<T>::type s_n = 0;
   double s_lv = 0.0, s_pe = 0.0, s_see = 0.0, s_vac = 0.0;
@@ -264,7 +305,10 @@ step_direct_kernel(StepArgs a, int moments_only) {
       const T cx = sizeof(T) == 8 ? (T)a.tab.cx[i] : (T)a.tab.cx32[i];
       T fx = (T)0;
       if (cx > (T)0)
-        fx = k > 0 ? fin[idx - plane] : (T)(gsee * a.tab.gse[tix]);
+        fx = k > 0 ? fin[idx - plane]
+                   : (T)(gsee * a.tab.gse[tix] +
+                         (p.refl > 0.0 ? p.refl * (double)fin[(size_t)(nv1 - 1 - i) * pitch + j]
+                                       : 0.0));
       else if (cx < (T)0)
         fx = k < nx - 1 ? fin[idx + plane] : (T)0;
       T fv = (T)0;
@@ -280,6 +324,11 @@ step_direct_kernel(StepArgs a, int moments_only) {
       T s = (T)0;
       if (band) s = sizeof(T) == 8 ? (T)a.tab.src[tix] : (T)a.tab.src32[tix];
       fn = update_cell<T>(f, fx, fv, fw, cx < (T)0 ? -cx : cx, a1, a2, s);
+      if (coll) {
+        const T m = sizeof(T) == 8 ? (T)(a.tab.m1[i] * a.tab.m2[j])
+                                   : (T)a.tab.m1_32[i] * (T)a.tab.m2_32[j];
+        fn += cs * m - ca * f;
+      }
       fout[idx] = fn;
       // loss through the downwind velocity edges, from f^n (ledger)
       if ((c1 > (T)0 && i == nv1 - 1) || (c1 < (T)0 && i == 0)) s_lv += (double)a1 * (double)f;
@@ -453,17 +502,19 @@ __device__ __forceinline__ void finalize_body(const StepArgs& a, const FinOut& o
       DevState d = *st;  // one batch of loads, updated in registers
       const double ntot = ntot_raw * p.dx;
       pe *= p.dvv;
-      see = p.see_enabled ? see * p.dvv : 0.0;  // with SEE off every primary is deposited
+      // secondaries come from the absorbed part (1 - refl) of the primaries;
+      // with SEE off every absorbed primary is deposited
+      see = p.see_enabled ? see * p.dvv * (1.0 - p.refl) : 0.0;
       vac *= p.dvv;
       if (mode == kModeStep) {
         const double lv = l * p.lv_scale;
-        d.cum_emit += p.dt * d.g_see;
+        d.cum_emit += p.dt * (d.g_see + p.refl * d.g_pe);  // secondaries and reflected
         d.cum_see += p.dt * d.g_see;
         d.cum_pe += p.dt * d.g_pe;
         d.cum_vac += p.dt * d.g_vac;
         d.cum_lv += p.dt * lv;
         d.cum_inj += p.dt * p.inj;
-        d.sigma += kQe * p.dt * (d.g_see - d.g_pe);
+        d.sigma += kQe * p.dt * (d.g_see - (1.0 - p.refl) * d.g_pe);
         d.step += 1;
       }
       if (mode == kModeReset) {
@@ -498,7 +549,17 @@ __device__ __forceinline__ void finalize_body(const StepArgs& a, const FinOut& o
     const double c = p.c1_per_ex * e;
     c1[kk] = c;
     c1_32[kk] = (float)c;
-    cmax = fmax(cmax, fabs(c));
+    double cfl = fabs(c);
+    if (p.collisions) {
+      // BGK coefficients of the new state (Eqs. 3-4): dt nu_k = bgk_c n_k
+      const double ak = n_k > 0.0 ? p.bgk_c * n_k : 0.0;
+      a.bgk[kk] = ak;
+      a.bgk[nx + kk] = ak * n_k;
+      a.bgk32[kk] = (float)ak;
+      a.bgk32[nx + kk] = (float)(ak * n_k);
+      cfl += ak;  // the collision term takes part in the positivity bound
+    }
+    cmax = fmax(cmax, cfl);
   }
   cmax = block_max<kFinThreads>(cmax, sh);
   __syncthreads();

@@ -118,27 +118,37 @@ template <typename T>
 __host__ __device__ constexpr size_t stage_bytes(int stage_elems) {
   return ((size_t)stage_elems * sizeof(T) + 127) / 128 * 128;
 }
-// mbarriers full[kStages], empty[kStages]; warp sums [kStages][kWarps][4]
-// (density, wall primary flux, wall secondary flux, vacuum outflow); two
-// control ints
-constexpr int kWs = 4;
-constexpr int kMaxTileRows = 64;  // also bounds the per-stage diagonal table
-// ... plus, for FP64 grids, the per-stage diagonal 1 - |c_x| - |c_1| - |c_2|
-// of every tile row [kStages][kMaxTileRows] double
-// ... plus, for FP32 grids, the separable source factors of the tile rows
-// [kMaxTileRows] and of the row cells [pitch] (float)
 // The dynamic shared memory of both kernels starts with a slot for the
 // unit's StepArgs (filled by the batched kernel), so that one tile plan fits
-// a grid stepped alone or in a batch.
-constexpr int kArgsBytes = 256;
+// a grid stepped alone or in a batch.  After the slot and the stages come:
+// mbarriers full[kStages], empty[kStages]; warp sums [kStages][kWarps][4]
+// (density, wall primary flux, wall secondary flux, vacuum outflow); for
+// FP64 grids the per-stage diagonal 1 - |c_x| - |c_1| - |c_2| (- dt nu) of
+// every tile row [kStages][kMaxTileRows] double, for FP32 grids the
+// separable source factors of the tile rows [kMaxTileRows] and of the row
+// cells [pitch] (float); the BGK equilibrium factors of Eq. 5 (FP32 grids:
+// m1 of the tile rows [kMaxTileRows] and m2 [pitch], float; FP64 grids:
+// dt nu_k n_k m1 per stage and tile row [kStages][kMaxTileRows] and m2
+// [pitch], double); two control ints.
+constexpr int kArgsBytes = 384;  // a multiple of 128: the stages stay 128-byte aligned
 static_assert(sizeof(StepArgs) <= kArgsBytes && sizeof(StepArgs) % 8 == 0,
               "StepArgs must fit its shared-memory slot");
+constexpr int kWs = 4;
+constexpr int kMaxTileRows = 64;  // also bounds the per-stage row tables
+template <typename T>
+__host__ __device__ constexpr size_t tail_main_bytes(int pitch) {
+  return sizeof(T) == 8 ? kStages * kMaxTileRows * sizeof(double)
+                        : ((size_t)(kMaxTileRows + pitch) * sizeof(float) + 15) / 16 * 16;
+}
+template <typename T>
+__host__ __device__ constexpr size_t tail_bgk_bytes(int pitch) {
+  return sizeof(T) == 8 ? (kStages * kMaxTileRows + (size_t)pitch) * sizeof(double)
+                        : ((size_t)(kMaxTileRows + pitch) * sizeof(float) + 15) / 16 * 16;
+}
 template <typename T>
 __host__ __device__ constexpr size_t tail_bytes(int pitch) {
   return kArgsBytes + 2 * kStages * sizeof(uint64_t) + kStages * kWarps * kWs * sizeof(double) +
-         (sizeof(T) == 8 ? kStages * kMaxTileRows * sizeof(double)
-                         : ((size_t)(kMaxTileRows + pitch) * sizeof(float) + 15) / 16 * 16) +
-         16;
+         tail_main_bytes<T>(pitch) + tail_bgk_bytes<T>(pitch) + 16;
 }
 
 // Exact split of a double x >= 2^-126 into hi + lo floats: hi keeps the top
@@ -203,8 +213,9 @@ __device__ __noinline__ void wall_terms(const T* oplane, const double* v1tab,
 }
 
 // One unit (tile t, chunk) of a grid; smem is the CTA's dynamic shared
-// memory past the argument slot.
-template <typename T, bool PADDED>
+// memory past the argument slot.  BGK: the grid has the electron-electron
+// collision term of Eq. 3 switched on.
+template <typename T, bool PADDED, bool BGK>
 __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, const int chunk,
                                             unsigned char* smem) {
   constexpr int VEC = Vec<T>::N;
@@ -215,13 +226,15 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * sbytes);
   uint64_t* empty = full + kStages;
   double* wsum = reinterpret_cast<double*>(empty + kStages);  // [kStages][kWarps][kWs]
-  double* dgl = wsum + kStages * kWarps * kWs;                 // [kStages][kMaxTileRows], FP64
-  float* srow_s = reinterpret_cast<float*>(dgl);               // [kMaxTileRows], FP32
-  float* scol_s = srow_s + kMaxTileRows;                       // [pitch], FP32
-  int* ctl = reinterpret_cast<int*>(
-      reinterpret_cast<unsigned char*>(dgl) +
-      (sizeof(T) == 8 ? kStages * kMaxTileRows * sizeof(double)
-                      : ((size_t)(kMaxTileRows + a.pitch) * sizeof(float) + 15) / 16 * 16));
+  double* dgl = wsum + kStages * kWarps * kWs;  // [kStages][kMaxTileRows], FP64
+  float* srow_s = reinterpret_cast<float*>(dgl);  // [kMaxTileRows], FP32
+  float* scol_s = srow_s + kMaxTileRows;          // [pitch], FP32
+  unsigned char* bgk_base = reinterpret_cast<unsigned char*>(dgl) + tail_main_bytes<T>(a.pitch);
+  double* dgs = reinterpret_cast<double*>(bgk_base);  // [kStages][kMaxTileRows], FP64
+  double* m2d = dgs + kStages * kMaxTileRows;         // [pitch], FP64
+  float* m1_s = reinterpret_cast<float*>(bgk_base);   // [kMaxTileRows], FP32
+  float* m2_s = m1_s + kMaxTileRows;                  // [pitch], FP32
+  int* ctl = reinterpret_cast<int*>(bgk_base + tail_bgk_bytes<T>(a.pitch));
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = gm.n_tiles;
@@ -247,6 +260,14 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   if (sizeof(T) == 4) {  // source factors of this tile (FP32 grids)
     for (int r = tid; r < i1 - i0; r += blockDim.x) srow_s[r] = a.tab.srow32[i0 + r];
     for (int j = tid; j < pitch; j += blockDim.x) scol_s[j] = a.tab.scol32[j];
+  }
+  if (BGK) {  // factors of the collision equilibrium (Eq. 5)
+    if (sizeof(T) == 4) {
+      for (int r = tid; r < i1 - i0; r += blockDim.x) m1_s[r] = a.tab.m1_32[i0 + r];
+      for (int j = tid; j < pitch; j += blockDim.x) m2_s[j] = a.tab.m2_32[j];
+    } else {
+      for (int j = tid; j < pitch; j += blockDim.x) m2d[j] = a.tab.m2[j];
+    }
   }
   if (tid == 0) {
     ctl[0] = (int)a.st->flags;
@@ -291,8 +312,13 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         // FP64 diagonal of the convex update per tile row, once per plane
         // here rather than per vector in the consumers
         const double a1 = c1 == 0.f ? 0.0 : fabs(a.c1[k]);
-        const double db = 1.0 - a1 - fabs(p.c2);
+        double db = 1.0 - a1 - fabs(p.c2);
+        if (BGK) db -= a.bgk[k];  // the loss part of the collision term, dt nu_k f
         for (int r = lane; r < rows; r += 32) dgl[st * kMaxTileRows + r] = db - fabs(a.tab.cx[i0 + r]);
+        if (BGK) {  // its gain part per tile row: dt nu_k n_k m1[i]
+          const double sk = a.bgk[nx + k];
+          for (int r = lane; r < rows; r += 32) dgs[st * kMaxTileRows + r] = sk * a.tab.m1[i0 + r];
+        }
       }
       __syncwarp();
       if (lane == 0) {
@@ -403,13 +429,22 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   if (!prime && dir > 0) {
     // first plane is x = 0 with v1 > 0: the upwind value is the re-emitted
     // distribution Gamma_see g_se of Eq. 15 (zero for the vacuum side)
+    // (plus, with reflection, refl times the incident f^n of the mirror
+    // cell at -v1 on the same plane)
     const double gsee = a.st->g_see;
+    const double refl = p.refl;
 #pragma unroll
     for (int m = 0; m < M; m++) {
       if (!(valid >> m & 1)) continue;
+      const int r = soff[m] >> 24;
+      const int c0 = (soff[m] & 0xFFFFFF) - r * pitch;
 #pragma unroll
-      for (int e = 0; e < VEC; e++)
-        xr[m][e] = (T)(gsee * a.tab.gse[(soff[m] & 0xFFFFFF) + gbase + e]);
+      for (int e = 0; e < VEC; e++) {
+        double g = gsee * a.tab.gse[(soff[m] & 0xFFFFFF) + gbase + e];
+        if (refl > 0.0)
+          g += refl * (double)fin[(size_t)(nv1 - 1 - (i0 + r)) * pitch + c0 + e];
+        xr[m][e] = (T)g;
+      }
     }
   }
   const T c2 = (T)p.c2;
@@ -427,6 +462,13 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
     const bool band = compute && k >= p.band_lo && k < p.band_hi;
     // source term: FP32 grids rebuild it from the separable factors in
     // shared memory, FP64 grids load the 2D table in the update loop
+    // collision term (Eq. 3) of FP32 grids: dt nu_k and dt nu_k n_k (FP64
+    // grids take it from the producer's row tables)
+    T bgk_a = (T)0, bgk_s = (T)0;
+    if (BGK && sizeof(T) == 4) {
+      bgk_a = (T)a.bgk32[k];
+      bgk_s = (T)a.bgk32[nx + k];
+    }
     const bool ok = mbar_wait(&full[st], (uint32_t)((q / kStages) & 1));
     if (__any_sync(0xffffffffu, !ok)) {
       if (lane == 0) atomicOr(&a.st->flags, kFlagTimeout);
@@ -485,12 +527,29 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
             src = *reinterpret_cast<const Vec<T>*>(srcbase + so + gbase);
           }
         }
+        if (BGK) {  // gain dt nu_k n_k m1[i] m2[j] of the collision term
+          const int r = soff[m] >> 24;
+          const int c0 = so - r * pitch;  // column of the vector's first cell
+          if constexpr (sizeof(T) == 4) {
+            const float ms = bgk_s * m1_s[r];
+            const Vec<float> mv = *reinterpret_cast<const Vec<float>*>(m2_s + c0);
+#pragma unroll
+            for (int e = 0; e < VEC; e++) src.e[e] = fmaf(ms, mv.e[e], src.e[e]);
+          } else {
+            const double ms = dgs[st * kMaxTileRows + r];
+            const Vec<double> mv = *reinterpret_cast<const Vec<double>*>(m2d + c0);
+#pragma unroll
+            for (int e = 0; e < VEC; e++) src.e[e] = fma(ms, mv.e[e], src.e[e]);
+          }
+        }
         Vec<T> out;
 #pragma unroll
         for (int e = 0; e < VEC; e++) {
           const T f = own.e[e];
           const T fw = e == 0 ? left : own.e[e - 1];
-          T fn = upd<T>(f, xr[m][e], nb.e[e], fw, ax[m], a1, a2, src.e[e], d);
+          T se = src.e[e];
+          if (BGK && sizeof(T) == 4) se = fmaf(-(float)bgk_a, (float)f, (float)se);  // loss dt nu f
+          T fn = upd<T>(f, xr[m][e], nb.e[e], fw, ax[m], a1, a2, se, d);
           if (PADDED && (so % pitch) + e >= nv2) fn = (T)0;  // row padding stays zero
           out.e[e] = fn;
           xr[m][e] = f;  // x-upwind value for the next plane is f^n here
@@ -543,17 +602,17 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
 }
 
 // One grid: CTA b runs tile b % n_tiles of chunk b / n_tiles.
-template <typename T, bool PADDED>
+template <typename T, bool PADDED, bool BGK>
 __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(const __grid_constant__ StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nt = a.geom.n_tiles;
-  stream_unit<T, PADDED>(a, blockIdx.x % nt, blockIdx.x / nt, smem + kArgsBytes);
+  stream_unit<T, PADDED, BGK>(a, blockIdx.x % nt, blockIdx.x / nt, smem + kArgsBytes);
 }
 
 // Many grids in one launch: CTA b copies the arguments of grid units[b].x
 // into the slot at the start of its shared memory and runs that grid's unit
 // units[b].y = tile + n_tiles * chunk.
-template <typename T, bool PADDED>
+template <typename T, bool PADDED, bool BGK>
 __global__ void __launch_bounds__(kBlock, 2)
 step_stream_batch_kernel(const BatchInst* __restrict__ inst, const int2* __restrict__ units) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -564,7 +623,7 @@ step_stream_batch_kernel(const BatchInst* __restrict__ inst, const int2* __restr
   __syncthreads();
   const StepArgs& a = *reinterpret_cast<const StepArgs*>(smem);
   const int nt = a.geom.n_tiles;
-  stream_unit<T, PADDED>(a, u.y % nt, u.y / nt, smem + kArgsBytes);
+  stream_unit<T, PADDED, BGK>(a, u.y % nt, u.y / nt, smem + kArgsBytes);
 }
 
 }  // namespace
@@ -606,10 +665,18 @@ cudaError_t fit_kernel(K k, int optin, size_t smem_bytes, int* best) {
 template <typename T>
 int ctas_per_sm(int optin, size_t smem_bytes) {
   int best = 1 << 30;
-  cudaError_t e = fit_kernel(step_stream_kernel<T, false>, optin, smem_bytes, &best);
-  if (e == cudaSuccess) e = fit_kernel(step_stream_kernel<T, true>, optin, smem_bytes, &best);
-  if (e == cudaSuccess) e = fit_kernel(step_stream_batch_kernel<T, false>, optin, smem_bytes, &best);
-  if (e == cudaSuccess) e = fit_kernel(step_stream_batch_kernel<T, true>, optin, smem_bytes, &best);
+  cudaError_t e = fit_kernel(step_stream_kernel<T, false, false>, optin, smem_bytes, &best);
+  if (e == cudaSuccess) e = fit_kernel(step_stream_kernel<T, true, false>, optin, smem_bytes, &best);
+  if (e == cudaSuccess) e = fit_kernel(step_stream_kernel<T, false, true>, optin, smem_bytes, &best);
+  if (e == cudaSuccess) e = fit_kernel(step_stream_kernel<T, true, true>, optin, smem_bytes, &best);
+  if (e == cudaSuccess)
+    e = fit_kernel(step_stream_batch_kernel<T, false, false>, optin, smem_bytes, &best);
+  if (e == cudaSuccess)
+    e = fit_kernel(step_stream_batch_kernel<T, true, false>, optin, smem_bytes, &best);
+  if (e == cudaSuccess)
+    e = fit_kernel(step_stream_batch_kernel<T, false, true>, optin, smem_bytes, &best);
+  if (e == cudaSuccess)
+    e = fit_kernel(step_stream_batch_kernel<T, true, true>, optin, smem_bytes, &best);
   return e == cudaSuccess ? best : 0;
 }
 }  // namespace
@@ -627,38 +694,56 @@ int stream_ctas_per_sm(int precision, size_t smem_bytes) {
                              : ctas_per_sm<double>(optin, smem_bytes);
 }
 
-cudaError_t launch_step_stream(const StepArgs& a, int precision, cudaStream_t s) {
+namespace {
+template <typename T, bool BGK>
+void launch_single(const StepArgs& a, int grid, size_t smem, bool padded, cudaStream_t s) {
+  if (padded)
+    step_stream_kernel<T, true, BGK><<<grid, kBlock, smem, s>>>(a);
+  else
+    step_stream_kernel<T, false, BGK><<<grid, kBlock, smem, s>>>(a);
+}
+template <typename T, bool BGK>
+void launch_batch(const BatchInst* inst, const int2* units, int n_units, size_t smem,
+                  bool padded, cudaStream_t s) {
+  if (padded)
+    step_stream_batch_kernel<T, true, BGK><<<n_units, kBlock, smem, s>>>(inst, units);
+  else
+    step_stream_batch_kernel<T, false, BGK><<<n_units, kBlock, smem, s>>>(inst, units);
+}
+}  // namespace
+
+cudaError_t launch_step_stream(const StepArgs& a, int precision, bool bgk, cudaStream_t s) {
   const int grid = a.geom.n_tiles * a.geom.n_chunks;
   const size_t smem = stream_smem_bytes(precision, a.geom.stage_elems, a.pitch);
   const bool padded = a.pitch != a.nv2;
   if (precision == FK_F32) {
-    if (padded)
-      step_stream_kernel<float, true><<<grid, kBlock, smem, s>>>(a);
+    if (bgk)
+      launch_single<float, true>(a, grid, smem, padded, s);
     else
-      step_stream_kernel<float, false><<<grid, kBlock, smem, s>>>(a);
+      launch_single<float, false>(a, grid, smem, padded, s);
   } else {
-    if (padded)
-      step_stream_kernel<double, true><<<grid, kBlock, smem, s>>>(a);
+    if (bgk)
+      launch_single<double, true>(a, grid, smem, padded, s);
     else
-      step_stream_kernel<double, false><<<grid, kBlock, smem, s>>>(a);
+      launch_single<double, false>(a, grid, smem, padded, s);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_step_stream_batch(const BatchInst* inst, const int2* units, int n_units,
-                                     int precision, bool padded, size_t smem_bytes,
+                                     int precision, bool padded, bool bgk, size_t smem_bytes,
                                      cudaStream_t s) {
   if (n_units <= 0) return cudaSuccess;
   if (precision == FK_F32) {
-    if (padded)
-      step_stream_batch_kernel<float, true><<<n_units, kBlock, smem_bytes, s>>>(inst, units);
+    if (bgk)
+      launch_batch<float, true>(inst, units, n_units, smem_bytes, padded, s);
     else
-      step_stream_batch_kernel<float, false><<<n_units, kBlock, smem_bytes, s>>>(inst, units);
+      launch_batch<float, false>(inst, units, n_units, smem_bytes, padded, s);
   } else {
-    if (padded)
-      step_stream_batch_kernel<double, true><<<n_units, kBlock, smem_bytes, s>>>(inst, units);
+    if (bgk)
+      launch_batch<double, true>(inst, units, n_units, smem_bytes, padded, s);
     else
-      step_stream_batch_kernel<double, false><<<n_units, kBlock, smem_bytes, s>>>(inst, units);
+      launch_batch<double, false>(inst, units, n_units, smem_bytes, padded, s);
   }
   return cudaGetLastError();
 }

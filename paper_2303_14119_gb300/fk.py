@@ -76,6 +76,8 @@ def load(build_if_missing: bool = True):
         "fk_set_source": [P, D, D, D, D],
         "fk_set_convergence": [P, I64, D],
         "fk_fowler_nordheim": [D, D, dp, dp],
+        "fk_set_collisions": [P, D, D, I],
+        "fk_set_reflection": [P, D],
         "fk_set_source_fn": [P, D, D, D, D, D],
         "fk_step": [P, I64],
         "fk_sync": [P],
@@ -184,6 +186,15 @@ def fk_fowler_nordheim(E, phi_V):
 def fk_set_source_fn(g, E_ctj, phi_V, x_lo, x_hi, T_fe_eV):
     _check(load().fk_set_source_fn(g, float(E_ctj), float(phi_V), float(x_lo), float(x_hi),
                                    float(T_fe_eV)), "fk_set_source_fn", g)
+
+
+def fk_set_collisions(g, T_e_eV=2.0, ln_lambda=10.0, enabled=True):
+    _check(load().fk_set_collisions(g, float(T_e_eV), float(ln_lambda), int(bool(enabled))),
+           "fk_set_collisions", g)
+
+
+def fk_set_reflection(g, R_f):
+    _check(load().fk_set_reflection(g, float(R_f)), "fk_set_reflection", g)
 
 
 def fk_set_convergence(g, window, rel_tol):
@@ -321,6 +332,12 @@ class Grid:
 
     def set_source_fn(self, E_ctj, phi_V, x_lo, x_hi, T_fe_eV):
         fk_set_source_fn(self.h, E_ctj, phi_V, x_lo, x_hi, T_fe_eV)
+
+    def set_collisions(self, T_e_eV=2.0, ln_lambda=10.0, enabled=True):
+        fk_set_collisions(self.h, T_e_eV, ln_lambda, enabled)
+
+    def set_reflection(self, R_f):
+        fk_set_reflection(self.h, R_f)
 
     def set_convergence(self, window, rel_tol):
         fk_set_convergence(self.h, window, rel_tol)
