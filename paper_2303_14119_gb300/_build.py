@@ -70,12 +70,18 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
 
 
-def source_hash() -> str:
-    """Short hash of the CUDA sources (identifies the kernels a profile was
-    taken on)."""
+# The sources the streaming step kernel is compiled from (its DRAM traffic
+# recorded under profiles/ stays valid while they are unchanged).
+STEP_KERNEL_SOURCES = (os.path.join(CSRC, "fk_stream.cu"), os.path.join(CSRC, "fk_internal.cuh"),
+                       os.path.join(INCLUDE, "fk.h"))
+
+
+def source_hash(files=STEP_KERNEL_SOURCES) -> str:
+    """Short hash of the given sources (by default those of the streaming
+    step kernel), identifying the code a profile was taken on."""
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh"))):
+    for p in sorted(files):
         h.update(os.path.basename(p).encode())
         with open(p, "rb") as fh:
             h.update(fh.read())
