@@ -223,6 +223,41 @@ def warm_start(sur, runs, prof_cold, res_cold, horizon=HORIZON, stream=None, pre
     }
 
 
+def fine_warm_start(weights, n_runs=4, nx=512, nv=128, horizon=HORIZON, stream=None,
+                    precision=fk.FK_F32):
+    """Warm starts on a finer grid than the network was trained on: the
+    first n_runs held-out parameter points of `weights` whose coarse run
+    saturated, solved on nx x nv x nv cold and from the network's
+    end-of-horizon charge, all in one batch."""
+    d = np.load(weights)
+    n_train, n_test, seed = int(d["n_train"]), int(d["n_test"]), int(d["seed"])
+    held = synth.surrogate_runs(n_train + n_test, seed)[n_train:]
+    sel = np.flatnonzero(d["test_ok"] & (d["test_sat_step"] >= 0) & (d["test_tsat"] < HORIZON))
+    sel = sel[:n_runs]
+    runs = [dict(held[q], nx=nx, nv1=nv, nv2=nv) for q in sel]
+    sur = Surrogate.load(weights, stream=stream)
+    pp, pt = sur.predict(runs)
+    sur.close()
+    sigma0 = np.concatenate([np.zeros(len(runs)), pp[:, -1]])
+    res = solve(runs + runs, horizon=horizon, sigma0=sigma0, stream=stream, precision=precision)
+    prof, _, ok = labels(res, horizon)
+    n = len(runs)
+    cold, warm = res["sat_step"][:n], res["sat_step"][n:]
+    end_c, end_w = prof[:n, -1], prof[n:, -1]
+    both = (cold >= 0) & (warm >= 0)
+    return {
+        "grid": [nx, nv, nv], "runs": n, "held_out_index": [int(q) for q in sel],
+        "cells_per_run": nx * nv * nv, "batch_steps": res["batch_steps"],
+        "solver_seconds": res["seconds"], "valid": [bool(x) for x in ok],
+        "sat_step_cold": [int(x) for x in cold], "sat_step_warm": [int(x) for x in warm],
+        "steps_saved_fraction": float(1.0 - warm[both].sum() / cold[both].sum()) if both.any() else None,
+        "sigma_end_cold": [float(x) for x in end_c], "sigma_end_warm": [float(x) for x in end_w],
+        "sigma_warm_start": [float(x) for x in pp[:, -1]],
+        "sigma_end_rel_diff": [float(abs(w - c) / max(abs(c), 1e-30)) for w, c in zip(end_w, end_c)],
+        "predicted_tsat_s": [float(x) for x in pt],
+    }
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--n-train", type=int, default=4096)
@@ -236,11 +271,23 @@ def main(argv=None):
     ap.add_argument("--data", default=None,
                     help="data.npz of an earlier run of the same draws (skips the solver runs)")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-start runs")
+    ap.add_argument("--fine", default=None, metavar="WEIGHTS",
+                    help="only run fine-grid warm starts with these trained weights")
+    ap.add_argument("--fine-runs", type=int, default=4)
+    ap.add_argument("--fine-nx", type=int, default=512)
+    ap.add_argument("--fine-nv", type=int, default=128)
     args = ap.parse_args(argv)
     import torch
     torch.cuda.set_stream(torch.cuda.Stream())
     stream = torch.cuda.current_stream().cuda_stream
     os.makedirs(args.out, exist_ok=True)
+    if args.fine:
+        rep = fine_warm_start(args.fine, args.fine_runs, args.fine_nx, args.fine_nv, args.horizon,
+                              stream)
+        with open(os.path.join(args.out, "fine_report.json"), "w") as fh:
+            json.dump(rep, fh, indent=1)
+        print(json.dumps(rep))
+        return
     runs = synth.surrogate_runs(args.n_train + args.n_test, args.seed)
     if args.data:
         d = np.load(args.data)
