@@ -84,6 +84,7 @@ def _load():
         "oracle_nu_ee": (D, [D, D, D]),
         "oracle_set_collisions": (I, [P, D, D, I]),
         "oracle_set_reflection": (I, [P, D]),
+        "oracle_set_scheme": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -182,6 +183,10 @@ class Oracle:
 
     def set_reflection(self, R_f):
         self._chk(self._lib.oracle_set_reflection(self._h, float(R_f)), "set_reflection")
+
+    def set_scheme(self, scheme):
+        """0: unsplit step, 1: Lie splitting (x, then velocity)."""
+        self._chk(self._lib.oracle_set_scheme(self._h, int(scheme)), "set_scheme")
 
     def set_convergence(self, window, tol):
         self._chk(self._lib.oracle_set_convergence(self._h, int(window), float(tol)),

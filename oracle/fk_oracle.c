@@ -59,7 +59,14 @@
  *      dGamma_pe(i, j) returns specularly at (-v1_i, v2_j) -- the mirror cell
  *      of a v1 grid symmetric about 0 -- and only the rest, (1 - R_f), is
  *      absorbed and induces SEE with yield delta(i, j); the surface charge
- *      changes by e dt (1 - R_f) sum (delta - 1) dGamma_pe.
+ *      changes by e dt (1 - R_f) sum (delta - 1) dGamma_pe;
+ *   R13 Lie splitting (off unless set): the step is an x-advection of f^n
+ *      (with the wall and vacuum boundaries of R4, R5, R12) followed by the
+ *      velocity step (v1, v2 advection, source, collisions) of that
+ *      intermediate state, both over dt and with the fields of f^n; the
+ *      surface charge and the wall and vacuum ledger terms come from f^n as
+ *      in the unsplit step, the velocity-edge loss from the intermediate
+ *      state.
  */
 #include <math.h>
 #include <stdint.h>
@@ -103,6 +110,9 @@ typedef struct {
   double *g_e0; /* equilibrium of Eq. 5, unit density on the grid */
   /* electron reflection at the dielectric (R12) */
   double refl;
+  /* time splitting (R13): 0 unsplit, 1 Lie (x, then velocity) */
+  int scheme;
+  double *f_tmp;
   /* state */
   double sigma;
   int64_t step;
@@ -330,19 +340,26 @@ static double flux_v2(const or_state *s, int k, int i, int jface) {
 }
 
 /* Boundary fluxes of the current state used by the ledger. */
-static void evaluate_boundaries(or_state *s) {
-  double emit = 0.0, vac = 0.0, lv = 0.0;
-  for (int i = 0; i < s->nv1; i++)
-    for (int j = 0; j < s->nv2; j++) {
-      if (s->v1[i] > 0.0) emit += flux_x(s, 0, i, j) * s->dv1 * s->dv2;
-      vac += flux_x(s, s->nx, i, j) * s->dv1 * s->dv2;
-    }
+/* Outflow through the velocity-grid edges (R9) of the state in s->f. */
+static double edge_loss(const or_state *s) {
+  double lv = 0.0;
   for (int k = 0; k < s->nx; k++) {
     for (int j = 0; j < s->nv2; j++)
       lv += (flux_v1(s, k, s->nv1, j) - flux_v1(s, k, 0, j)) * s->dx * s->dv2;
     for (int i = 0; i < s->nv1; i++)
       lv += (flux_v2(s, k, i, s->nv2) - flux_v2(s, k, i, 0)) * s->dx * s->dv1;
   }
+  return lv;
+}
+
+static void evaluate_boundaries(or_state *s) {
+  double emit = 0.0, vac = 0.0;
+  for (int i = 0; i < s->nv1; i++)
+    for (int j = 0; j < s->nv2; j++) {
+      if (s->v1[i] > 0.0) emit += flux_x(s, 0, i, j) * s->dv1 * s->dv2;
+      vac += flux_x(s, s->nx, i, j) * s->dv1 * s->dv2;
+    }
+  const double lv = edge_loss(s);
   double ntot = 0.0;
   for (int k = 0; k < s->nx; k++) ntot += s->ne[k] * s->dx;
   s->g_emit = emit;
@@ -413,7 +430,7 @@ static int refresh(or_state *s) {
 void oracle_destroy(or_state *s) {
   if (!s) return;
   free(s->x); free(s->v1); free(s->v2);
-  free(s->f); free(s->f_next);
+  free(s->f); free(s->f_next); free(s->f_tmp);
   free(s->delta); free(s->g_se); free(s->g_fe); free(s->g_e0);
   free(s->ne); free(s->Ex); free(s->a1);
   free(s->hist);
@@ -444,6 +461,7 @@ or_state *oracle_create(int nx, int nv1, int nv2, double h_max, double v1_min,
   s->v2 = (double *)malloc(nv2 * sizeof(double));
   s->f = (double *)calloc(ncell, sizeof(double));
   s->f_next = (double *)calloc(ncell, sizeof(double));
+  s->f_tmp = (double *)calloc(ncell, sizeof(double));
   s->delta = (double *)calloc(nv, sizeof(double));
   s->g_se = (double *)calloc(nv, sizeof(double));
   s->g_fe = (double *)calloc(nv, sizeof(double));
@@ -451,7 +469,7 @@ or_state *oracle_create(int nx, int nv1, int nv2, double h_max, double v1_min,
   s->ne = (double *)calloc(nx, sizeof(double));
   s->Ex = (double *)calloc(nx, sizeof(double));
   s->a1 = (double *)calloc(nx, sizeof(double));
-  if (!s->x || !s->v1 || !s->v2 || !s->f || !s->f_next || !s->delta || !s->g_se ||
+  if (!s->x || !s->v1 || !s->v2 || !s->f || !s->f_next || !s->f_tmp || !s->delta || !s->g_se ||
       !s->g_fe || !s->g_e0 || !s->ne || !s->Ex || !s->a1) {
     oracle_destroy(s);
     return NULL;
@@ -519,6 +537,13 @@ int oracle_set_reflection(or_state *s, double R_f) {
   return refresh(s);
 }
 
+/* Time splitting (R13): 0 unsplit, 1 Lie. */
+int oracle_set_scheme(or_state *s, int scheme) {
+  if (scheme != 0 && scheme != 1) return OR_EINVAL;
+  s->scheme = scheme;
+  return OR_OK;
+}
+
 int oracle_set_convergence(or_state *s, int64_t window, double tol) {
   if (window < 1 || !(tol >= 0.0)) return OR_EINVAL;
   s->sat_window = window;
@@ -544,8 +569,8 @@ double oracle_courant_sum(const or_state *s) {
 }
 
 /* Steps 3-5 for one time step (R1, R4). */
-static int one_step(or_state *s) {
-  if (oracle_courant_sum(s) > 1.0 + 1e-12) return OR_ECFL;
+/* Step 3 (R1): every cell of f^n updated with all face fluxes from f^n. */
+static void unsplit_update(or_state *s) {
   const double dt = s->dt;
   for (int k = 0; k < s->nx; k++) {
     const double nu = nu_plane(s, k);
@@ -561,6 +586,46 @@ static int one_step(or_state *s) {
                                       dt * source(s, k, i, j) + dt * coll;
       }
   }
+}
+
+/* R13: x-advection of f^n into f_next, then the velocity step of that
+ * intermediate state (the flux helpers read s->f, so it stands in for f^n
+ * meanwhile) into f_tmp, copied back to f_next.  *lv receives the
+ * velocity-edge loss of the intermediate state. */
+static void lie_update(or_state *s, double *lv) {
+  const double dt = s->dt;
+  for (int k = 0; k < s->nx; k++)
+    for (int i = 0; i < s->nv1; i++)
+      for (int j = 0; j < s->nv2; j++) {
+        double dFx = flux_x(s, k + 1, i, j) - flux_x(s, k, i, j);
+        s->f_next[cell(s, k, i, j)] = s->f[cell(s, k, i, j)] - dt / s->dx * dFx;
+      }
+  double *fn = s->f;
+  s->f = s->f_next;
+  for (int k = 0; k < s->nx; k++) {
+    const double nu = nu_plane(s, k); /* n_e of f^n (s->ne) */
+    for (int i = 0; i < s->nv1; i++)
+      for (int j = 0; j < s->nv2; j++) {
+        double dFv1 = flux_v1(s, k, i + 1, j) - flux_v1(s, k, i, j);
+        double dFv2 = flux_v2(s, k, i, j + 1) - flux_v2(s, k, i, j);
+        double coll = nu * (s->ne[k] * s->g_e0[vcell(s, i, j)] - s->f[cell(s, k, i, j)]);
+        s->f_tmp[cell(s, k, i, j)] = s->f[cell(s, k, i, j)] - dt / s->dv1 * dFv1 -
+                                     dt / s->dv2 * dFv2 + dt * source(s, k, i, j) + dt * coll;
+      }
+  }
+  *lv = edge_loss(s);
+  s->f = fn;
+  memcpy(s->f_next, s->f_tmp, (size_t)s->nx * s->nv1 * s->nv2 * sizeof(double));
+}
+
+static int one_step(or_state *s) {
+  if (oracle_courant_sum(s) > 1.0 + 1e-12) return OR_ECFL;
+  const double dt = s->dt;
+  double lv_step = s->l_v; /* loss of the state the velocity advection acts on */
+  if (s->scheme == 1)
+    lie_update(s, &lv_step);
+  else
+    unsplit_update(s);
   /* ledger: fluxes of state n times dt */
   double inj = 0.0;
   for (int k = 0; k < s->nx; k++)
@@ -570,7 +635,7 @@ static int one_step(or_state *s) {
   s->cum_see += dt * s->g_see;
   s->cum_pe += dt * s->g_pe;
   s->cum_vac += dt * s->g_vac;
-  s->cum_lv += dt * s->l_v;
+  s->cum_lv += dt * lv_step;
   s->cum_inj += dt * inj;
   /* Eq. 18: sigma^{n+1} = sigma^n + e dt sum_{v1<0} (delta - 1) dGamma_pe */
   double dsig = 0.0;

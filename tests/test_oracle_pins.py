@@ -670,3 +670,58 @@ def test_reflection_needs_a_symmetric_v1_grid():
     o.set_reflection(0.0)
     with pytest.raises(oracle.OracleError):
         Oracle(8, 6, 6, 20e-6, -6e7, 6e7, -3e7, 3e7).set_reflection(1.5)
+
+
+# ---- Lie splitting (x, then velocity)
+def test_lie_equals_unsplit_without_velocity_terms():
+    h = 20e-6
+    f0 = np.random.default_rng(3).uniform(size=(9, 10, 8)) * 1e10
+    out = []
+    for scheme in (0, 1):
+        o = Oracle(9, 10, 8, h, -6e7, 6e7, -3e7, 3e7, cfl=0.4)
+        o.set_fields(0.0, False, 0.0)          # no force: no v1 or v2 advection
+        o.set_see(3.0, 400.0, 1.0, 400.0)     # wall inflow active
+        o.set_scheme(scheme)
+        o.set_state(f0, 0.0)
+        o.step(3)
+        out.append(o.get_f())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_lie_splitting_error_is_second_order():
+    """With X f = f - dt (A f + b) and V g = g - dt (B g - s), Lie gives
+    V X f = (unsplit step) + dt^2 B (A f + b): the difference from the
+    unsplit step scales exactly as dt^2."""
+    nx, nv1, nv2 = 10, 12, 10
+    o0, f0, sigma, p = _strong_case(nx, nv1, nv2, seed=21)
+    diffs = []
+    for scale in (1.0, 0.5):
+        res = []
+        for scheme in (0, 1):
+            o = Oracle(nx, nv1, nv2, 20e-6, -6e7, 6e7, -3e7, 3e7, dt=p["dt"] * scale)
+            o.set_fields(p["Ey"], True, 0.0)
+            o.set_see(3.0, 400.0, 1.0, 400.0)
+            o.set_source(p["J"], p["x_lo"], p["x_hi"], 300.0)
+            o.set_scheme(scheme)
+            o.set_state(f0, sigma)
+            o.step(1)
+            res.append(o.get_f())
+        d = res[1] - res[0]
+        assert np.abs(d).max() > 1e-6 * np.abs(res[0]).max()  # the schemes differ
+        diffs.append(d)
+    ratio = np.linalg.norm(diffs[0]) / np.linalg.norm(diffs[1])
+    assert ratio == pytest.approx(4.0, rel=1e-8)
+    assert np.allclose(diffs[0], 4.0 * diffs[1], rtol=1e-7, atol=1e-9 * np.abs(diffs[0]).max())
+
+
+def test_lie_ledger_closes():
+    o, f0, sigma, p = _strong_case(14, 12, 10, seed=22)
+    o.set_scheme(1)
+    o.set_state(f0, sigma)
+    o.step(40)
+    L = o.ledger()
+    rhs = L["emit"] - L["pe"] - L["vac"] - L["lv"] + L["inj"]
+    scale = max(abs(L["emit"]), abs(L["pe"]), abs(L["vac"]), abs(L["lv"]), abs(L["inj"]), L["N"])
+    assert abs((L["N"] - L["N0"]) - rhs) < 1e-12 * scale
+    dsig = o.surface_charge() - L["sigma0"]
+    assert dsig / QE == pytest.approx(L["see"] - L["pe"], rel=1e-12)
