@@ -154,6 +154,20 @@ fk_status fk_set_collisions(fk_grid *grid, double T_e_eV, double ln_lambda, int 
  * Default 0. */
 fk_status fk_set_reflection(fk_grid *grid, double R_f);
 
+/* Time scheme of fk_step.  FK_SCHEME_UNSPLIT (the default): one forward-
+ * Euler step with every flux from f^n, fused into one pass over f.
+ * FK_SCHEME_LIE: Lie splitting -- x-advection of f^n (with the wall and
+ * vacuum boundaries) over dt, then the velocity step (v1, v2 advection,
+ * source, collisions) of that intermediate state over dt, both with the
+ * fields of f^n; the surface charge and the wall ledger terms come from f^n
+ * as in the unsplit step.  Sec. 2 states only an explicit upwind update;
+ * the split form runs as two passes over f (the direct-load kernel and one
+ * more buffer of f), and grids using it cannot join a batch.  FK_EINVAL for
+ * another value; FK_ESTATE while the grid is in a batch. */
+#define FK_SCHEME_UNSPLIT 0
+#define FK_SCHEME_LIE 1
+fk_status fk_set_scheme(fk_grid *grid, int scheme);
+
 /* Convergence test of Sec. 2 (paragraph after Eq. 18): the run is saturated
  * at the first step n >= window with |q_n - q_{n-window}| <= rel_tol |q_n|
  * for q = sigma, Gamma_pe and Gamma_see.  Defaults: window 10000, rel_tol
@@ -271,7 +285,7 @@ fk_status fk_density_moment_noalloc(const double *f_dev, int32_t nx, int32_t nv1
  *  - The batch borrows the grids; the caller keeps ownership.  While a grid
  *    belongs to a batch, every call that changes it (fk_step, the setters,
  *    fk_set_f, fk_set_surface_charge, fk_set_collisions, fk_set_reflection,
- *    fk_set_kernel_timing and
+ *    fk_set_scheme, fk_set_kernel_timing and
  *    fk_destroy_grid) returns FK_ESTATE; the getters work and see every
  *    batch step enqueued before them.  fk_batch_destroy releases the grids.
  *  - A grid that meets a sticky device error (FK_ECFL, FK_ENUMERIC,

@@ -126,9 +126,20 @@ cudaError_t enqueue_step(fk_grid* g, int cur, cudaStream_t s, cudaEvent_t ev0, c
   StepArgs a = make_args(g, cur);
   cudaError_t e = cudaSuccess;
   if (ev0) e = cudaEventRecord(ev0, s);
-  if (e == cudaSuccess)
-    e = g->use_stream ? launch_step_stream(a, g->prec, g->prm.collisions != 0, s)
-                      : launch_step(a, g->prec, 0, s);
+  if (e == cudaSuccess) {
+    if (g->scheme == kSchemeLie) {
+      // x-advection of f^n into the intermediate buffer, then the velocity
+      // step of that state into f^{n+1} (both direct-load passes)
+      StepArgs ax = a, av = a;
+      ax.f_out = g->d_f3;
+      av.f_in = g->d_f3;
+      e = launch_step_pass(ax, g->prec, kPassX, s);
+      if (e == cudaSuccess) e = launch_step_pass(av, g->prec, kPassV, s);
+    } else {
+      e = g->use_stream ? launch_step_stream(a, g->prec, g->prm.collisions != 0, s)
+                        : launch_step(a, g->prec, 0, s);
+    }
+  }
   if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
   if (e == cudaSuccess)
     e = launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, g->fin, kModeStep, s);
@@ -185,7 +196,7 @@ void free_grid(fk_grid* g) {
                   g->tab.m1_32, g->tab.m2_32, g->d_bgk, g->d_bgk32, g->part.n, g->part.lv,
                   g->part.pe, g->part.see,
                   g->part.vac, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist,
-                  g->d_stage, g->fin.pre, g->fin.bsum, g->fin.blv, g->fin.counter};
+                  g->d_stage, g->d_f3, g->fin.pre, g->fin.bsum, g->fin.blv, g->fin.counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
@@ -565,6 +576,27 @@ fk_status fk_set_reflection(fk_grid* g, double R_f) {
     return fail(g, FK_EINVAL, "reflection needs a v1 grid symmetric about 0");
   g->prm.refl = R_f;
   return refresh(g, false);  // the state's Gamma_see changes with R_f
+}
+
+fk_status fk_set_scheme(fk_grid* g, int scheme) {
+  if (!g) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
+  if (scheme != FK_SCHEME_UNSPLIT && scheme != FK_SCHEME_LIE)
+    return fail(g, FK_EINVAL, "scheme must be FK_SCHEME_UNSPLIT or FK_SCHEME_LIE");
+  FK_CUDA(g, cudaSetDevice(g->dev));
+  if (scheme == FK_SCHEME_LIE && !g->d_f3)
+    FK_CUDA(g, cudaMalloc(&g->d_f3, (size_t)g->nx * g->nv1 * g->pitch * g->esize));
+  if (scheme != g->scheme) {
+    // the captured graphs hold the other scheme's kernels
+    FK_CUDA(g, cudaStreamSynchronize(g->stream));
+    for (int q = 0; q < 2; q++)
+      if (g->graph[q]) {
+        cudaGraphExecDestroy(g->graph[q]);
+        g->graph[q] = nullptr;
+      }
+  }
+  g->scheme = scheme;
+  return FK_OK;
 }
 
 fk_status fk_set_convergence(fk_grid* g, int64_t window, double rel_tol) {

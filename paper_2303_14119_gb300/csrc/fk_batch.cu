@@ -315,6 +315,8 @@ fk_status fk_batch_create(fk_grid* const* grids, int32_t n, void* cuda_stream, f
     if (g->prec != gs[0]->prec) return bfail(nullptr, FK_EINVAL, who + " has another precision");
     if (!g->use_stream)
       return bfail(nullptr, FK_EINVAL, who + " uses the direct-load step kernel (rows too wide)");
+    if (g->scheme != kSchemeUnsplit)
+      return bfail(nullptr, FK_EINVAL, who + " uses a split time scheme (steps alone only)");
   }
   {
     std::vector<fk_grid*> sorted(gs);

@@ -49,12 +49,23 @@ struct fk_grid {
   int ev_used = 0;              // pairs recorded since the last read
   // batch that steps this grid: while set, calls that change the state are
   // refused and the getters wait for the batch's last enqueued step
+  int scheme = 0;             // kSchemeUnsplit or kSchemeLie
+  void* d_f3 = nullptr;       // intermediate state of the Lie-split step
   fk_batch* batch = nullptr;
   cudaEvent_t batch_done = nullptr;
   std::string err;
 };
 
 namespace fk {
+
+// Passes of the direct-load step kernel: a whole step, the moments of f_in
+// only, and the two passes of the Lie-split step (x-advection with the wall
+// and vacuum boundaries; then v1, v2 advection, source and collisions).
+enum StepPass { kPassFull = 0, kPassMoments = 1, kPassX = 2, kPassV = 3 };
+cudaError_t launch_step_pass(const StepArgs& a, int precision, int mode, cudaStream_t s);
+
+// Time schemes of a grid (fk_set_scheme).
+enum Scheme { kSchemeUnsplit = 0, kSchemeLie = 1 };
 
 // Per-step arguments of the grid with f^n in buffer cur.
 StepArgs make_args(fk_grid* g, int cur);

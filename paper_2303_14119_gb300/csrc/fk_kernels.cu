@@ -5,7 +5,7 @@
 // Paper: Sun et al., arXiv 2303.14119, Sec. 2.
 #include <math.h>
 
-#include "fk_internal.cuh"
+#include "fk_host.cuh"
 
 namespace fk {
 
@@ -264,7 +264,7 @@ struct Acc<float> { using type = float; };
 
 template <typename T>
 __global__ void __launch_bounds__(kStepThreads)
-step_direct_kernel(StepArgs a, int moments_only) {
+step_direct_kernel(StepArgs a, int mode) {
   __shared__ double sh[32];
   __shared__ unsigned s_flags;
   const int nt = a.part.nu;
@@ -273,6 +273,11 @@ step_direct_kernel(StepArgs a, int moments_only) {
   const Params& p = *a.prm;
   if (threadIdx.x == 0) s_flags = a.st->flags;
   __syncthreads();
+  // mode: kPassFull, kPassMoments (moments of f_in only), kPassX (x-advection
+  // with the wall and vacuum boundaries only), kPassV (v1, v2 advection,
+  // source and collisions only); the last two make the Lie-split step
+  const bool moments_only = mode == kPassMoments;
+  const bool xpass = mode == kPassX, vpass = mode == kPassV;
   if (!moments_only && s_flags) return;  // sticky error: freeze the state
   const T* __restrict__ fin = static_cast<const T*>(a.f_in);
   T* __restrict__ fout = static_cast<T*>(a.f_out);
@@ -282,13 +287,13 @@ step_direct_kernel(StepArgs a, int moments_only) {
   tile_rows(a.geom, nv1, t, &i0, &i1, &dir);
   // per-plane coefficients in the arithmetic type (no FP64 work per cell
   // on the FP32 path)
-  const T c1 = sizeof(T) == 8 ? (T)a.c1[k] : (T)a.c1_32[k];
-  const T c2 = (T)p.c2;
+  const T c1 = xpass ? (T)0 : (sizeof(T) == 8 ? (T)a.c1[k] : (T)a.c1_32[k]);
+  const T c2 = xpass ? (T)0 : (T)p.c2;
   const T a1 = c1 < (T)0 ? -c1 : c1, a2 = c2 < (T)0 ? -c2 : c2;
   const double gsee = a.st->g_see;
-  const bool band = k >= p.band_lo && k < p.band_hi;
+  const bool band = !xpass && k >= p.band_lo && k < p.band_hi;
   // BGK relaxation of this plane (Eq. 3): dt nu_k and dt nu_k n_k
-  const bool coll = p.collisions != 0;
+  const bool coll = !xpass && p.collisions != 0;
   const T ca = coll ? (sizeof(T) == 8 ? (T)a.bgk[k] : (T)a.bgk32[k]) : (T)0;
   const T cs = coll ? (sizeof(T) == 8 ? (T)a.bgk[nx + k] : (T)a.bgk32[nx + k]) : (T)0;
   const int ncell = (i1 - i0) * nv2;
@@ -302,7 +307,7 @@ step_direct_kernel(StepArgs a, int moments_only) {
     const T f = fin[idx];
     T fn = f;
     if (!moments_only) {
-      const T cx = sizeof(T) == 8 ? (T)a.tab.cx[i] : (T)a.tab.cx32[i];
+      const T cx = vpass ? (T)0 : (sizeof(T) == 8 ? (T)a.tab.cx[i] : (T)a.tab.cx32[i]);
       T fx = (T)0;
       if (cx > (T)0)
         fx = k > 0 ? fin[idx - plane]
@@ -342,6 +347,7 @@ step_direct_kernel(StepArgs a, int moments_only) {
     }
     if (k == nx - 1 && dir > 0) s_vac += a.tab.v1[i] * (double)fn;
   }
+  if (xpass) return;  // the velocity pass writes every partial sum (uniform)
   const double n_tot = block_sum<kStepThreads>((double)s_n, sh);
   s_lv = block_sum<kStepThreads>(s_lv, sh);
   if (k == 0) {
@@ -360,13 +366,17 @@ step_direct_kernel(StepArgs a, int moments_only) {
   }
 }
 
-cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cudaStream_t s) {
+cudaError_t launch_step_pass(const StepArgs& a, int precision, int mode, cudaStream_t s) {
   const int nblk = a.nx * a.part.nu;
   if (precision == FK_F32)
-    step_direct_kernel<float><<<nblk, kStepThreads, 0, s>>>(a, moments_only);
+    step_direct_kernel<float><<<nblk, kStepThreads, 0, s>>>(a, mode);
   else
-    step_direct_kernel<double><<<nblk, kStepThreads, 0, s>>>(a, moments_only);
+    step_direct_kernel<double><<<nblk, kStepThreads, 0, s>>>(a, mode);
   return cudaGetLastError();
+}
+
+cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cudaStream_t s) {
+  return launch_step_pass(a, precision, moments_only ? kPassMoments : kPassFull, s);
 }
 
 // ---------------------------------------------------------------------------

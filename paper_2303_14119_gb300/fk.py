@@ -21,6 +21,7 @@ from . import _build
 
 FK_OK, FK_EINVAL, FK_ENOMEM, FK_ECUDA, FK_ECFL, FK_ENUMERIC, FK_ETIMEOUT, FK_ESTATE = range(8)
 FK_F64, FK_F32 = 0, 1
+FK_SCHEME_UNSPLIT, FK_SCHEME_LIE = 0, 1
 FK_HISTORY_COLS = 8
 FK_LEDGER_LEN = 9
 STATUS_NAMES = {0: "FK_OK", 1: "FK_EINVAL", 2: "FK_ENOMEM", 3: "FK_ECUDA", 4: "FK_ECFL",
@@ -78,6 +79,7 @@ def load(build_if_missing: bool = True):
         "fk_fowler_nordheim": [D, D, dp, dp],
         "fk_set_collisions": [P, D, D, I],
         "fk_set_reflection": [P, D],
+        "fk_set_scheme": [P, I],
         "fk_set_source_fn": [P, D, D, D, D, D],
         "fk_step": [P, I64],
         "fk_sync": [P],
@@ -195,6 +197,10 @@ def fk_set_collisions(g, T_e_eV=2.0, ln_lambda=10.0, enabled=True):
 
 def fk_set_reflection(g, R_f):
     _check(load().fk_set_reflection(g, float(R_f)), "fk_set_reflection", g)
+
+
+def fk_set_scheme(g, scheme):
+    _check(load().fk_set_scheme(g, int(scheme)), "fk_set_scheme", g)
 
 
 def fk_set_convergence(g, window, rel_tol):
@@ -338,6 +344,9 @@ class Grid:
 
     def set_reflection(self, R_f):
         fk_set_reflection(self.h, R_f)
+
+    def set_scheme(self, scheme):
+        fk_set_scheme(self.h, scheme)
 
     def set_convergence(self, window, rel_tol):
         fk_set_convergence(self.h, window, rel_tol)

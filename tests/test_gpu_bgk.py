@@ -168,3 +168,44 @@ def test_reflection_ledger_and_multi_step():
     with pytest.raises(fk.FkError):
         fk.Grid(8, 8, 8, H, -5e7, V1, -V2, V2).set_reflection(0.5)
     g.close()
+
+
+# ---- Lie splitting (x, then velocity)
+@pytest.mark.parametrize("prec,tol", [(fk.FK_F64, 1e-12), (fk.FK_F32, 3e-7)])
+def test_lie_per_step_all_terms(prec, tol):
+    shape = (18, 40, 34)
+    g, o, _ = setup(shape, prec, 61)
+    for x in (g, o):
+        x.set_reflection(0.2)
+        x.set_scheme(fk.FK_SCHEME_LIE)
+    for _ in range(3):
+        o.set_state(g.get_f(), g.surface_charge())
+        g.step(1)
+        o.step(1)
+        assert rel_l1(g.get_f(), o.get_f()) <= tol
+        assert abs(g.surface_charge() - o.surface_charge()) <= tol * abs(o.surface_charge())
+    g.close()
+
+
+def test_lie_multi_step_ledger_and_switching_back():
+    shape = (22, 32, 28)
+    g, o, lnL = setup(shape, fk.FK_F64, 62, dtnu=0.02)
+    for x in (g, o):
+        x.set_scheme(fk.FK_SCHEME_LIE)
+    g.step(70)  # two graph replays and six direct steps
+    o.step(70)
+    assert rel_l1(g.get_f(), o.get_f()) <= 1e-10
+    lg, lo = g.ledger(), o.ledger()
+    for key in ("emit", "pe", "see", "vac", "lv", "inj"):
+        assert abs(lg[key] - lo[key]) <= 1e-9 * abs(lo[key]), key
+    with pytest.raises(fk.FkError) as e:
+        fk.Batch([g])
+    assert e.value.status == fk.FK_EINVAL
+    # back to the fused unsplit step
+    for x in (g, o):
+        x.set_scheme(fk.FK_SCHEME_UNSPLIT)
+    o.set_state(g.get_f(), g.surface_charge())
+    g.step(33)
+    o.step(33)
+    assert rel_l1(g.get_f(), o.get_f()) <= 1e-10
+    g.close()
