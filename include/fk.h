@@ -224,6 +224,18 @@ fk_status fk_set_f(fk_grid *grid, const double *host_f);
 /* Replace sigma (C/m^2) and restart the run at step 0 like fk_set_f. */
 fk_status fk_set_surface_charge(fk_grid *grid, double sigma);
 
+/* Checkpoints.  fk_get_state writes the whole run into a host buffer the
+ * caller owns: f in its storage precision, the surface charge, fluxes,
+ * ledger, step and sticky flags, the fields and Courant numbers of the
+ * current state, the history ring and every parameter set on the grid.
+ * Call it with buf = NULL to get the size in *len; a smaller *len returns
+ * FK_EINVAL with the size in *len.  fk_set_state restores such a buffer
+ * into a grid created with the same description (shape, precision,
+ * history capacity; FK_EINVAL otherwise): the restored grid then steps on
+ * exactly -- bit for bit -- as the original would have.  Both synchronise. */
+fk_status fk_get_state(fk_grid *grid, void *buf, size_t *len);
+fk_status fk_set_state(fk_grid *grid, const void *buf, size_t len);
+
 /* Grid facts, FK_INFO_LEN doubles: dx, dv1, dv2, dt (s), c2 (signed
  * v2-Courant number a2 dt/dv2), max |c_x|, step kernel (1 streaming,
  * 0 direct-load), v1-row tiles per plane, x-chunks, planes per chunk.
@@ -285,7 +297,7 @@ fk_status fk_density_moment_noalloc(const double *f_dev, int32_t nx, int32_t nv1
  *  - The batch borrows the grids; the caller keeps ownership.  While a grid
  *    belongs to a batch, every call that changes it (fk_step, the setters,
  *    fk_set_f, fk_set_surface_charge, fk_set_collisions, fk_set_reflection,
- *    fk_set_scheme, fk_set_kernel_timing and
+ *    fk_set_scheme, fk_set_state, fk_set_kernel_timing and
  *    fk_destroy_grid) returns FK_ESTATE; the getters work and see every
  *    batch step enqueued before them.  fk_batch_destroy releases the grids.
  *  - A grid that meets a sticky device error (FK_ECFL, FK_ENUMERIC,

@@ -793,6 +793,161 @@ fk_status fk_set_surface_charge(fk_grid* g, double sigma) {
   return flags_status(g, st.flags);
 }
 
+// ---- checkpoints: everything a continued run depends on, so that a grid
+// restored from a checkpoint steps on bit for bit as the original would.
+namespace {
+
+struct StateHeader {
+  char magic[8];
+  int32_t nx, nv1, nv2, precision, pitch, scheme;
+  int64_t hist_cap, f_bytes;
+  // parameters as set (the tables are rebuilt from them)
+  double Ey, Ex_ext, delta_max, A_max, k_s, T_se, J, x_lo, x_hi, T_fe, T_e, ln_lambda;
+  int32_t self_consistent, see_enabled;
+  Params prm;
+  DevState st;
+};
+constexpr char kStateMagic[8] = {'F', 'K', 'S', 'T', 'A', 'T', 'E', '1'};
+
+size_t f_bytes(const fk_grid* g) { return (size_t)g->nx * g->nv1 * g->pitch * g->esize; }
+
+// bytes after the header: f, then ne, Ex, c1 (double [nx]), c1_32 (float
+// [nx]), bgk (double [2 nx]), bgk32 (float [2 nx]), history ring
+size_t state_bytes(const fk_grid* g) {
+  return sizeof(StateHeader) + f_bytes(g) + 3 * g->nx * sizeof(double) + g->nx * sizeof(float) +
+         2 * g->nx * sizeof(double) + 2 * g->nx * sizeof(float) +
+         (size_t)g->prm.hist_cap * FK_HISTORY_COLS * sizeof(double);
+}
+
+}  // namespace
+
+fk_status fk_get_state(fk_grid* g, void* buf, size_t* len) {
+  if (!g || !len) return FK_EINVAL;
+  const size_t need = state_bytes(g);
+  if (!buf) {
+    *len = need;
+    return FK_OK;
+  }
+  if (*len < need) {
+    *len = need;
+    return fail(g, FK_EINVAL, "checkpoint buffer too small (size returned in *len)");
+  }
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  StateHeader h{};
+  memcpy(h.magic, kStateMagic, 8);
+  h.nx = g->nx;
+  h.nv1 = g->nv1;
+  h.nv2 = g->nv2;
+  h.precision = g->prec;
+  h.pitch = g->pitch;
+  h.scheme = g->scheme;
+  h.hist_cap = g->prm.hist_cap;
+  h.f_bytes = (int64_t)f_bytes(g);
+  h.Ey = g->Ey;
+  h.Ex_ext = g->Ex_ext;
+  h.delta_max = g->delta_max;
+  h.A_max = g->A_max;
+  h.k_s = g->k_s;
+  h.T_se = g->T_se;
+  h.J = g->J;
+  h.x_lo = g->x_lo;
+  h.x_hi = g->x_hi;
+  h.T_fe = g->T_fe;
+  h.T_e = g->T_e;
+  h.ln_lambda = g->ln_lambda;
+  h.self_consistent = g->self_consistent;
+  h.see_enabled = g->see_enabled;
+  h.prm = g->prm;
+  h.st = st;
+  unsigned char* p = static_cast<unsigned char*>(buf);
+  memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  struct Part {
+    const void* src;
+    size_t bytes;
+  } parts[] = {{g->d_f[g->base_cur], f_bytes(g)},
+               {g->d_ne, g->nx * sizeof(double)},
+               {g->d_Ex, g->nx * sizeof(double)},
+               {g->d_c1, g->nx * sizeof(double)},
+               {g->d_c1_32, g->nx * sizeof(float)},
+               {g->d_bgk, 2 * g->nx * sizeof(double)},
+               {g->d_bgk32, 2 * g->nx * sizeof(float)},
+               {g->d_hist, (size_t)g->prm.hist_cap * FK_HISTORY_COLS * sizeof(double)}};
+  for (const Part& q : parts) {
+    FK_CUDA(g, cudaMemcpy(p, q.src, q.bytes, cudaMemcpyDeviceToHost));
+    p += q.bytes;
+  }
+  *len = need;
+  return FK_OK;  // a frozen (flagged) state is a valid checkpoint too
+}
+
+fk_status fk_set_state(fk_grid* g, const void* buf, size_t len) {
+  if (!g || !buf) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
+  StateHeader h;
+  if (len < sizeof h) return fail(g, FK_EINVAL, "checkpoint too short");
+  memcpy(&h, buf, sizeof h);
+  if (memcmp(h.magic, kStateMagic, 8) != 0) return fail(g, FK_EINVAL, "not a checkpoint of this library");
+  if (h.nx != g->nx || h.nv1 != g->nv1 || h.nv2 != g->nv2 || h.precision != g->prec ||
+      h.pitch != g->pitch || h.hist_cap != g->prm.hist_cap || h.f_bytes != (int64_t)f_bytes(g))
+    return fail(g, FK_EINVAL,
+                "checkpoint of another grid (shape, precision or history capacity differ)");
+  if (len < state_bytes(g)) return fail(g, FK_EINVAL, "checkpoint truncated");
+  DevState cur;
+  fk_status s = sync_state(g, &cur);
+  if (s != FK_OK) return s;
+  if (h.scheme == kSchemeLie && !g->d_f3)
+    FK_CUDA(g, cudaMalloc(&g->d_f3, f_bytes(g)));
+  // graphs were captured for the old kernel variants
+  for (int q = 0; q < 2; q++)
+    if (g->graph[q]) {
+      cudaGraphExecDestroy(g->graph[q]);
+      g->graph[q] = nullptr;
+    }
+  g->scheme = h.scheme;
+  g->Ey = h.Ey;
+  g->Ex_ext = h.Ex_ext;
+  g->delta_max = h.delta_max;
+  g->A_max = h.A_max;
+  g->k_s = h.k_s;
+  g->T_se = h.T_se;
+  g->J = h.J;
+  g->x_lo = h.x_lo;
+  g->x_hi = h.x_hi;
+  g->T_fe = h.T_fe;
+  g->T_e = h.T_e;
+  g->ln_lambda = h.ln_lambda;
+  g->self_consistent = h.self_consistent;
+  g->see_enabled = h.see_enabled;
+  g->prm = h.prm;
+  if ((s = upload_params(g)) != FK_OK) return s;
+  if ((s = rebuild_tables(g)) != FK_OK) return s;
+  const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof h;
+  struct Part {
+    void* dst;
+    size_t bytes;
+  } parts[] = {{g->d_f[0], f_bytes(g)},
+               {g->d_ne, g->nx * sizeof(double)},
+               {g->d_Ex, g->nx * sizeof(double)},
+               {g->d_c1, g->nx * sizeof(double)},
+               {g->d_c1_32, g->nx * sizeof(float)},
+               {g->d_bgk, 2 * g->nx * sizeof(double)},
+               {g->d_bgk32, 2 * g->nx * sizeof(float)},
+               {g->d_hist, (size_t)g->prm.hist_cap * FK_HISTORY_COLS * sizeof(double)}};
+  for (const Part& q : parts) {
+    FK_CUDA(g, cudaMemcpyAsync(q.dst, p, q.bytes, cudaMemcpyHostToDevice, g->stream));
+    p += q.bytes;
+  }
+  FK_CUDA(g, cudaMemcpyAsync(g->d_st, &h.st, sizeof(DevState), cudaMemcpyHostToDevice, g->stream));
+  FK_CUDA(g, cudaStreamSynchronize(g->stream));
+  g->base_cur = g->enq_cur = 0;
+  g->base_step = h.st.step;
+  g->known_flags = h.st.flags;
+  return FK_OK;
+}
+
 fk_status fk_grid_info(const fk_grid* g, double* out) {
   if (!g || !out) return FK_EINVAL;
   out[0] = g->dx;

@@ -80,6 +80,8 @@ def load(build_if_missing: bool = True):
         "fk_set_collisions": [P, D, D, I],
         "fk_set_reflection": [P, D],
         "fk_set_scheme": [P, I],
+        "fk_get_state": [P, P, C.POINTER(C.c_size_t)],
+        "fk_set_state": [P, P, C.c_size_t],
         "fk_set_source_fn": [P, D, D, D, D, D],
         "fk_step": [P, I64],
         "fk_sync": [P],
@@ -197,6 +199,20 @@ def fk_set_collisions(g, T_e_eV=2.0, ln_lambda=10.0, enabled=True):
 
 def fk_set_reflection(g, R_f):
     _check(load().fk_set_reflection(g, float(R_f)), "fk_set_reflection", g)
+
+
+def fk_get_state(g):
+    """The grid's checkpoint as bytes."""
+    n = C.c_size_t(0)
+    _check(load().fk_get_state(g, None, C.byref(n)), "fk_get_state", g)
+    buf = (C.c_ubyte * n.value)()
+    _check(load().fk_get_state(g, buf, C.byref(n)), "fk_get_state", g)
+    return bytes(buf)
+
+
+def fk_set_state(g, state):
+    buf = (C.c_ubyte * len(state)).from_buffer_copy(state)
+    _check(load().fk_set_state(g, buf, len(state)), "fk_set_state", g)
 
 
 def fk_set_scheme(g, scheme):
@@ -344,6 +360,12 @@ class Grid:
 
     def set_reflection(self, R_f):
         fk_set_reflection(self.h, R_f)
+
+    def checkpoint(self):
+        return fk_get_state(self.h)
+
+    def restore(self, state):
+        fk_set_state(self.h, state)
 
     def set_scheme(self, scheme):
         fk_set_scheme(self.h, scheme)
