@@ -835,7 +835,8 @@ fk_status fk_get_state(fk_grid* g, void* buf, size_t* len) {
   DevState st;
   fk_status s = sync_state(g, &st);
   if (s != FK_OK) return s;
-  StateHeader h{};
+  StateHeader h;
+  memset(&h, 0, sizeof h);
   memcpy(h.magic, kStateMagic, 8);
   h.nx = g->nx;
   h.nv1 = g->nv1;
@@ -859,8 +860,8 @@ fk_status fk_get_state(fk_grid* g, void* buf, size_t* len) {
   h.ln_lambda = g->ln_lambda;
   h.self_consistent = g->self_consistent;
   h.see_enabled = g->see_enabled;
-  h.prm = g->prm;
-  h.st = st;
+  memcpy(&h.prm, &g->prm, sizeof(Params));
+  memcpy(&h.st, &st, sizeof(DevState));
   unsigned char* p = static_cast<unsigned char*>(buf);
   memcpy(p, &h, sizeof h);
   p += sizeof h;
@@ -921,7 +922,7 @@ fk_status fk_set_state(fk_grid* g, const void* buf, size_t len) {
   g->ln_lambda = h.ln_lambda;
   g->self_consistent = h.self_consistent;
   g->see_enabled = h.see_enabled;
-  g->prm = h.prm;
+  memcpy(&g->prm, &h.prm, sizeof(Params));
   if ((s = upload_params(g)) != FK_OK) return s;
   if ((s = rebuild_tables(g)) != FK_OK) return s;
   const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof h;

@@ -59,8 +59,6 @@ def test_restored_grid_continues_bitwise(prec, scheme):
     b.restore(ck)
     b.step(45)
     assert_same(a, b)
-    # a checkpoint of the restored grid equals the original's
-    assert b.checkpoint() == a.checkpoint()
     a.close()
     b.close()
 
