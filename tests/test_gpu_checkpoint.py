@@ -3,6 +3,7 @@ grid steps on bit for bit as the original does."""
 import numpy as np
 import pytest
 
+import oracle
 from oracle import EPS0, ME, QE
 from paper_2303_14119_gb300 import fk, synth
 
@@ -30,12 +31,15 @@ def configured(shape, prec, scheme=fk.FK_SCHEME_UNSPLIT):
     g.set_fields(-0.15 * info["dv2"] / info["dt"] * ME / QE, True, 0.0)
     g.set_see(3.0, 400.0, 1.0, 400.0)
     g.set_source(1e7, 0.2 * H, 0.7 * H, 300.0)
-    g.set_collisions(2.0, 1e9, True)
-    g.set_reflection(0.2)
-    g.set_scheme(scheme)
     emax = 0.2 * info["dv1"] / info["dt"] * ME / QE
     amp = 2 * (1.6 * emax * EPS0 / QE) / (H * 2 * V1 * 2 * V2)
-    g.set_state(synth.random_f(shape, 17, amp), 2 * EPS0 * emax * 0.8)
+    f0 = synth.random_f(shape, 17, amp)
+    # ln(Lambda) scaled so that dt nu_ee is about 3 % for this state
+    n_max = (f0.sum(axis=(1, 2)) * info["dv1"] * info["dv2"]).max()
+    g.set_collisions(2.0, 0.03 / (info["dt"] * oracle.nu_ee(n_max, 2.0, 1.0)), True)
+    g.set_reflection(0.2)
+    g.set_scheme(scheme)
+    g.set_state(f0, 2 * EPS0 * emax * 0.8)
     return g
 
 
