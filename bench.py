@@ -259,13 +259,24 @@ def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True):
     assert stream, "e2e_arm needs a non-default current stream"
     grids = make_grids(fk, w, precision, stream)
     nx = w["nx"]
-    out_f = torch.empty(f0_pinned.shape, dtype=torch.float64, pin_memory=True).numpy()
+    # an FP32 grid exchanges f with the host in its own storage type
+    f32 = precision == fk.FK_F32
+    if f32:
+        f_host = torch.empty(f0_pinned.shape, dtype=torch.float32, pin_memory=True).numpy()
+        f_host[...] = f0_pinned
+    else:
+        f_host = f0_pinned
+    out_f = torch.empty(f0_pinned.shape, dtype=torch.float32 if f32 else torch.float64,
+                        pin_memory=True).numpy()
     ne = np.empty(nx)
     ex = np.empty(nx)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for g in grids:
-        g.set_f(f0_pinned)
+        if f32:
+            g.set_f32(f_host)
+        else:
+            g.set_f(f_host)
     b = fk.Batch(grids, stream) if batch else None
     for _ in range(steps):
         if b is not None:
@@ -276,7 +287,10 @@ def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True):
             fk.fk_moments(g.h, nx, ne, ex)
             g.surface_charge()
     for g in grids:
-        g.get_f(out_f)
+        if f32:
+            g.get_f32(out_f)
+        else:
+            g.get_f(out_f)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     if b is not None:
@@ -285,7 +299,7 @@ def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True):
         g.close()
     cells = w["nx"] * w["nv1"] * w["nv2"]
     n = len(grids)
-    h2d = n * f0_pinned.nbytes / steps
+    h2d = n * f_host.nbytes / steps
     d2h = n * (2 * nx * 8 + 2 * 8 + 8) + n * out_f.nbytes / steps
     return dict(value=n * cells * steps / dt, unit=UNIT, h2d_bytes_per_step=int(h2d),
                 d2h_bytes_per_step=int(d2h), steps=steps)

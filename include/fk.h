@@ -221,6 +221,12 @@ fk_status fk_get_f(fk_grid *grid, double *host_f);
  * grid rounds each value to nearest. */
 fk_status fk_set_f(fk_grid *grid, const double *host_f);
 
+/* FP32 grids only (FK_EINVAL otherwise): fk_get_f and fk_set_f with host
+ * arrays in the grid's own storage type, float [nx][nv1][nv2]: one strided
+ * copy each way, no conversion and half the bytes of the FP64 forms. */
+fk_status fk_get_f32(fk_grid *grid, float *host_f);
+fk_status fk_set_f32(fk_grid *grid, const float *host_f);
+
 /* Replace sigma (C/m^2) and restart the run at step 0 like fk_set_f. */
 fk_status fk_set_surface_charge(fk_grid *grid, double sigma);
 
@@ -296,7 +302,7 @@ fk_status fk_density_moment_noalloc(const double *f_dev, int32_t nx, int32_t nv1
  * Ownership and state rules:
  *  - The batch borrows the grids; the caller keeps ownership.  While a grid
  *    belongs to a batch, every call that changes it (fk_step, the setters,
- *    fk_set_f, fk_set_surface_charge, fk_set_collisions, fk_set_reflection,
+ *    fk_set_f, fk_set_f32, fk_set_surface_charge, fk_set_collisions, fk_set_reflection,
  *    fk_set_scheme, fk_set_state, fk_set_kernel_timing and
  *    fk_destroy_grid) returns FK_ESTATE; the getters work and see every
  *    batch step enqueued before them.  fk_batch_destroy releases the grids.

@@ -776,6 +776,40 @@ fk_status fk_set_f(fk_grid* g, const double* host_f) {
   return flags_status(g, st.flags);
 }
 
+fk_status fk_get_f32(fk_grid* g, float* host_f) {
+  if (!g || !host_f) return FK_EINVAL;
+  if (g->prec != FK_F32) return fail(g, FK_EINVAL, "fk_get_f32 needs an FP32 grid");
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  // one strided copy from the row-pitch layout to the dense host array
+  FK_CUDA(g, cudaMemcpy2DAsync(host_f, g->nv2 * sizeof(float), g->d_f[g->base_cur],
+                               g->pitch * sizeof(float), g->nv2 * sizeof(float),
+                               (size_t)g->nx * g->nv1, cudaMemcpyDeviceToHost, g->stream));
+  FK_CUDA(g, cudaStreamSynchronize(g->stream));
+  return flags_status(g, st.flags);
+}
+
+fk_status fk_set_f32(fk_grid* g, const float* host_f) {
+  if (!g || !host_f) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
+  if (g->prec != FK_F32) return fail(g, FK_EINVAL, "fk_set_f32 needs an FP32 grid");
+  DevState st;
+  fk_status s = sync_state(g, &st);
+  if (s != FK_OK) return s;
+  FK_CUDA(g, cudaMemcpy2DAsync(g->d_f[0], g->pitch * sizeof(float), host_f,
+                               g->nv2 * sizeof(float), g->nv2 * sizeof(float),
+                               (size_t)g->nx * g->nv1, cudaMemcpyHostToDevice, g->stream));
+  g->base_cur = g->enq_cur = 0;
+  g->base_step = 0;
+  FK_CUDA(g, cudaMemsetAsync(&g->d_st->flags, 0, sizeof(unsigned), g->stream));
+  g->known_flags = 0;
+  s = evaluate(g, kModeReset);
+  if (s != FK_OK) return s;
+  if ((s = sync_state(g, &st)) != FK_OK) return s;
+  return flags_status(g, st.flags);
+}
+
 fk_status fk_set_surface_charge(fk_grid* g, double sigma) {
   if (!g || !isfinite(sigma)) return g ? fail(g, FK_EINVAL, "sigma must be finite") : FK_EINVAL;
   FK_NOT_IN_BATCH(g);

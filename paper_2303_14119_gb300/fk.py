@@ -80,6 +80,8 @@ def load(build_if_missing: bool = True):
         "fk_set_collisions": [P, D, D, I],
         "fk_set_reflection": [P, D],
         "fk_set_scheme": [P, I],
+        "fk_get_f32": [P, fp],
+        "fk_set_f32": [P, fp],
         "fk_get_state": [P, P, C.POINTER(C.c_size_t)],
         "fk_set_state": [P, P, C.c_size_t],
         "fk_set_source_fn": [P, D, D, D, D, D],
@@ -289,6 +291,20 @@ def fk_set_f(g, f):
     _check(load().fk_set_f(g, _dp(f)), "fk_set_f", g)
 
 
+def fk_get_f32(g, shape, out=None):
+    n = int(np.prod(shape))
+    out = np.empty(shape, dtype=np.float32) if out is None else out
+    if out.dtype != np.float32 or out.size != n or not out.flags.c_contiguous:
+        raise ValueError("out must be a contiguous FP32 array of %d elements" % n)
+    _check(load().fk_get_f32(g, out.ctypes.data_as(C.POINTER(C.c_float))), "fk_get_f32", g)
+    return out
+
+
+def fk_set_f32(g, f):
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    _check(load().fk_set_f32(g, f.ctypes.data_as(C.POINTER(C.c_float))), "fk_set_f32", g)
+
+
 def fk_set_surface_charge(g, sigma):
     _check(load().fk_set_surface_charge(g, float(sigma)), "fk_set_surface_charge", g)
 
@@ -399,6 +415,12 @@ class Grid:
 
     def set_f(self, f):
         fk_set_f(self.h, f)
+
+    def get_f32(self, out=None):
+        return fk_get_f32(self.h, self.shape, out)
+
+    def set_f32(self, f):
+        fk_set_f32(self.h, f)
 
     def set_state(self, f, sigma):
         fk_set_f(self.h, f)

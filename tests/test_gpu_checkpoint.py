@@ -82,3 +82,18 @@ def test_foreign_or_damaged_checkpoints_are_refused():
         assert e.value.status == fk.FK_EINVAL
     b.restore(ck)
     assert np.array_equal(a.get_f(), b.get_f())
+
+
+def test_fp32_host_exchange_matches_the_fp64_forms():
+    shape = (9, 20, 18)
+    g = new_grid(shape, fk.FK_F32)
+    f = synth.random_f(shape, 5, 1e9)
+    g.set_f32(f.astype(np.float32))
+    a = g.get_f32()
+    assert np.array_equal(a, f.astype(np.float32))
+    assert np.array_equal(g.get_f(), a.astype(np.float64))
+    g.set_f(f)  # the FP64 form rounds each value to nearest, the same
+    assert np.array_equal(g.get_f32(), a)
+    with pytest.raises(fk.FkError):
+        new_grid(shape, fk.FK_F64).set_f32(f.astype(np.float32))
+    g.close()
