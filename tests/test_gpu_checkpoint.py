@@ -87,7 +87,7 @@ def test_foreign_or_damaged_checkpoints_are_refused():
 def test_fp32_host_exchange_matches_the_fp64_forms():
     shape = (9, 20, 18)
     g = new_grid(shape, fk.FK_F32)
-    f = synth.random_f(shape, 5, 1e9)
+    f = synth.random_f(shape, 5, 1e2)  # weak enough that its field keeps the CFL bound
     g.set_f32(f.astype(np.float32))
     a = g.get_f32()
     assert np.array_equal(a, f.astype(np.float32))
