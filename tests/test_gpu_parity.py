@@ -382,3 +382,40 @@ def test_coarse_copy_fp32_against_oracle():
     assert rel_l1(g.get_f(), o.get_f()) <= 1e-5
     assert rel(g.surface_charge(), o.surface_charge()) <= 1e-4
     g.close()
+
+
+# ----------------------------------------------------------------- limits
+@pytest.mark.parametrize("prec,tol", [(fk.FK_F64, 1e-12), (fk.FK_F32, 3e-7)])
+def test_longest_x_range(prec, tol):
+    """nx = 8192, the largest the ABI accepts: the finalize kernel runs its
+    most blocks (64) and the Gauss-law prefix spans them all."""
+    shape = (8192, 4, 8)
+    g, o = make_pair(shape, prec=prec)
+    f0, sigma = strong_physics(g, o, shape, seed=81)
+    g.set_state(f0, sigma)
+    for _ in range(2):
+        o.set_state(g.get_f(), g.surface_charge())
+        g.step(1)
+        o.step(1)
+        assert rel_l1(g.get_f(), o.get_f()) <= tol
+        ne_g, ex_g, _, _ = g.moments()
+        ne_o, ex_o, _, _ = o.moments()
+        assert np.abs(ex_g - ex_o).max() <= 10 * tol * np.abs(ex_o).max()
+    g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(fk.FK_F64, 1e-12), (fk.FK_F32, 3e-7)])
+def test_rows_too_wide_for_the_streaming_kernel(prec, tol):
+    """v2 rows wider than one streaming tile (nv2 = 7300) fall back to the
+    direct-load kernel, which must give the same step."""
+    shape = (3, 4, 7300)
+    g, o = make_pair(shape, prec=prec)
+    assert g.info()["kernel"] == "direct"
+    f0, sigma = strong_physics(g, o, shape, seed=82)
+    g.set_state(f0, sigma)
+    for _ in range(2):
+        o.set_state(g.get_f(), g.surface_charge())
+        g.step(1)
+        o.step(1)
+        assert rel_l1(g.get_f(), o.get_f()) <= tol
+    g.close()
