@@ -8,7 +8,7 @@ and to log10 of its saturation time (the convergence test of Sec. 2).  It is
 trained on runs of the batched solver (fk_batch_*), with the network's
 forward, backward and Adam kernels on the tensor cores (fk_mlp_*), and used
 to warm-start the surface charge of new runs and to triage sweep points.
-The paper has no surrogate; the solver stays the judge of its error.
+The paper has no surrogate; its error is always measured against the solver.
 
 ``python -m paper_2303_14119_gb300.surrogate --out DIR`` runs the whole
 pipeline (data, training, evaluation, warm starts) and writes a JSON report.
