@@ -1,6 +1,6 @@
 """Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
 
-Tolerances (stated in the task's numerics targets and derived in DESIGN):
+Tolerances (the stated numeric targets, and the bounds rounding gives them):
   FP64 path: relative L1 of f <= 1e-12 after one step from the same state;
   FP32 path: relative L1 of f <= 1e-5 after 1000 steps; surface charge 1e-4.
 Scalars (sigma, fluxes, moments) of the FP64 path agree to 1e-12 relative
