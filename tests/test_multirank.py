@@ -53,3 +53,23 @@ def test_single_process_defaults():
     import bench
     assert bench.reduce_over_ranks(7.0, None) == 7.0
     assert bench.job_throughput(1, 3, 10, 2, 1000.0) == pytest.approx(60.0)
+
+
+def test_reference_arm_prints_its_json_line():
+    """bench.py --impl reference times the CPU oracle and prints one JSON line
+    with the contract's keys (no GPU needed)."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--steps", "2", "--warmup", "1", "--workload", "small_64x48x48"],
+                         capture_output=True, text=True, timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "cpu_baseline", "e2e", "config"):
+        assert key in line, key
+    assert line["value"] > 0 and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
