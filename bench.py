@@ -230,7 +230,7 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
                     ctas_per_sm=info["ctas_per_sm"], chunk_len=b.chunks(),
                     n_tiles=grids[0].info()["n_tiles"], autotune_steps=tuned)
         cells_per_launch = cells * len(grids)
-        gpu_launches = 2 * steps
+        gpu_launches = (info["step_launches"] + 1) * steps  # step kernel(s) + finalize
         b.close()
     else:
         launches, kms = 0, 0.0
@@ -530,7 +530,12 @@ def run_sweep(args):
     res = dict(launches=launches, kernel_ms=kms, cells_per_launch=cells)
     roof = roofline(res, args.precision, peak, peak_kind)
     if roof is not None:
-        roof["kernel"] = "batched fused upwind step (all %d instances per launch)" % len(ins)
+        if info["step_launches"] == 1:
+            roof["kernel"] = "batched fused upwind step (all %d instances per launch)" % len(ins)
+        else:  # whole-CTA and half-CTA units: two launches, timed together per step
+            roof["kernel"] = ("batched fused upwind step (all %d instances per step: one launch "
+                              "of whole-CTA units, one of half-CTA units, timed together)"
+                              % len(ins))
         roof["traffic"] = None
     line = {
         "metric": "batched instances/hr (%d steps per instance)" % per_inst, "value": value,
@@ -556,7 +561,7 @@ def run_sweep(args):
                      "units_per_launch": info["units"],
                      "chunk_len_range": [min(chunks), max(chunks)]},
         "roofline": roof,
-        "gpu_launches": 2 * steps,
+        "gpu_launches": (info["step_launches"] + 1) * steps,  # step kernel(s) + finalize
         "clocks": ck,
     }
     if rank == 0:

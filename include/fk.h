@@ -244,9 +244,12 @@ fk_status fk_set_state(fk_grid *grid, const void *buf, size_t len);
 
 /* Grid facts, FK_INFO_LEN doubles: dx, dv1, dv2, dt (s), c2 (signed
  * v2-Courant number a2 dt/dv2), max |c_x|, step kernel (1 streaming,
- * 0 direct-load), v1-row tiles per plane, x-chunks, planes per chunk.
+ * 0 direct-load), v1-row tiles per plane, x-chunks, planes per chunk,
+ * work units per CTA of the streaming kernel (2 where each sign half of the
+ * v1 rows fits the tile of a half-CTA unit, else 1; the environment
+ * variable FK_STREAM_HALF=0 at grid creation keeps 1).
  * Host-side, no synchronisation. */
-#define FK_INFO_LEN 10
+#define FK_INFO_LEN 11
 fk_status fk_grid_info(const fk_grid *grid, double *out);
 
 /* Kernel timing (tracing).  enabled != 0: later fk_step calls launch each
@@ -356,11 +359,13 @@ fk_status fk_batch_autotune(fk_batch *batch, int32_t steps_per_trial, int64_t *s
 fk_status fk_batch_get_chunks(const fk_batch *batch, int32_t *chunk_len);
 fk_status fk_batch_set_chunks(fk_batch *batch, const int32_t *chunk_len);
 
-/* Batch facts, FK_BATCH_INFO_LEN doubles: grids, work units of one step
- * kernel launch, finalize blocks, dynamic shared memory per CTA (bytes),
- * CTAs per SM, phase-space cells of all grids, size buckets, batch steps
- * enqueued.  Host-side, no synchronisation. */
-#define FK_BATCH_INFO_LEN 8
+/* Batch facts, FK_BATCH_INFO_LEN doubles: grids, work units of one batch
+ * step, finalize blocks, dynamic shared memory per CTA (bytes), CTAs per
+ * SM, phase-space cells of all grids, size buckets, batch steps enqueued,
+ * CTAs of whole-CTA units, CTAs of half units (two to a CTA).  A batch step
+ * launches the step kernel once per nonzero CTA count, then the finalize
+ * kernel.  Host-side, no synchronisation. */
+#define FK_BATCH_INFO_LEN 10
 fk_status fk_batch_info(const fk_batch *batch, double *out);
 
 /* Kernel timing for the batch, as fk_set_kernel_timing / fk_kernel_timing:

@@ -233,7 +233,9 @@ fk_status build_graph(fk_grid* g, int parity) {
 }
 
 // Tiles of v1 rows (never straddling the sign change of v1) and chunks of
-// x-planes: one streaming CTA per (tile, chunk), about one wave of CTAs.
+// x-planes: one streaming unit per (tile, chunk), about one wave of them.
+// Where each sign half of the v1 rows fits the tile of a half-CTA unit,
+// units run two to a CTA (FK_STREAM_HALF=0 keeps one unit per CTA).
 fk_status plan_geometry(fk_grid* g) {
   const char* env = getenv("FK_STEP_KERNEL");
   FK_CUDA(g, cudaSetDevice(g->dev));
@@ -241,7 +243,7 @@ fk_status plan_geometry(fk_grid* g) {
   FK_CUDA(g, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->dev));
   FK_CUDA(g, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, g->dev));
   FK_CUDA(g, cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, g->dev));
-  int ti_max = stream_tile_rows(g->prec, g->pitch, smem_sm, reserved);
+  int ti_max = stream_tile_rows(g->prec, g->pitch, smem_sm, reserved, false);
   g->use_stream = ti_max > 0 && !(env && strcmp(env, "direct") == 0);
   if (!g->use_stream) ti_max = std::max(1, 4096 / g->pitch);
   int i_neg = 0;
@@ -249,6 +251,15 @@ fk_status plan_geometry(fk_grid* g) {
     if (g->desc.v1_min + ((double)i + 0.5) * g->dv1 <= 0.0) i_neg++;
   Geom& m = g->geom;
   m.i_neg = i_neg;
+  m.half = 0;
+  const char* env_half = getenv("FK_STREAM_HALF");
+  if (g->use_stream && !(env_half && strcmp(env_half, "0") == 0)) {
+    const int ti_half = stream_tile_rows(g->prec, g->pitch, smem_sm, reserved, true);
+    if (ti_half > 0 && std::max(i_neg, g->nv1 - i_neg) <= ti_half) {
+      m.half = 1;
+      ti_max = ti_half;
+    }
+  }
   auto split = [&](int rows, int* nt, int* ti) {
     if (rows <= 0) {
       *nt = 0;
@@ -266,14 +277,15 @@ fk_status plan_geometry(fk_grid* g) {
   m.n_chunks = 1;
   m.chunk_len = g->nx;
   if (g->use_stream) {
-    const int per_sm =
-        stream_ctas_per_sm(g->prec, stream_smem_bytes(g->prec, m.stage_elems, g->pitch));
+    const int per_sm = stream_ctas_per_sm(g->prec, stream_cta_smem_bytes(g->prec, m, g->pitch));
     if (per_sm <= 0) {
       g->use_stream = false;
+      m.half = 0;
     } else {
-      // about one wave: (tiles x chunks) CTAs for the resident slots, and at
-      // least 4 planes per chunk (the upwind plane is loaded once per chunk)
-      const int nc = std::max(1, std::min(sms * per_sm / m.n_tiles, (g->nx + 3) / 4));
+      // about one wave: (tiles x chunks) units for the resident slots, and
+      // at least 4 planes per chunk (the upwind plane is loaded once per chunk)
+      const int slots = sms * per_sm * (m.half ? 2 : 1);
+      const int nc = std::max(1, std::min(slots / m.n_tiles, (g->nx + 3) / 4));
       m.chunk_len = (g->nx + nc - 1) / nc;
       m.n_chunks = (g->nx + m.chunk_len - 1) / m.chunk_len;
     }
@@ -995,6 +1007,7 @@ fk_status fk_grid_info(const fk_grid* g, double* out) {
   out[7] = g->geom.n_tiles;
   out[8] = g->geom.n_chunks;
   out[9] = g->geom.chunk_len;
+  out[10] = g->geom.half ? 2.0 : 1.0;
   return FK_OK;
 }
 

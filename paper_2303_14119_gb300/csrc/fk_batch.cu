@@ -45,11 +45,14 @@ struct fk_batch {
   long long steps = 0;         // batch steps enqueued
   double cells = 0;            // phase-space cells of all grids
   BatchInst* d_inst = nullptr; // [2][n]: grid arguments for even / odd batch steps
-  int2* d_units = nullptr;     // [max_units] work units, largest first
+  int2* d_units = nullptr;     // [max_units] whole-CTA work units, largest first
   int n_units = 0, max_units = 0;
+  int4* d_pairs = nullptr;     // [max_pairs] CTAs of two half units, largest first
+  int n_pairs = 0, max_pairs = 0;
   int2* d_fblk = nullptr;      // [n_fblk] finalize blocks
   int n_fblk = 0;
-  size_t smem = 0;             // dynamic shared memory per CTA of the step kernel
+  size_t smem = 0;             // dynamic shared memory per CTA (whole-CTA units)
+  int half_bytes = 0;          // shared memory of one half unit's region
   int per_sm = 0, sms = 0;
   bool dirty = true;           // units / arguments must be re-uploaded
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -132,10 +135,34 @@ std::vector<int2> plan_units(const fk_batch* b) {
   return out;
 }
 
+// Split a unit list into the whole-CTA units and the CTAs of half units,
+// two to a CTA in list order (so that a pair's units are of about the same
+// size; the second half of a last odd one stays idle).
+void split_units(const fk_batch* b, const std::vector<int2>& units, std::vector<int2>* whole,
+                 std::vector<int4>* pairs) {
+  whole->clear();
+  pairs->clear();
+  bool open = false;  // the last pair's second half is free
+  for (const int2& u : units) {
+    if (!b->grids[u.x]->geom.half) {
+      whole->push_back(u);
+    } else if (open) {
+      pairs->back().z = u.x;
+      pairs->back().w = u.y;
+      open = false;
+    } else {
+      pairs->push_back(make_int4(u.x, u.y, -1, 0));
+      open = true;
+    }
+  }
+}
+
 // Default chunking: units of about (all cells) / (kDefaultWaves x resident
 // CTAs), at least kMinChunk planes, one chunk if the grid is smaller.
 void default_chunks(fk_batch* b) {
-  const double slots = (double)b->sms * b->per_sm;
+  bool all_half = true;
+  for (const fk_grid* g : b->grids) all_half = all_half && g->geom.half;
+  const double slots = (double)b->sms * b->per_sm * (all_half ? 2 : 1);  // unit slots
   const double target = b->cells / (kDefaultWaves * slots);
   for (int i = 0; i < b->n; i++) {
     const fk_grid* g = b->grids[i];
@@ -184,7 +211,9 @@ fk_status upload_plan(fk_batch* b) {
       bi.a.geom = batch_geom(b, i);
       bi.o = FinOut{g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, g->fin};
     }
-  const std::vector<int2> units = plan_units(b);
+  std::vector<int2> units;
+  std::vector<int4> pairs;
+  split_units(b, plan_units(b), &units, &pairs);
   BK_CUDA(b, cudaStreamSynchronize(b->stream));
   drop_graphs(b);
   if ((int)units.size() > b->max_units) {
@@ -194,11 +223,22 @@ fk_status upload_plan(fk_batch* b) {
     BK_CUDA(b, cudaMalloc(&b->d_units, units.size() * sizeof(int2)));
     b->max_units = (int)units.size();
   }
+  if ((int)pairs.size() > b->max_pairs) {
+    if (b->d_pairs) BK_CUDA(b, cudaFree(b->d_pairs));
+    b->d_pairs = nullptr;
+    b->max_pairs = 0;
+    BK_CUDA(b, cudaMalloc(&b->d_pairs, pairs.size() * sizeof(int4)));
+    b->max_pairs = (int)pairs.size();
+  }
   b->n_units = (int)units.size();
+  b->n_pairs = (int)pairs.size();
   BK_CUDA(b, cudaMemcpyAsync(b->d_inst, h.data(), h.size() * sizeof(BatchInst),
                              cudaMemcpyHostToDevice, b->stream));
   if (b->n_units)
     BK_CUDA(b, cudaMemcpyAsync(b->d_units, units.data(), units.size() * sizeof(int2),
+                               cudaMemcpyHostToDevice, b->stream));
+  if (b->n_pairs)
+    BK_CUDA(b, cudaMemcpyAsync(b->d_pairs, pairs.data(), pairs.size() * sizeof(int4),
                                cudaMemcpyHostToDevice, b->stream));
   BK_CUDA(b, cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
   b->dirty = false;
@@ -213,8 +253,8 @@ cudaError_t enqueue_batch_step(fk_batch* b, int p, cudaStream_t s, cudaEvent_t e
   cudaError_t e = cudaSuccess;
   if (ev0) e = cudaEventRecord(ev0, s);
   if (e == cudaSuccess)
-    e = launch_step_stream_batch(inst, b->d_units, b->n_units, b->prec, b->padded, b->bgk,
-                                 b->smem, s);
+    e = launch_step_stream_batch(inst, b->d_units, b->n_units, b->d_pairs, b->n_pairs, b->prec,
+                                 b->padded, b->bgk, b->smem, b->half_bytes, s);
   if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
   if (e == cudaSuccess) e = launch_finalize_batch(inst, b->d_fblk, b->n_fblk, s);
   return e;
@@ -286,7 +326,7 @@ void free_batch(fk_batch* b) {
     DevState st;
     sync_state(g, &st);
   }
-  void* ptrs[] = {b->d_inst, b->d_units, b->d_fblk};
+  void* ptrs[] = {b->d_inst, b->d_units, b->d_pairs, b->d_fblk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
@@ -357,7 +397,11 @@ fk_status fk_batch_create(fk_grid* const* grids, int32_t n, void* cuda_stream, f
   std::vector<int2> fblk;
   for (int i = 0; i < n; i++) {
     fk_grid* g = gs[i];
-    b->smem = std::max(b->smem, stream_smem_bytes(g->prec, g->geom.stage_elems, g->pitch));
+    if (g->geom.half)
+      b->half_bytes = std::max(
+          b->half_bytes, (int)stream_half_bytes(g->prec, g->geom.stage_elems, g->pitch));
+    else
+      b->smem = std::max(b->smem, stream_smem_bytes(g->prec, g->geom.stage_elems, g->pitch));
     if (g->pitch != g->nv2) b->padded = true;
     if (g->prm.collisions) b->bgk = true;
     b->cells += (double)g->nx * g->nv1 * g->nv2;
@@ -371,7 +415,7 @@ fk_status fk_batch_create(fk_grid* const* grids, int32_t n, void* cuda_stream, f
     }
     b->cur0[i] = g->enq_cur;
   }
-  b->per_sm = stream_ctas_per_sm(b->prec, b->smem);
+  b->per_sm = stream_ctas_per_sm(b->prec, std::max(b->smem, 2 * (size_t)b->half_bytes));
   if (b->per_sm <= 0) {
     free_batch(b);
     return bfail(nullptr, FK_EINVAL, "the grids' shared-memory plans do not fit an SM");
@@ -466,16 +510,22 @@ fk_status fk_batch_set_chunks(fk_batch* b, const int32_t* chunk_len) {
 
 fk_status fk_batch_info(const fk_batch* b, double* out) {
   if (!b || !out) return FK_EINVAL;
-  // the unit count of the chunking in force (re-planned if it changed)
-  const int units = b->dirty ? (int)plan_units(b).size() : b->n_units;
+  // the units and CTAs of the chunking in force (planned on the host)
+  std::vector<int2> whole;
+  std::vector<int4> pairs;
+  split_units(b, plan_units(b), &whole, &pairs);
+  int halves = 2 * (int)pairs.size();
+  if (!pairs.empty() && pairs.back().z < 0) halves -= 1;
   out[0] = b->n;
-  out[1] = units;
+  out[1] = (double)whole.size() + halves;
   out[2] = b->n_fblk;
-  out[3] = (double)b->smem;
+  out[3] = (double)std::max(b->smem, 2 * (size_t)b->half_bytes);
   out[4] = b->per_sm;
   out[5] = b->cells;
   out[6] = b->n_buckets;
   out[7] = (double)b->steps;
+  out[8] = (double)whole.size();
+  out[9] = (double)pairs.size();
   return FK_OK;
 }
 

@@ -110,6 +110,7 @@ struct Geom {
   int t_neg, n_tiles;  // tiles in the lower half, tiles in total
   int chunk_len, n_chunks;
   int stage_elems;     // elements of one shared-memory stage
+  int half;            // 1: units run two to a CTA, one per half (thin tiles)
 };
 
 __host__ __device__ inline void tile_rows(const Geom& g, int nv1, int t, int* i0, int* i1,
@@ -181,16 +182,24 @@ cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cuda
 // Streaming step: one CTA per (tile, chunk), bulk-async staged planes.
 cudaError_t launch_step_stream(const StepArgs& a, int precision, bool bgk, cudaStream_t s);
 // Rows per tile of the streaming kernel for this precision and row pitch
-// so that two CTAs fit on an SM (0 if a row does not fit), its shared
-// memory per CTA, resident CTAs per SM.
-int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per_block);
+// so that two CTAs fit on an SM (half: a unit on half a CTA, two units per
+// CTA; 0 if a row does not fit); the shared memory of one unit, of one
+// half-CTA region and of a CTA of grid geometry gm; resident CTAs per SM.
+int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per_block,
+                     bool half);
 size_t stream_smem_bytes(int precision, int stage_elems, int pitch);
+size_t stream_half_bytes(int precision, int stage_elems, int pitch);
+size_t stream_cta_smem_bytes(int precision, const Geom& gm, int pitch);
 int stream_ctas_per_sm(int precision, size_t smem_bytes);
-// Batched streaming step: CTA b runs unit units[b] = (grid index into inst,
-// tile + n_tiles * chunk of that grid); smem_bytes >= every grid's
-// stream_smem_bytes.  padded: some grid has pitch > nv2.
+// Batched streaming step: one launch over the whole-CTA units, CTA b
+// running units[b] = (grid index into inst, tile + n_tiles * chunk of that
+// grid) with smem_bytes >= every such grid's stream_smem_bytes; then one
+// launch over the half units, CTA b running pairs[b] = (grid, unit, grid2,
+// unit2; grid2 < 0: the second half idle), each half in a region of
+// half_bytes.  padded: some grid has pitch > nv2.
 cudaError_t launch_step_stream_batch(const BatchInst* inst, const int2* units, int n_units,
-                                     int precision, bool padded, bool bgk, size_t smem_bytes,
+                                     const int4* pairs, int n_pairs, int precision, bool padded,
+                                     bool bgk, size_t smem_bytes, int half_bytes,
                                      cudaStream_t s);
 // Batched finalize (step mode): block b finalizes block blocks[b].y of grid
 // blocks[b].x; every grid's blocks 0 .. finalize_blocks(nx) - 1 appear once.

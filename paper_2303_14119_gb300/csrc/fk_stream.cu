@@ -33,9 +33,14 @@ namespace fk {
 
 namespace {
 
-constexpr int kThreads = 224;            // consumer threads (7 warps)
-constexpr int kWarps = kThreads / 32;    // consumer warps; one producer warp follows
+constexpr int kThreads = 224;            // consumer threads of a whole-CTA unit (7 warps)
+constexpr int kWarps = kThreads / 32;    // its consumer warps; one producer warp follows
 constexpr int kBlock = kThreads + 32;
+// Thin tiles (few cells per plane) run two units per CTA, each on one half:
+// 3 consumer warps and its own producer warp, stages and mbarriers.
+constexpr int kHalfThreads = 96;
+constexpr int kHalfBlock = kHalfThreads + 32;
+static_assert(2 * kHalfBlock == kBlock, "two half units fill one CTA");
 constexpr int kStages = 4;
 constexpr int kVecPerThread = 8;         // 16-byte vectors per consumer thread and plane
 constexpr long long kWaitLimit = 4000000000LL;  // cycles (~2 s) before giving up
@@ -122,6 +127,7 @@ __host__ __device__ constexpr size_t stage_bytes(int stage_elems) {
 // unit's StepArgs (filled by the batched kernel), so that one tile plan fits
 // a grid stepped alone or in a batch.  After the slot and the stages come:
 // mbarriers full[kStages], empty[kStages]; warp sums [kStages][kWarps][4]
+// (a half unit uses the first 3 warps of each stage)
 // (density, wall primary flux, wall secondary flux, vacuum outflow); for
 // FP64 grids the per-stage diagonal 1 - |c_x| - |c_1| - |c_2| (- dt nu) of
 // every tile row [kStages][kMaxTileRows] double, for FP32 grids the
@@ -184,13 +190,13 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
 // loop carries no FP64 instruction for them.
 template <typename T>
 __device__ __noinline__ void wall_terms(const T* oplane, const double* v1tab,
-                                        const double* delta, int tid, int i0, int rows,
-                                        int nv2, int pitch, bool wall, double* out3) {
+                                        const double* delta, int tid, int nthreads, int i0,
+                                        int rows, int nv2, int pitch, bool wall, double* out3) {
   constexpr int VEC = 16 / sizeof(T);
   const int QV = pitch / VEC;
   double pe = 0.0, see = 0.0, vac = 0.0;
   for (int m = 0; m < kVecPerThread; m++) {
-    const int v = tid + kThreads * m;
+    const int v = tid + nthreads * m;
     if (v >= rows * QV) break;
     const int r = v / QV, q = v - (v / QV) * QV;
     const int i = i0 + r;
@@ -212,12 +218,26 @@ __device__ __noinline__ void wall_terms(const T* oplane, const double* v1tab,
   out3[2] = vac;
 }
 
-// One unit (tile t, chunk) of a grid; smem is the CTA's dynamic shared
-// memory past the argument slot.  BGK: the grid has the electron-electron
+// Barrier over the threads of one unit: the whole CTA (barrier 0), or one
+// half of it (named barrier 1 or 2, kHalfBlock threads).
+template <int NT>
+__device__ __forceinline__ void unit_sync(int bar) {
+  if constexpr (NT == kThreads) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(NT + 32) : "memory");
+  }
+}
+
+// One unit (tile t, chunk) of a grid on NT consumer threads (kThreads, or
+// kHalfThreads for a half-CTA unit) plus a producer warp; tid: the thread's
+// index within the unit, bar: the unit's barrier; smem is the unit's shared
+// memory past its argument slot.  BGK: the grid has the electron-electron
 // collision term of Eq. 3 switched on.
-template <typename T, bool PADDED, bool BGK>
+template <typename T, bool PADDED, bool BGK, int NT>
 __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, const int chunk,
-                                            unsigned char* smem) {
+                                            unsigned char* smem, const int tid, const int bar) {
+  constexpr int NW = NT / 32;  // consumer warps
   constexpr int VEC = Vec<T>::N;
   constexpr int M = kVecPerThread;
   const Geom& gm = a.geom;
@@ -236,7 +256,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   float* m2_s = m1_s + kMaxTileRows;                  // [pitch], FP32
   int* ctl = reinterpret_cast<int*>(bgk_base + tail_bgk_bytes<T>(a.pitch));
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = tid & 31, warp = tid >> 5;
   const int nt = gm.n_tiles;
   const int nx = a.nx, nv1 = a.nv1, nv2 = a.nv2, pitch = a.pitch;
   int i0, i1, dir;
@@ -258,26 +278,26 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   };
 
   if (sizeof(T) == 4) {  // source factors of this tile (FP32 grids)
-    for (int r = tid; r < i1 - i0; r += blockDim.x) srow_s[r] = a.tab.srow32[i0 + r];
-    for (int j = tid; j < pitch; j += blockDim.x) scol_s[j] = a.tab.scol32[j];
+    for (int r = tid; r < i1 - i0; r += NT + 32) srow_s[r] = a.tab.srow32[i0 + r];
+    for (int j = tid; j < pitch; j += NT + 32) scol_s[j] = a.tab.scol32[j];
   }
   if (BGK) {  // factors of the collision equilibrium (Eq. 5)
     if (sizeof(T) == 4) {
-      for (int r = tid; r < i1 - i0; r += blockDim.x) m1_s[r] = a.tab.m1_32[i0 + r];
-      for (int j = tid; j < pitch; j += blockDim.x) m2_s[j] = a.tab.m2_32[j];
+      for (int r = tid; r < i1 - i0; r += NT + 32) m1_s[r] = a.tab.m1_32[i0 + r];
+      for (int j = tid; j < pitch; j += NT + 32) m2_s[j] = a.tab.m2_32[j];
     } else {
-      for (int j = tid; j < pitch; j += blockDim.x) m2d[j] = a.tab.m2[j];
+      for (int j = tid; j < pitch; j += NT + 32) m2d[j] = a.tab.m2[j];
     }
   }
   if (tid == 0) {
     ctl[0] = (int)a.st->flags;
     for (int s = 0; s < kStages; s++) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kThreads);
+      mbar_init(&empty[s], NT);
     }
     fence_mbar_init();
   }
-  __syncthreads();
+  unit_sync<NT>(bar);
   if (ctl[0]) return;  // sticky error: freeze the state (uniform)
 
   const Params& p = *a.prm;
@@ -287,7 +307,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   const int QV = pitch / VEC;  // vectors per row
   const int rows = i1 - i0;
 
-  if (warp == kWarps) {
+  if (warp == NW) {
     // ============================ producer warp ============================
     // all 32 lanes: where the upwind v1 halo row lies outside the velocity
     // grid, fill its slot with zeros (zero inflow through the v1 edge) so
@@ -359,9 +379,9 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         // fold the consumer warps' sums in a fixed order
         double sn = 0.0, spe = 0.0, ssee = 0.0, svac = 0.0;
         const double* ws = wsum + st * kWarps * kWs;
-        for (int w = 0; w < kWarps; w++) sn += ws[w * kWs + 0];
+        for (int w = 0; w < NW; w++) sn += ws[w * kWs + 0];
         if (k == 0 || k == nx - 1)
-          for (int w = 0; w < kWarps; w++) {
+          for (int w = 0; w < NW; w++) {
             spe += ws[w * kWs + 1];
             ssee += ws[w * kWs + 2];
             svac += ws[w * kWs + 3];
@@ -403,7 +423,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   }
 
   // ============================ consumer warps =============================
-  // this thread's cells: vectors v = tid + kThreads*m of the tile, fixed for
+  // this thread's cells: vectors v = tid + NT*m of the tile, fixed for
   // the whole march; per vector its offset in a stage and in a plane
   int soff[M];  // offset from the tile's first cell (low 24 bits) and row (top byte)
   const int gbase = i0 * pitch;  // the tile's first cell in a plane
@@ -412,7 +432,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   T xr[M][VEC];
 #pragma unroll
   for (int m = 0; m < M; m++) {
-    const int v = tid + kThreads * m;
+    const int v = tid + NT * m;
     soff[m] = 0;
     ax[m] = (T)0;
     if (v < rows * QV) {
@@ -586,7 +606,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       const bool wall = k == 0 && dir < 0, vout = k == nx - 1 && dir > 0;
       if (wall || vout) {  // uniform over the block
         double b3[3];
-        wall_terms<T>(oplane, a.tab.v1, a.tab.delta, tid, i0, rows, nv2, pitch, wall, b3);
+        wall_terms<T>(oplane, a.tab.v1, a.tab.delta, tid, NT, i0, rows, nv2, pitch, wall, b3);
         const double w1 = warp_sum(b3[0]), w2 = warp_sum(b3[1]), w3 = warp_sum(b3[2]);
         if (lane == 0) {
           wsl[1] = w1;
@@ -601,17 +621,45 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   }
 }
 
-// One grid: CTA b runs tile b % n_tiles of chunk b / n_tiles.
+// Shared memory of one unit: argument slot, stages and tail.  A CTA of two
+// half units holds two such regions, each rounded up to 128 bytes.
+template <typename T>
+__host__ __device__ constexpr size_t unit_smem_bytes(int stage_elems, int pitch) {
+  return kStages * stage_bytes<T>(stage_elems) + tail_bytes<T>(pitch);
+}
+template <typename T>
+__host__ __device__ constexpr size_t half_region_bytes(int stage_elems, int pitch) {
+  return (unit_smem_bytes<T>(stage_elems, pitch) + 127) / 128 * 128;
+}
+
+// One grid, whole-CTA units: CTA b runs tile b % n_tiles of chunk
+// b / n_tiles.
 template <typename T, bool PADDED, bool BGK>
 __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(const __grid_constant__ StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nt = a.geom.n_tiles;
-  stream_unit<T, PADDED, BGK>(a, blockIdx.x % nt, blockIdx.x / nt, smem + kArgsBytes);
+  stream_unit<T, PADDED, BGK, kThreads>(a, blockIdx.x % nt, blockIdx.x / nt, smem + kArgsBytes,
+                                        threadIdx.x, 0);
 }
 
-// Many grids in one launch: CTA b copies the arguments of grid units[b].x
-// into the slot at the start of its shared memory and runs that grid's unit
-// units[b].y = tile + n_tiles * chunk.
+// One grid, half units: CTA b runs units 2b and 2b + 1 on its two halves,
+// each in a region of half_region_bytes.
+template <typename T, bool PADDED, bool BGK>
+__global__ void __launch_bounds__(kBlock, 2)
+step_stream_half_kernel(const __grid_constant__ StepArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int nt = a.geom.n_tiles;
+  const int h = threadIdx.x / kHalfBlock;
+  const int u = 2 * blockIdx.x + h;
+  if (u >= nt * a.geom.n_chunks) return;
+  unsigned char* region = smem + h * half_region_bytes<T>(a.geom.stage_elems, a.pitch);
+  stream_unit<T, PADDED, BGK, kHalfThreads>(a, u % nt, u / nt, region + kArgsBytes,
+                                            threadIdx.x - h * kHalfBlock, 1 + h);
+}
+
+// Many grids in one launch, whole-CTA units: CTA b copies the arguments of
+// grid units[b].x into the slot at the start of its shared memory and runs
+// that grid's unit units[b].y = tile + n_tiles * chunk.
 template <typename T, bool PADDED, bool BGK>
 __global__ void __launch_bounds__(kBlock, 2)
 step_stream_batch_kernel(const BatchInst* __restrict__ inst, const int2* __restrict__ units) {
@@ -623,22 +671,50 @@ step_stream_batch_kernel(const BatchInst* __restrict__ inst, const int2* __restr
   __syncthreads();
   const StepArgs& a = *reinterpret_cast<const StepArgs*>(smem);
   const int nt = a.geom.n_tiles;
-  stream_unit<T, PADDED, BGK>(a, u.y % nt, u.y / nt, smem + kArgsBytes);
+  stream_unit<T, PADDED, BGK, kThreads>(a, u.y % nt, u.y / nt, smem + kArgsBytes, threadIdx.x, 0);
+}
+
+// Many grids in one launch, half units: CTA b runs unit pairs[b].y of grid
+// pairs[b].x on threads [0, kHalfBlock) and unit pairs[b].w of grid
+// pairs[b].z (none if pairs[b].z < 0) on the rest, each half in a region of
+// half_bytes whose slot receives that grid's arguments.
+template <typename T, bool PADDED, bool BGK>
+__global__ void __launch_bounds__(kBlock, 2)
+step_stream_batch_half_kernel(const BatchInst* __restrict__ inst, const int4* __restrict__ pairs,
+                              int half_bytes) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int4 c = pairs[blockIdx.x];
+  const int h = threadIdx.x / kHalfBlock, ht = threadIdx.x - h * kHalfBlock;
+  const int g = h ? c.z : c.x, u = h ? c.w : c.y;
+  unsigned char* region = smem + (size_t)h * half_bytes;
+  if (g >= 0) {
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&inst[g].a);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(region);
+    for (int w = ht; w < (int)(sizeof(StepArgs) / 8); w += kHalfBlock) dst[w] = src[w];
+  }
+  __syncthreads();
+  if (g < 0) return;  // the idle half of a CTA with one unit
+  const StepArgs& a = *reinterpret_cast<const StepArgs*>(region);
+  const int nt = a.geom.n_tiles;
+  stream_unit<T, PADDED, BGK, kHalfThreads>(a, u % nt, u / nt, region + kArgsBytes, ht, 1 + h);
 }
 
 }  // namespace
 
-int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per_block) {
+int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per_block,
+                     bool half) {
   const int esize = precision == FK_F32 ? 4 : 8;
   const int vec = 16 / esize;
-  const int cells = kThreads * kVecPerThread * vec;
+  const int cells = (half ? kHalfThreads : kThreads) * kVecPerThread * vec;
   if (pitch > cells) return 0;
   int rows = cells / pitch;
   if (rows > kMaxTileRows) rows = kMaxTileRows;
-  // two CTAs per SM: each holds kStages stages of (rows + 1) * pitch elements
+  // two CTAs per SM: each unit holds kStages stages of (rows + 1) * pitch
+  // elements (a half unit gets half of its CTA, less the region's rounding)
   const long tail =
       (long)(precision == FK_F32 ? tail_bytes<float>(pitch) : tail_bytes<double>(pitch));
-  const long budget = (long)smem_per_sm / 2 - reserved_per_block - tail;
+  const long cta = (long)smem_per_sm / 2 - reserved_per_block;
+  const long budget = (half ? cta / 2 - 127 : cta) - tail;
   const long stage = budget / kStages / 128 * 128;
   const long fit = stage / ((long)pitch * esize) - 1;  // one halo slot per stage
   if (fit < rows) rows = (int)fit;
@@ -646,9 +722,18 @@ int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per
 }
 
 size_t stream_smem_bytes(int precision, int stage_elems, int pitch) {
-  if (precision == FK_F32)
-    return kStages * stage_bytes<float>(stage_elems) + tail_bytes<float>(pitch);
-  return kStages * stage_bytes<double>(stage_elems) + tail_bytes<double>(pitch);
+  return precision == FK_F32 ? unit_smem_bytes<float>(stage_elems, pitch)
+                             : unit_smem_bytes<double>(stage_elems, pitch);
+}
+
+size_t stream_half_bytes(int precision, int stage_elems, int pitch) {
+  return precision == FK_F32 ? half_region_bytes<float>(stage_elems, pitch)
+                             : half_region_bytes<double>(stage_elems, pitch);
+}
+
+size_t stream_cta_smem_bytes(int precision, const Geom& gm, int pitch) {
+  return gm.half ? 2 * stream_half_bytes(precision, gm.stage_elems, pitch)
+                 : stream_smem_bytes(precision, gm.stage_elems, pitch);
 }
 
 namespace {
@@ -677,6 +762,18 @@ int ctas_per_sm(int optin, size_t smem_bytes) {
     e = fit_kernel(step_stream_batch_kernel<T, false, true>, optin, smem_bytes, &best);
   if (e == cudaSuccess)
     e = fit_kernel(step_stream_batch_kernel<T, true, true>, optin, smem_bytes, &best);
+  if (e == cudaSuccess) e = fit_kernel(step_stream_half_kernel<T, false, false>, optin, smem_bytes, &best);
+  if (e == cudaSuccess) e = fit_kernel(step_stream_half_kernel<T, true, false>, optin, smem_bytes, &best);
+  if (e == cudaSuccess) e = fit_kernel(step_stream_half_kernel<T, false, true>, optin, smem_bytes, &best);
+  if (e == cudaSuccess) e = fit_kernel(step_stream_half_kernel<T, true, true>, optin, smem_bytes, &best);
+  if (e == cudaSuccess)
+    e = fit_kernel(step_stream_batch_half_kernel<T, false, false>, optin, smem_bytes, &best);
+  if (e == cudaSuccess)
+    e = fit_kernel(step_stream_batch_half_kernel<T, true, false>, optin, smem_bytes, &best);
+  if (e == cudaSuccess)
+    e = fit_kernel(step_stream_batch_half_kernel<T, false, true>, optin, smem_bytes, &best);
+  if (e == cudaSuccess)
+    e = fit_kernel(step_stream_batch_half_kernel<T, true, true>, optin, smem_bytes, &best);
   return e == cudaSuccess ? best : 0;
 }
 }  // namespace
@@ -696,54 +793,78 @@ int stream_ctas_per_sm(int precision, size_t smem_bytes) {
 
 namespace {
 template <typename T, bool BGK>
-void launch_single(const StepArgs& a, int grid, size_t smem, bool padded, cudaStream_t s) {
-  if (padded)
-    step_stream_kernel<T, true, BGK><<<grid, kBlock, smem, s>>>(a);
-  else
-    step_stream_kernel<T, false, BGK><<<grid, kBlock, smem, s>>>(a);
+void launch_single(const StepArgs& a, int grid, size_t smem, bool padded, bool half,
+                   cudaStream_t s) {
+  if (half) {
+    if (padded)
+      step_stream_half_kernel<T, true, BGK><<<grid, kBlock, smem, s>>>(a);
+    else
+      step_stream_half_kernel<T, false, BGK><<<grid, kBlock, smem, s>>>(a);
+  } else {
+    if (padded)
+      step_stream_kernel<T, true, BGK><<<grid, kBlock, smem, s>>>(a);
+    else
+      step_stream_kernel<T, false, BGK><<<grid, kBlock, smem, s>>>(a);
+  }
 }
 template <typename T, bool BGK>
 void launch_batch(const BatchInst* inst, const int2* units, int n_units, size_t smem,
-                  bool padded, cudaStream_t s) {
-  if (padded)
-    step_stream_batch_kernel<T, true, BGK><<<n_units, kBlock, smem, s>>>(inst, units);
-  else
-    step_stream_batch_kernel<T, false, BGK><<<n_units, kBlock, smem, s>>>(inst, units);
+                  const int4* pairs, int n_pairs, int half_bytes, bool padded, cudaStream_t s) {
+  if (n_units > 0) {
+    if (padded)
+      step_stream_batch_kernel<T, true, BGK><<<n_units, kBlock, smem, s>>>(inst, units);
+    else
+      step_stream_batch_kernel<T, false, BGK><<<n_units, kBlock, smem, s>>>(inst, units);
+  }
+  if (n_pairs > 0) {
+    const size_t hs = 2 * (size_t)half_bytes;
+    if (padded)
+      step_stream_batch_half_kernel<T, true, BGK><<<n_pairs, kBlock, hs, s>>>(inst, pairs, half_bytes);
+    else
+      step_stream_batch_half_kernel<T, false, BGK><<<n_pairs, kBlock, hs, s>>>(inst, pairs, half_bytes);
+  }
 }
 }  // namespace
 
 cudaError_t launch_step_stream(const StepArgs& a, int precision, bool bgk, cudaStream_t s) {
-  const int grid = a.geom.n_tiles * a.geom.n_chunks;
-  const size_t smem = stream_smem_bytes(precision, a.geom.stage_elems, a.pitch);
+  const int units = a.geom.n_tiles * a.geom.n_chunks;
+  const bool half = a.geom.half != 0;
+  const int grid = half ? (units + 1) / 2 : units;
+  const size_t smem = stream_cta_smem_bytes(precision, a.geom, a.pitch);
   const bool padded = a.pitch != a.nv2;
   if (precision == FK_F32) {
     if (bgk)
-      launch_single<float, true>(a, grid, smem, padded, s);
+      launch_single<float, true>(a, grid, smem, padded, half, s);
     else
-      launch_single<float, false>(a, grid, smem, padded, s);
+      launch_single<float, false>(a, grid, smem, padded, half, s);
   } else {
     if (bgk)
-      launch_single<double, true>(a, grid, smem, padded, s);
+      launch_single<double, true>(a, grid, smem, padded, half, s);
     else
-      launch_single<double, false>(a, grid, smem, padded, s);
+      launch_single<double, false>(a, grid, smem, padded, half, s);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_step_stream_batch(const BatchInst* inst, const int2* units, int n_units,
-                                     int precision, bool padded, bool bgk, size_t smem_bytes,
+                                     const int4* pairs, int n_pairs, int precision, bool padded,
+                                     bool bgk, size_t smem_bytes, int half_bytes,
                                      cudaStream_t s) {
-  if (n_units <= 0) return cudaSuccess;
+  if (n_units <= 0 && n_pairs <= 0) return cudaSuccess;
   if (precision == FK_F32) {
     if (bgk)
-      launch_batch<float, true>(inst, units, n_units, smem_bytes, padded, s);
+      launch_batch<float, true>(inst, units, n_units, smem_bytes, pairs, n_pairs, half_bytes,
+                                padded, s);
     else
-      launch_batch<float, false>(inst, units, n_units, smem_bytes, padded, s);
+      launch_batch<float, false>(inst, units, n_units, smem_bytes, pairs, n_pairs, half_bytes,
+                                 padded, s);
   } else {
     if (bgk)
-      launch_batch<double, true>(inst, units, n_units, smem_bytes, padded, s);
+      launch_batch<double, true>(inst, units, n_units, smem_bytes, pairs, n_pairs, half_bytes,
+                                 padded, s);
     else
-      launch_batch<double, false>(inst, units, n_units, smem_bytes, padded, s);
+      launch_batch<double, false>(inst, units, n_units, smem_bytes, pairs, n_pairs, half_bytes,
+                                  padded, s);
   }
   return cudaGetLastError();
 }

@@ -309,7 +309,7 @@ def fk_set_surface_charge(g, sigma):
     _check(load().fk_set_surface_charge(g, float(sigma)), "fk_set_surface_charge", g)
 
 
-FK_INFO_LEN = 10
+FK_INFO_LEN = 11
 
 
 def fk_grid_info(g):
@@ -317,7 +317,7 @@ def fk_grid_info(g):
     _check(load().fk_grid_info(g, _dp(out)), "fk_grid_info", g)
     return dict(dx=out[0], dv1=out[1], dv2=out[2], dt=out[3], c2=out[4], cx_max=out[5],
                 kernel="stream" if out[6] else "direct", n_tiles=int(out[7]),
-                n_chunks=int(out[8]), chunk_len=int(out[9]))
+                n_chunks=int(out[8]), chunk_len=int(out[9]), units_per_cta=int(out[10]))
 
 
 def fk_set_kernel_timing(g, enabled):
@@ -569,7 +569,7 @@ class Mlp:
 
 
 # --- batches ---------------------------------------------------------------
-FK_BATCH_INFO_LEN = 8
+FK_BATCH_INFO_LEN = 10
 
 
 def _bcheck(status, what, handle=None):
@@ -642,7 +642,9 @@ def fk_batch_info(b):
     _bcheck(load().fk_batch_info(b, _dp(out)), "fk_batch_info", b)
     return dict(grids=int(out[0]), units=int(out[1]), finalize_blocks=int(out[2]),
                 smem_bytes=int(out[3]), ctas_per_sm=int(out[4]), cells=float(out[5]),
-                buckets=int(out[6]), steps=int(out[7]))
+                buckets=int(out[6]), steps=int(out[7]), whole_ctas=int(out[8]),
+                half_ctas=int(out[9]),
+                step_launches=int(out[8] > 0) + int(out[9] > 0))
 
 
 def fk_batch_set_kernel_timing(b, enabled):
