@@ -441,12 +441,13 @@ def make_sweep_grids(fk, instances, precision, stream):
 
 
 def run_sweep(args):
-    """Parameter sweep: every instance of synth.sweep_instances stepped as
-    one batch (x-chunks autotuned per size bucket), against the same
-    instances stepped one after another with fk_step (each instance's steps
-    as CUDA-graph replays).  Both arms give bitwise identical states; the
-    metric is instances per hour at the workload's steps per instance,
-    from the timed per-step rate."""
+    """Batched workload: every instance of the parameter sweep
+    (synth.sweep_instances) or of the surrogate's training runs
+    (synth.surrogate_runs) stepped as one batch (x-chunks autotuned per size
+    bucket), against the same instances stepped one after another with
+    fk_step (each instance's steps as CUDA-graph replays).  Both arms give
+    bitwise identical states; the metric is instances per hour at the
+    workload's steps per instance, from the timed per-step rate."""
     rank, world, local = dist_env()
     import torch
     from paper_2303_14119_gb300 import fk
@@ -460,7 +461,7 @@ def run_sweep(args):
         dist = td
     stream = torch.cuda.current_stream().cuda_stream
     w = synth.WORKLOADS[args.workload]
-    ins = synth.sweep_instances(w["sweep"], w["seed"])
+    ins = synth.batch_instances(w)
     prec = fk.FK_F32 if args.precision == "f32" else fk.FK_F64
     steps = args.steps
     grids = make_sweep_grids(fk, ins, prec, stream)
@@ -522,6 +523,16 @@ def run_sweep(args):
     for g in grids + twins:
         g.close()
     per_inst = w["steps"]
+    if "sweep" in w:
+        workload_text = ("%s: %d instances, nx 128-512, nv1 = nv2 64-192, E_y log-uniform "
+                         "3e5-5e6 V/m, delta_max 2-4, A_max 250-600 eV, T_se 1-5 eV, one seed "
+                         "(%d); f0 = 0" % (args.workload, len(ins), w["seed"]))
+    else:
+        workload_text = ("%s: %d surrogate training runs of 64 x 48 x 48, E_y log-uniform "
+                         "3e5-5e6 V/m, delta_max 2-4, A_max 250-600 eV, T_se 1-5 eV, J "
+                         "log-uniform 1e5-1e7 A/m^2, h_max 16-24 um, one seed (%d); f0 = 0; "
+                         "%d steps reach the 1.25 ns horizon at the smallest gap"
+                         % (args.workload, len(ins), w["seed"], per_inst))
     ms_step_b = ms_b / steps
     ms_step_s = ms_s / steps
     value = world * len(ins) * 3600.0 / (ms_step_b * per_inst / 1e3)
@@ -542,9 +553,7 @@ def run_sweep(args):
         "unit": "instances/hr", "n_gpus": world, "steps": steps, "warmup": args.warmup,
         "ms_per_step": ms_step_b, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": "%s: %d instances, nx 128-512, nv1 = nv2 64-192, E_y log-uniform "
-                               "3e5-5e6 V/m, delta_max 2-4, A_max 250-600 eV, T_se 1-5 eV, "
-                               "one seed (%d); f0 = 0" % (args.workload, len(ins), w["seed"]),
+        "config": {"workload": workload_text,
                    "cells_all_instances": cells, "steps_per_instance": per_inst,
                    "rate": "instances/hr from the timed per-step time x %d steps" % per_inst,
                    "l2": "inputs larger than L2 (no flush)",
@@ -578,8 +587,8 @@ def run_reference(args):
         return
     import oracle
     w = synth.WORKLOADS[args.workload]
-    if "sweep" in w:  # the sampled instance: the sweep's first
-        w = synth.sweep_instances(w["sweep"], w["seed"])[0]
+    if "sweep" in w or "runs" in w:  # the sampled instance: the batch's first
+        w = synth.batch_instances(w)[0]
     shape = (w["nx"], w["nv1"], w["nv2"])
     o = oracle.Oracle(*shape, w["h_max"], -w["v1_span"], w["v1_span"], -w["v2_span"],
                       w["v2_span"], cfl=w["cfl"])
@@ -611,7 +620,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif "sweep" in synth.WORKLOADS[args.workload]:
+    elif any(k in synth.WORKLOADS[args.workload] for k in ("sweep", "runs")):
         run_sweep(args)
     else:
         run_ours(args)

@@ -83,6 +83,10 @@ WORKLOADS = {
     # parameter sweep: 256 independent instances of uneven size, each run
     # 5000 steps, every size and parameter drawn from one seed (sweep_instances)
     "sweep_256": dict(BASE, sweep=256, steps=5000, seed=2023),
+    # the surrogate's training data: 1536 runs of 64 x 48 x 48 (surrogate_runs)
+    # stepped as one batch; 750 000 steps reach a 1.25 ns horizon at the
+    # smallest gap (h_max = 16 um: dt = 0.4 (h_max / 64) / 6e7 m/s)
+    "surrogate_1536": dict(BASE, runs=1536, steps=750000, seed=11),
 }
 
 # Offset of the sweep's draws in the SplitMix64 stream (far from the cell
@@ -106,6 +110,14 @@ def sweep_instances(n: int = 256, seed: int = 2023):
                         A_max=250.0 + 350.0 * float(u[q, 4]),
                         T_se=1.0 + 4.0 * float(u[q, 5]), seed=seed + 1 + q))
     return out
+
+
+def batch_instances(w):
+    """The instance list of a batched workload entry: a parameter sweep
+    (key 'sweep') or the surrogate's training runs (key 'runs')."""
+    if "sweep" in w:
+        return sweep_instances(w["sweep"], w["seed"])
+    return surrogate_runs(w["runs"], w["seed"])
 
 
 # Surrogate training runs: the sweep's parameter draws plus the two inputs

@@ -32,7 +32,7 @@ def test_initial_f_scale_and_shape():
 
 def test_workloads_are_consistent():
     for name, w in synth.WORKLOADS.items():
-        if "sweep" in w:
+        if "sweep" in w or "runs" in w:
             continue
         assert w["nx"] >= 2 and w["Ey"] < 0
         assert f"{w['nx']}x{w['nv1']}x{w['nv2']}" in name
@@ -57,3 +57,15 @@ def test_sweep_instances_ranges_and_determinism():
         v = np.array([p[key] for p in ins])
         assert v.min() >= lo and v.max() <= hi and v.std() > 0.2 * (hi - lo)
     assert len({p["seed"] for p in ins}) == 256
+
+
+def test_batched_workload_entries():
+    w = synth.WORKLOADS["surrogate_1536"]
+    runs = synth.batch_instances(w)
+    assert runs == synth.surrogate_runs(1536, 11)
+    assert all((p["nx"], p["nv1"], p["nv2"]) == (64, 48, 48) for p in runs)
+    # the step count covers the horizon at the smallest gap drawn
+    h_min = min(p["h_max"] for p in runs)
+    dt = w["cfl"] * (h_min / 64) / w["v1_span"]
+    assert h_min >= synth.SURROGATE_H[0] and w["steps"] * dt >= 1.25e-9
+    assert synth.batch_instances(synth.WORKLOADS["sweep_256"]) == synth.sweep_instances(256, 2023)
