@@ -309,14 +309,37 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
 
   if (warp == NW) {
     // ============================ producer warp ============================
+    // Per item q: wait until every consumer released the stage of item
+    // q - kStages, read what its partial sums need from that stage and from
+    // the warp sums (gather), refill the stage with item q (issue), then
+    // reduce and store the partial sums of item q - kStages (finish): the
+    // reductions run while the copy is in flight.
+    //
+    // c_1 (FP32 copy) of item q sits in lane q % 32 of c1w (items wbase ..
+    // wbase + 31) or of c1n (the next 32 items, loaded a window ahead);
+    // lane st of c1slot / a1slot holds c_1 and |c_1| (FP64 grids) of the
+    // item in stage st.
+    const T a2t = (T)fabs(p.c2);
+    const bool has_a2 = p.c2 != 0.0;
+    float c1w = lane < n_items ? a.c1_32[item_plane(lane)] : 0.f;
+    float c1n = lane + 32 < n_items ? a.c1_32[item_plane(lane + 32)] : 0.f;
+    int wbase = 0;
+    float c1slot = 0.f;
+    double a1slot = 0.0;
     // all 32 lanes: where the upwind v1 halo row lies outside the velocity
     // grid, fill its slot with zeros (zero inflow through the v1 edge) so
     // the consumers read a neighbour row without a bounds test; then lane 0
     // copies plane k's tile rows plus the halo row inside the grid
     auto issue = [&](int q) {
+      if (q == wbase + 32) {  // next window; prefetch the one after
+        c1w = c1n;
+        wbase += 32;
+        c1n = wbase + 32 + lane < n_items ? a.c1_32[item_plane(wbase + 32 + lane)] : 0.f;
+      }
       const int k = item_plane(q);
-      const float c1 = a.c1_32[k];
+      const float c1 = __shfl_sync(0xffffffffu, c1w, q & 31);
       const int st = q % kStages;
+      if (lane == st) c1slot = c1;
       T* stage = reinterpret_cast<T*>(stage_base + st * sbytes);
       // stage layout: the tile's rows start at row 1 when the halo lies
       // above (c_1 > 0), at row 0 otherwise (halo, if any, at row `rows`)
@@ -332,6 +355,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         // FP64 diagonal of the convex update per tile row, once per plane
         // here rather than per vector in the consumers
         const double a1 = c1 == 0.f ? 0.0 : fabs(a.c1[k]);
+        if (lane == st) a1slot = a1;
         double db = 1.0 - a1 - fabs(p.c2);
         if (BGK) db -= a.bgk[k];  // the loss part of the collision term, dt nu_k f
         for (int r = lane; r < rows; r += 32) dgl[st * kMaxTileRows + r] = db - fabs(a.tab.cx[i0 + r]);
@@ -352,66 +376,93 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         bulk_g2s(dst, src, bytes, &full[st]);
       }
     };
-    // a consumed compute item: partial sums of its plane (all 32 lanes)
-    auto retire = [&](int q) {
-      if (prime && q == 0) return;
+    // What the partial sums of a consumed compute item need from its stage
+    // and from the warp sums, read before the stage is refilled.
+    struct Gathered {
+      int k;       // plane (-1: the prime item, no sums)
+      T lvt;       // this lane's share of the velocity-edge outflow
+      double ws[kWs];  // lane w < NW: warp w's sums (all four on a wall plane)
+    };
+    auto gather = [&](int q) -> Gathered {
+      Gathered g;
+      g.k = -1;
+      g.lvt = (T)0;
+#pragma unroll
+      for (int i = 0; i < kWs; i++) g.ws[i] = 0.0;
+      if (prime && q == 0) return g;
       const int k = item_plane(q);
       const int st = q % kStages;
+      g.k = k;
       const T* sb = reinterpret_cast<const T*>(stage_base + st * sbytes);
-      const float c1f = a.c1_32[k];
-      const double a1 = c1f == 0.f ? 0.0 : fabs(a.c1[k]);
-      const double a2 = fabs(p.c2);
+      const float c1f = __shfl_sync(0xffffffffu, c1slot, st);
+      const double a1d = sizeof(T) == 8 ? __shfl_sync(0xffffffffu, a1slot, st) : 0.0;
       // ledger: outflow of f^n through the downwind velocity edges, summed
-      // in the grid's precision per lane (a ledger diagnostic: FP32 grids
-      // keep FP64 instructions off this per-plane path), FP64 across lanes
-      T lvt = (T)0;
-      const T a1t = (T)a1, a2t = (T)a2;
+      // in the grid's precision (a ledger diagnostic: FP32 grids keep FP64
+      // instructions off this per-plane path)
+      const T a1t = sizeof(T) == 4 ? (T)fabsf(c1f) : (T)a1d;
       const int erow = (c1f > 0.f && i1 == nv1) ? nv1 - 1 : ((c1f < 0.f && i0 == 0) ? 0 : -1);
       const int rb = c1f > 0.f ? 1 : 0;  // stage row of the tile's first row
       if (erow >= 0) {
         const T* r = sb + (size_t)(erow - i0 + rb) * pitch;
-        for (int j = lane; j < nv2; j += 32) lvt += a1t * r[j];
+        for (int j = lane; j < nv2; j += 32) g.lvt += a1t * r[j];
       }
-      if (a2 > 0.0)
-        for (int r = lane; r < rows; r += 32) lvt += a2t * sb[(size_t)(r + rb) * pitch + nv2 - 1];
-      const double lv = warp_sum((double)lvt);
+      if (has_a2)
+        for (int r = lane; r < rows; r += 32) g.lvt += a2t * sb[(size_t)(r + rb) * pitch + nv2 - 1];
+      if (lane < NW) {
+        const double* ws = wsum + (st * kWarps + lane) * kWs;
+        g.ws[0] = ws[0];
+        if (k == 0 || k == nx - 1) {
+#pragma unroll
+          for (int i = 1; i < kWs; i++) g.ws[i] = ws[i];
+        }
+      }
+      return g;
+    };
+    // fold the gathered sums (the warps' in a fixed order) and store them
+    auto finish = [&](const Gathered& g) {
+      if (g.k < 0) return;
+      const int k = g.k;
+      const double lv = (double)warp_sum(g.lvt);
+      double sum[kWs] = {0.0, 0.0, 0.0, 0.0};
+      const bool wall = k == 0 || k == nx - 1;
+#pragma unroll
+      for (int w = 0; w < NW; w++) {
+        sum[0] += __shfl_sync(0xffffffffu, g.ws[0], w);
+        if (wall) {
+#pragma unroll
+          for (int i = 1; i < kWs; i++) sum[i] += __shfl_sync(0xffffffffu, g.ws[i], w);
+        }
+      }
       if (lane == 0) {
-        // fold the consumer warps' sums in a fixed order
-        double sn = 0.0, spe = 0.0, ssee = 0.0, svac = 0.0;
-        const double* ws = wsum + st * kWarps * kWs;
-        for (int w = 0; w < NW; w++) sn += ws[w * kWs + 0];
-        if (k == 0 || k == nx - 1)
-          for (int w = 0; w < NW; w++) {
-            spe += ws[w * kWs + 1];
-            ssee += ws[w * kWs + 2];
-            svac += ws[w * kWs + 3];
-          }
-        a.part.n[(size_t)k * nt + t] = sn;
+        a.part.n[(size_t)k * nt + t] = sum[0];
         a.part.lv[(size_t)k * nt + t] = lv;
         if (k == 0) {
-          a.part.pe[t] = spe;
-          a.part.see[t] = ssee;
+          a.part.pe[t] = sum[1];
+          a.part.see[t] = sum[2];
         }
-        if (k == nx - 1) a.part.vac[t] = svac;
+        if (k == nx - 1) a.part.vac[t] = sum[3];
       }
     };
     int issued = 0;
     bool ok = true;
     for (int q = 0; q < n_items; q++) {
+      Gathered g{};
+      g.k = -1;
       if (q >= kStages) {
         // stage reuse: wait until every consumer thread released item q - kStages
         ok = __all_sync(0xffffffffu,
                         mbar_wait(&empty[q % kStages], (uint32_t)(((q / kStages) - 1) & 1)));
         if (!ok) break;
-        retire(q - kStages);
+        g = gather(q - kStages);
         __syncwarp();  // the stage is read by every lane before it is refilled
       }
       issue(q);
       issued = q + 1;
+      finish(g);
     }
     for (int q = max(0, issued - kStages); q < issued && ok; q++) {
       ok = __all_sync(0xffffffffu, mbar_wait(&empty[q % kStages], (uint32_t)((q / kStages) & 1)));
-      if (ok) retire(q);
+      if (ok) finish(gather(q));
     }
     if (!ok && lane == 0) {
       atomicOr(&a.st->flags, kFlagTimeout);
