@@ -76,15 +76,44 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 STEP_KERNEL_SOURCES = (os.path.join(CSRC, "fk_stream.cu"), os.path.join(CSRC, "fk_internal.cuh"))
 
 
+def code_only(text: str) -> str:
+    """C/C++/CUDA source with its comments removed and every run of white
+    space made one blank: what the compiler sees, not how it is annotated
+    or laid out (string and character literals are kept as they are)."""
+    out = []
+    i, n = 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == "/" and i + 1 < n and text[i + 1] == "/":
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+            out.append(" ")
+        elif c == "/" and i + 1 < n and text[i + 1] == "*":
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def source_hash(files=STEP_KERNEL_SOURCES) -> str:
-    """Short hash of the given sources (by default those of the streaming
-    step kernel), identifying the code a profile was taken on."""
+    """Short hash of the code of the given sources (by default those of the
+    streaming step kernel), identifying the code a profile was taken on;
+    edits to comments or layout leave it unchanged."""
     import hashlib
     h = hashlib.sha256()
     for p in sorted(files):
         h.update(os.path.basename(p).encode())
-        with open(p, "rb") as fh:
-            h.update(fh.read())
+        with open(p, encoding="utf-8") as fh:
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -3,11 +3,12 @@
 // f^n and one write of f^{n+1} per cell.
 //
 // Decomposition.  A CTA owns one unit = (tile of v1 rows [i0, i1) times all
-// v2 cells, chunk of consecutive x-planes).  All rows of a tile have the
-// same sign of v1, so the x-upwind neighbour of plane k is plane k - dir
-// for the whole tile; the CTA marches through its chunk in the direction
-// dir, and every consumer thread keeps the previous plane's input values of
-// its own cells in registers: the x-neighbour never comes from memory twice.
+// v2 cells, chunk of consecutive x-planes), or two units of thin tiles, one
+// per half of the CTA.  All rows of a tile have the same sign of v1, so the
+// x-upwind neighbour of plane k is plane k - dir for the whole tile; the
+// unit marches through its chunk in the direction dir, and every consumer
+// thread keeps the previous plane's input values of its own cells in
+// registers: the x-neighbour never comes from memory twice.
 //
 // Pipeline.  Planes arrive in shared memory through cp.async.bulk copies
 // (the TMA engine) into a ring of kStages stages.  Each stage holds the
@@ -16,11 +17,12 @@
 //  - consumer warps (kWarps): wait until a stage is full, update their cells
 //    (FP32/INT work only on the FP32 path), store f^{n+1}, sum it per warp,
 //    and release the stage;
-//  - the producer warp: when a stage is released, fold the warp sums of its
-//    plane into the per-(plane, tile) partial sums, add the boundary terms
-//    of that plane (outflow through the downwind velocity edges from f^n,
-//    still in the stage; on x = 0 and x = h_max the wall fluxes of
-//    Eqs. 12-14 and the vacuum outflow of f^{n+1}), then refill the stage.
+//  - the producer warp: when a stage is released, read what the partial
+//    sums of its plane need (the warp sums; the outflow of f^n through the
+//    downwind velocity edges, still in the stage), refill the stage, then
+//    fold them into the per-(plane, tile) partial sums (on x = 0 and
+//    x = h_max with the wall fluxes of Eqs. 12-14 and the vacuum outflow
+//    of f^{n+1}).
 // There is no block-wide barrier inside the march.
 //
 // Per cell: f' = f + |c_x|(f_ux - f) + |c_1|(f_u1 - f) + |c_2|(f_u2 - f) + dt S
