@@ -98,10 +98,23 @@ fk_status upload_params(fk_grid* g) {
 }  // namespace
 
 fk_status fk::sync_state(fk_grid* g, DevState* out) {
+  return sync_state_with(g, out, nullptr, nullptr);
+}
+
+fk_status fk::sync_state_with(fk_grid* g, DevState* out, double* n_e, double* Ex) {
   FK_CUDA(g, cudaSetDevice(g->dev));
   if (g->batch_done) FK_CUDA(g, cudaStreamWaitEvent(g->stream, g->batch_done, 0));
-  FK_CUDA(g, cudaMemcpyAsync(out, g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
+  // every copy lands in the grid's pinned buffer; one wait for all of them
+  DevState* hst = static_cast<DevState*>(g->h_stage);
+  double* hv = reinterpret_cast<double*>(hst + 1);  // n_e, then E_x
+  const size_t vb = (size_t)g->nx * sizeof(double);
+  FK_CUDA(g, cudaMemcpyAsync(hst, g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
+  if (n_e) FK_CUDA(g, cudaMemcpyAsync(hv, g->d_ne, vb, cudaMemcpyDeviceToHost, g->stream));
+  if (Ex) FK_CUDA(g, cudaMemcpyAsync(hv + g->nx, g->d_Ex, vb, cudaMemcpyDeviceToHost, g->stream));
   FK_CUDA(g, cudaStreamSynchronize(g->stream));
+  *out = *hst;
+  if (n_e) memcpy(n_e, hv, vb);
+  if (Ex) memcpy(Ex, hv + g->nx, vb);
   const long long adv = out->step - g->base_step;
   g->base_cur = (int)((g->base_cur + (adv & 1)) & 1);
   g->base_step = out->step;
@@ -199,6 +212,7 @@ void free_grid(fk_grid* g) {
                   g->d_stage, g->d_f3, g->fin.pre, g->fin.bsum, g->fin.blv, g->fin.counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (g->h_stage) cudaFreeHost(g->h_stage);
   for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
@@ -400,6 +414,7 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   const size_t nparts = (size_t)d.nx * g->part.nu;
   CREATE_CUDA(dalloc(&g->d_prm, sizeof(Params)));
   CREATE_CUDA(dalloc(&g->d_st, sizeof(DevState)));
+  CREATE_CUDA(cudaMallocHost(&g->h_stage, sizeof(DevState) + 2 * (size_t)d.nx * sizeof(double)));
   CREATE_CUDA(dalloc(&g->d_f[0], fbytes));
   CREATE_CUDA(dalloc(&g->d_f[1], fbytes));
   CREATE_CUDA(dalloc(&g->tab.v1, d.nv1 * sizeof(double)));
@@ -662,10 +677,8 @@ fk_status fk_sync(fk_grid* g) {
 fk_status fk_moments(fk_grid* g, double* n_e, double* Ex, double* gamma_pe, double* gamma_see) {
   if (!g) return FK_EINVAL;
   DevState st;
-  fk_status s = sync_state(g, &st);
+  fk_status s = sync_state_with(g, &st, n_e, Ex);
   if (s != FK_OK) return s;
-  if (n_e) FK_CUDA(g, cudaMemcpy(n_e, g->d_ne, g->nx * sizeof(double), cudaMemcpyDeviceToHost));
-  if (Ex) FK_CUDA(g, cudaMemcpy(Ex, g->d_Ex, g->nx * sizeof(double), cudaMemcpyDeviceToHost));
   if (gamma_pe) *gamma_pe = st.g_pe;
   if (gamma_see) *gamma_see = st.g_see;
   return flags_status(g, st.flags);

@@ -336,6 +336,20 @@ void free_batch(fk_batch* b) {
   delete b;
 }
 
+// Read every grid's device scalars into its pinned read-back buffer (all
+// copies enqueued, one wait) and return them there.
+fk_status read_states(fk_batch* b, std::vector<const DevState*>* st) {
+  st->resize(b->n);
+  for (int i = 0; i < b->n; i++) {
+    fk_grid* g = b->grids[i];
+    BK_CUDA(b, cudaMemcpyAsync(g->h_stage, g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                               b->stream));
+    (*st)[i] = static_cast<const DevState*>(g->h_stage);
+  }
+  BK_CUDA(b, cudaStreamSynchronize(b->stream));
+  return FK_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -457,16 +471,13 @@ fk_status fk_batch_step(fk_batch* b, int64_t n) {
 fk_status fk_batch_sync(fk_batch* b, int32_t* status) {
   if (!b) return FK_EINVAL;
   BK_CUDA(b, cudaSetDevice(b->dev));
-  BK_CUDA(b, cudaStreamSynchronize(b->stream));
-  std::vector<DevState> st(b->n);
-  for (int i = 0; i < b->n; i++)
-    BK_CUDA(b, cudaMemcpyAsync(&st[i], b->grids[i]->d_st, sizeof(DevState),
-                               cudaMemcpyDeviceToHost, b->stream));
-  BK_CUDA(b, cudaStreamSynchronize(b->stream));
+  std::vector<const DevState*> st;
+  const fk_status rs = read_states(b, &st);
+  if (rs != FK_OK) return rs;
   fk_status first = FK_OK;
   for (int i = 0; i < b->n; i++) {
     fk_grid* g = b->grids[i];
-    const fk_status s = flags_status(g, st[i].flags);
+    const fk_status s = flags_status(g, st[i]->flags);
     if (status) status[i] = s;
     if (s != FK_OK && first == FK_OK) {
       first = s;
@@ -480,16 +491,14 @@ fk_status fk_batch_scalars(fk_batch* b, double* sigma, int64_t* step, int64_t* s
                            int32_t* status) {
   if (!b) return FK_EINVAL;
   BK_CUDA(b, cudaSetDevice(b->dev));
-  std::vector<DevState> st(b->n);
-  for (int i = 0; i < b->n; i++)
-    BK_CUDA(b, cudaMemcpyAsync(&st[i], b->grids[i]->d_st, sizeof(DevState),
-                               cudaMemcpyDeviceToHost, b->stream));
-  BK_CUDA(b, cudaStreamSynchronize(b->stream));
+  std::vector<const DevState*> st;
+  const fk_status rs = read_states(b, &st);
+  if (rs != FK_OK) return rs;
   for (int i = 0; i < b->n; i++) {
-    if (sigma) sigma[i] = st[i].sigma;
-    if (step) step[i] = st[i].step;
-    if (sat_step) sat_step[i] = st[i].sat_step;
-    if (status) status[i] = flags_status(b->grids[i], st[i].flags);
+    if (sigma) sigma[i] = st[i]->sigma;
+    if (step) step[i] = st[i]->step;
+    if (sat_step) sat_step[i] = st[i]->sat_step;
+    if (status) status[i] = flags_status(b->grids[i], st[i]->flags);
   }
   return FK_OK;
 }

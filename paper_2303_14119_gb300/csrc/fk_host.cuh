@@ -32,6 +32,8 @@ struct fk_grid {
   float* d_c1_32 = nullptr;
   fk::FinScratch fin{};
   void* d_stage = nullptr;
+  // pinned read-back buffer of the getters: DevState, then n_e and E_x [nx]
+  void* h_stage = nullptr;
   // physics parameters as last set
   double Ey = 0, Ex_ext = 0;
   int self_consistent = 1;
@@ -72,6 +74,9 @@ StepArgs make_args(fk_grid* g, int cur);
 // Synchronise the grid's stream (after the batch that steps it, if any),
 // read the device scalars and re-base the buffer bookkeeping.
 fk_status sync_state(fk_grid* g, DevState* out);
+// The same, also reading n_e and E_x [nx] into the host arrays given
+// (either may be NULL): one wait for all the copies.
+fk_status sync_state_with(fk_grid* g, DevState* out, double* n_e, double* Ex);
 // Status for sticky device flags (FK_OK if none); sets the grid's message.
 fk_status flags_status(fk_grid* g, unsigned flags);
 
