@@ -258,6 +258,60 @@ def fine_warm_start(weights, n_runs=4, nx=512, nv=128, horizon=HORIZON, stream=N
     }
 
 
+DATA_KEYS = ("prof", "tsat", "ok", "status", "sat_step", "dt")
+
+
+def part_slice(n, part):
+    """Indices of part "I/P" of n runs: the I-th of P contiguous,
+    nearly equal slices."""
+    i, p = (int(v) for v in part.split("/"))
+    if not 0 <= i < p:
+        raise ValueError("part must be I/P with 0 <= I < P")
+    return np.array_split(np.arange(n), p)[i]
+
+
+def save_data(path, idx, runs, res, prof, tsat, ok):
+    """Labels of the runs with indices idx (runs: all draws), with the
+    solver's cost."""
+    np.savez(path, idx=idx, X=features([runs[q] for q in idx]), prof=prof, tsat=tsat, ok=ok,
+             status=res["status"], sat_step=res["sat_step"], dt=res["dt"],
+             seconds=res["seconds"], batch_steps=res["batch_steps"], cells=res["cells"])
+
+
+def load_data(paths, runs):
+    """Merge data files (whole sets or parts) into the labels of all runs
+    in draw order; every run must be covered exactly once and by the same
+    draw.  The solver cost adds up over the parts (cell_steps: cells x batch
+    steps)."""
+    n = len(runs)
+    X = features(runs)
+    seen = np.zeros(n, dtype=bool)
+    out = {}
+    seconds = cell_steps = 0.0
+    batch_steps = 0
+    for path in paths:
+        d = np.load(path)
+        idx = d["idx"] if "idx" in d.files else np.arange(len(d["X"]))
+        if idx.size and (idx.min() < 0 or idx.max() >= n):
+            raise ValueError("%s: run indices outside the %d draws" % (path, n))
+        if seen[idx].any():
+            raise ValueError("%s: runs covered twice" % path)
+        if not np.array_equal(d["X"], X[idx]):
+            raise ValueError("%s was made from other draws" % path)
+        seen[idx] = True
+        for k in DATA_KEYS:
+            if k not in out:
+                out[k] = np.zeros((n,) + d[k].shape[1:], dtype=d[k].dtype)
+            out[k][idx] = d[k]
+        seconds += float(d["seconds"])
+        cell_steps += float(d["cells"]) * int(d["batch_steps"])
+        batch_steps = max(batch_steps, int(d["batch_steps"]))
+    if not seen.all():
+        raise ValueError("%d of %d runs have no data" % (int((~seen).sum()), n))
+    out.update(seconds=seconds, batch_steps=batch_steps, cell_steps=cell_steps)
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--n-train", type=int, default=4096)
@@ -269,7 +323,10 @@ def main(argv=None):
     ap.add_argument("--horizon", type=float, default=HORIZON)
     ap.add_argument("--out", default="surrogate_out")
     ap.add_argument("--data", default=None,
-                    help="data.npz of an earlier run of the same draws (skips the solver runs)")
+                    help="comma-separated data files of earlier runs of the same draws, whole "
+                         "or parts (skips the solver runs)")
+    ap.add_argument("--solve-part", default=None, metavar="I/P",
+                    help="only solve part I of P of the draws and save its data_partIofP.npz")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-start runs")
     ap.add_argument("--fine", default=None, metavar="WEIGHTS",
                     help="only run fine-grid warm starts with these trained weights")
@@ -289,20 +346,31 @@ def main(argv=None):
         print(json.dumps(rep))
         return
     runs = synth.surrogate_runs(args.n_train + args.n_test, args.seed)
+    if args.solve_part:
+        idx = part_slice(len(runs), args.solve_part)
+        res = solve([runs[q] for q in idx], horizon=args.horizon, stream=stream)
+        prof, tsat, ok = labels(res, args.horizon)
+        i, p = args.solve_part.split("/")
+        path = os.path.join(args.out, "data_part%sof%s.npz" % (i, p))
+        save_data(path, idx, runs, res, prof, tsat, ok)
+        print(json.dumps({"part": args.solve_part, "runs": int(idx.size), "valid": int(ok.sum()),
+                          "solver_seconds": res["seconds"], "batch_steps": res["batch_steps"],
+                          "file": path}))
+        return
     if args.data:
-        d = np.load(args.data)
-        if not np.array_equal(d["X"], features(runs)):
-            raise SystemExit("--data was made from other draws")
+        try:
+            d = load_data(args.data.split(","), runs)
+        except ValueError as e:
+            raise SystemExit("--data: %s" % e)
         res = {k: d[k] for k in ("status", "sat_step", "dt")}
-        res.update(seconds=float(d["seconds"]), batch_steps=int(d["batch_steps"]),
-                   cells=float(d["cells"]))
+        res.update(seconds=d["seconds"], batch_steps=d["batch_steps"], cell_steps=d["cell_steps"])
         prof, tsat, ok = d["prof"], d["tsat"], d["ok"]
     else:
         res = solve(runs, horizon=args.horizon, stream=stream)
+        res["cell_steps"] = res["cells"] * res["batch_steps"]
         prof, tsat, ok = labels(res, args.horizon)
-        np.savez(os.path.join(args.out, "data.npz"), X=features(runs), prof=prof, tsat=tsat,
-                 ok=ok, status=res["status"], sat_step=res["sat_step"], dt=res["dt"],
-                 seconds=res["seconds"], batch_steps=res["batch_steps"], cells=res["cells"])
+        save_data(os.path.join(args.out, "data.npz"), np.arange(len(runs)), runs, res, prof,
+                  tsat, ok)
     tr = np.arange(args.n_train)
     te = np.arange(args.n_train, args.n_train + args.n_test)
     tr_ok = tr[ok[tr]]
@@ -329,7 +397,7 @@ def main(argv=None):
                  "grid": [runs[0]["nx"], runs[0]["nv1"], runs[0]["nv2"]],
                  "horizon_s": args.horizon, "batch_steps": res["batch_steps"],
                  "solver_seconds": res["seconds"],
-                 "cell_updates_per_s": res["cells"] * res["batch_steps"] / res["seconds"]},
+                 "cell_updates_per_s": res["cell_steps"] / res["seconds"]},
         "training": {"epochs": args.epochs, "lr": args.lr, "batch": args.batch,
                      "samples": int(tr_ok.size), "seconds": train_s,
                      "loss_first": float(hist[0]), "loss_last": float(hist[-1])},

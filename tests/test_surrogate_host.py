@@ -1,8 +1,10 @@
 """Host-side logic of the surrogate pipeline (no GPU): features, labels from
-sampled histories (interpolation, censoring, invalid runs) and targets."""
+sampled histories (interpolation, censoring, invalid runs), targets, and the
+data set solved in parts and merged."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_2303_14119_gb300 import fk, surrogate as S, synth
 
@@ -55,3 +57,41 @@ def test_targets_layout():
     Y = S.targets(prof, tsat)
     assert Y.shape == (3, S.N_PROFILE + 1)
     assert np.allclose(Y[:, :-1], 2.0) and np.allclose(Y[:, -1], np.log10(tsat / 1e-9))
+
+
+def _fake_part(runs, idx, seed):
+    rng = np.random.default_rng(seed)
+    m = idx.size
+    res = dict(status=np.zeros(m, dtype=np.int32), sat_step=rng.integers(-1, 9, m),
+               dt=rng.random(m), seconds=1.5, batch_steps=100 + seed, cells=float(m * 10))
+    prof = rng.random((m, S.N_PROFILE))
+    return res, prof, rng.random(m), rng.random(m) > 0.2
+
+
+def test_parts_cover_the_draws_and_merge_back(tmp_path):
+    runs = synth.surrogate_runs(11, 5)
+    parts = [S.part_slice(11, "%d/3" % i) for i in range(3)]
+    assert np.array_equal(np.concatenate(parts), np.arange(11))
+    assert [p.size for p in parts] == [4, 4, 3]
+    with pytest.raises(ValueError):
+        S.part_slice(11, "3/3")
+    paths, want = [], {}
+    for i, idx in enumerate(parts):
+        res, prof, tsat, ok = _fake_part(runs, idx, i)
+        path = str(tmp_path / ("p%d.npz" % i))
+        S.save_data(path, idx, runs, res, prof, tsat, ok)
+        paths.append(path)
+        want[i] = (idx, res, prof, tsat, ok)
+    d = S.load_data(paths[::-1], runs)  # any order
+    for idx, res, prof, tsat, ok in want.values():
+        assert np.array_equal(d["prof"][idx], prof) and np.array_equal(d["tsat"][idx], tsat)
+        assert np.array_equal(d["ok"][idx], ok) and np.array_equal(d["sat_step"][idx], res["sat_step"])
+    assert d["seconds"] == 4.5 and d["batch_steps"] == 102
+    assert d["cell_steps"] == 40 * 100 + 40 * 101 + 30 * 102
+    # a missing part, a doubled part, other draws: refused
+    with pytest.raises(ValueError, match="no data"):
+        S.load_data(paths[:2], runs)
+    with pytest.raises(ValueError, match="twice"):
+        S.load_data(paths + paths[:1], runs)
+    with pytest.raises(ValueError, match="other draws"):
+        S.load_data(paths, synth.surrogate_runs(11, 6))
