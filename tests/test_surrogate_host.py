@@ -88,6 +88,11 @@ def test_parts_cover_the_draws_and_merge_back(tmp_path):
         assert np.array_equal(d["ok"][idx], ok) and np.array_equal(d["sat_step"][idx], res["sat_step"])
     assert d["seconds"] == 4.5 and d["batch_steps"] == 102
     assert d["cell_steps"] == 40 * 100 + 40 * 101 + 30 * 102
+    # features made on another machine may differ in the last bit
+    z = dict(np.load(paths[0]))
+    z["X"] = np.nextafter(z["X"], np.inf)
+    np.savez(paths[0], **z)
+    assert np.array_equal(S.load_data(paths, runs)["prof"], d["prof"])
     # a missing part, a doubled part, other draws: refused
     with pytest.raises(ValueError, match="no data"):
         S.load_data(paths[:2], runs)
