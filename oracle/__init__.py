@@ -185,7 +185,8 @@ class Oracle:
         self._chk(self._lib.oracle_set_reflection(self._h, float(R_f)), "set_reflection")
 
     def set_scheme(self, scheme):
-        """0: unsplit step, 1: Lie splitting (x, then velocity)."""
+        """0: unsplit step, 1: Lie splitting (x, then velocity), 2: Strang
+        splitting (x over dt/2, velocity over dt, x over dt/2)."""
         self._chk(self._lib.oracle_set_scheme(self._h, int(scheme)), "set_scheme")
 
     def set_convergence(self, window, tol):

@@ -27,7 +27,7 @@
  *   5. moments of f^{n+1}, history row, conservation ledger and the
  *      convergence test stated at the end of Sec. 2.
  *
- * Readings taken where the paper is silent (cited as R1..R10 below):
+ * Readings taken where the paper is silent (cited as R1..R14 below):
  *   R1 unsplit forward Euler, all fluxes from f^n;
  *   R2 first-order donor cell upwind;
  *   R3 uniform cell-centred grids in x, v1, v2;
@@ -66,7 +66,16 @@
  *      intermediate state, both over dt and with the fields of f^n; the
  *      surface charge and the wall and vacuum ledger terms come from f^n as
  *      in the unsplit step, the velocity-edge loss from the intermediate
- *      state.
+ *      state;
+ *   R14 Strang splitting (off unless set): an x-advection over dt/2, the
+ *      velocity step over dt, and a second x-advection over dt/2.  The
+ *      velocity step uses the fields and collision rates of f^n, as in R13.
+ *      Each x half-step takes its wall fluxes (Eqs. 12-15, with R12) from its
+ *      own input state, so that what leaves through the wall and what the
+ *      surface charge receives stay the same.  The surface charge and the
+ *      wall and vacuum ledger terms therefore take dt/2 of the fluxes of
+ *      f^n and dt/2 of those of the second half-step's input.  The
+ *      velocity-edge loss comes from the state the velocity step acts on.
  */
 #include <math.h>
 #include <stdint.h>
@@ -537,9 +546,9 @@ int oracle_set_reflection(or_state *s, double R_f) {
   return refresh(s);
 }
 
-/* Time splitting (R13): 0 unsplit, 1 Lie. */
+/* Time splitting: 0 unsplit, 1 Lie (R13), 2 Strang (R14). */
 int oracle_set_scheme(or_state *s, int scheme) {
-  if (scheme != 0 && scheme != 1) return OR_EINVAL;
+  if (scheme != 0 && scheme != 1 && scheme != 2) return OR_EINVAL;
   s->scheme = scheme;
   return OR_OK;
 }
@@ -588,56 +597,50 @@ static void unsplit_update(or_state *s) {
   }
 }
 
-/* R13: x-advection of f^n into f_next, then the velocity step of that
- * intermediate state (the flux helpers read s->f, so it stands in for f^n
- * meanwhile) into f_tmp, copied back to f_next.  *lv receives the
- * velocity-edge loss of the intermediate state. */
-static void lie_update(or_state *s, double *lv) {
-  const double dt = s->dt;
+/* x-advection over h of the state in s->f into out, with the wall inflow of
+ * Eq. 15 from s->g_see (the wall fluxes of that state). */
+static void x_pass(or_state *s, double h, double *out) {
   for (int k = 0; k < s->nx; k++)
     for (int i = 0; i < s->nv1; i++)
       for (int j = 0; j < s->nv2; j++) {
         double dFx = flux_x(s, k + 1, i, j) - flux_x(s, k, i, j);
-        s->f_next[cell(s, k, i, j)] = s->f[cell(s, k, i, j)] - dt / s->dx * dFx;
+        out[cell(s, k, i, j)] = s->f[cell(s, k, i, j)] - h / s->dx * dFx;
       }
-  double *fn = s->f;
-  s->f = s->f_next;
+}
+
+/* Velocity step over h of the state in s->f into out, with the fields and
+ * collision rates of f^n (s->a1, s->ne). */
+static void v_pass(or_state *s, double h, double *out) {
   for (int k = 0; k < s->nx; k++) {
-    const double nu = nu_plane(s, k); /* n_e of f^n (s->ne) */
+    const double nu = nu_plane(s, k);
     for (int i = 0; i < s->nv1; i++)
       for (int j = 0; j < s->nv2; j++) {
         double dFv1 = flux_v1(s, k, i + 1, j) - flux_v1(s, k, i, j);
         double dFv2 = flux_v2(s, k, i, j + 1) - flux_v2(s, k, i, j);
         double coll = nu * (s->ne[k] * s->g_e0[vcell(s, i, j)] - s->f[cell(s, k, i, j)]);
-        s->f_tmp[cell(s, k, i, j)] = s->f[cell(s, k, i, j)] - dt / s->dv1 * dFv1 -
-                                     dt / s->dv2 * dFv2 + dt * source(s, k, i, j) + dt * coll;
+        out[cell(s, k, i, j)] = s->f[cell(s, k, i, j)] - h / s->dv1 * dFv1 -
+                                h / s->dv2 * dFv2 + h * source(s, k, i, j) + h * coll;
       }
   }
+}
+
+/* R13: x-advection of f^n into f_next, then the velocity step of that
+ * intermediate state (the flux helpers read s->f, so it stands in for f^n
+ * meanwhile) into f_tmp, copied back to f_next.  *lv receives the
+ * velocity-edge loss of the intermediate state. */
+static void lie_update(or_state *s, double *lv) {
+  double *fn = s->f;
+  x_pass(s, s->dt, s->f_next);
+  s->f = s->f_next;
+  v_pass(s, s->dt, s->f_tmp);
   *lv = edge_loss(s);
   s->f = fn;
   memcpy(s->f_next, s->f_tmp, (size_t)s->nx * s->nv1 * s->nv2 * sizeof(double));
 }
 
-static int one_step(or_state *s) {
-  if (oracle_courant_sum(s) > 1.0 + 1e-12) return OR_ECFL;
-  const double dt = s->dt;
-  double lv_step = s->l_v; /* loss of the state the velocity advection acts on */
-  if (s->scheme == 1)
-    lie_update(s, &lv_step);
-  else
-    unsplit_update(s);
-  /* ledger: fluxes of state n times dt */
-  double inj = 0.0;
-  for (int k = 0; k < s->nx; k++)
-    for (int i = 0; i < s->nv1; i++)
-      for (int j = 0; j < s->nv2; j++) inj += source(s, k, i, j) * s->dx * s->dv1 * s->dv2;
-  s->cum_emit += dt * s->g_emit;
-  s->cum_see += dt * s->g_see;
-  s->cum_pe += dt * s->g_pe;
-  s->cum_vac += dt * s->g_vac;
-  s->cum_lv += dt * lv_step;
-  s->cum_inj += dt * inj;
-  /* Eq. 18: sigma^{n+1} = sigma^n + e dt sum_{v1<0} (delta - 1) dGamma_pe */
+/* Charge deposited per unit time by the wall fluxes of the state in s->f
+ * (the sum of Eq. 18 without e dt). */
+static double wall_charge_rate(const or_state *s) {
   double dsig = 0.0;
   for (int i = 0; i < s->nv1; i++) {
     if (!(s->v1[i] < 0.0)) continue;
@@ -647,7 +650,78 @@ static int one_step(or_state *s) {
       dsig += (1.0 - s->refl) * (d - 1.0) * dG; /* R12: reflected electrons deposit nothing */
     }
   }
-  s->sigma += OR_QE * dt * dsig;
+  return dsig;
+}
+
+/* Boundary terms of the second x half-step of a Strang step. */
+typedef struct {
+  double emit, see, pe, vac, dsig;
+} half_wall;
+
+/* R14: Strang, x over dt/2, velocity over dt, x over dt/2.  The first x
+ * half-step takes the wall fluxes of f^n, the second those of its own
+ * input (Eqs. 12-15 on that state), returned in *w2 for sigma and the
+ * ledger; *lv receives the velocity-edge loss of the state the velocity
+ * step acts on.  f_next receives f^{n+1}; s->f and the wall fluxes of f^n
+ * are left as they were. */
+static void strang_update(or_state *s, double *lv, half_wall *w2) {
+  const double h = 0.5 * s->dt;
+  double *fn = s->f, *f1 = s->f_next, *f2 = s->f_tmp;
+  const double g_pe = s->g_pe, g_see = s->g_see;
+  x_pass(s, h, f1);
+  s->f = f1;
+  v_pass(s, s->dt, f2);
+  *lv = edge_loss(s);
+  s->f = f2;
+  evaluate_wall(s); /* Gamma_pe, Gamma_see of the second half-step's input */
+  w2->pe = s->g_pe;
+  w2->see = s->g_see;
+  w2->emit = w2->vac = 0.0;
+  for (int i = 0; i < s->nv1; i++)
+    for (int j = 0; j < s->nv2; j++) {
+      if (s->v1[i] > 0.0) w2->emit += flux_x(s, 0, i, j) * s->dv1 * s->dv2;
+      w2->vac += flux_x(s, s->nx, i, j) * s->dv1 * s->dv2;
+    }
+  w2->dsig = wall_charge_rate(s);
+  x_pass(s, h, f1);
+  s->f = fn;
+  s->g_pe = g_pe;
+  s->g_see = g_see;
+}
+
+static int one_step(or_state *s) {
+  if (oracle_courant_sum(s) > 1.0 + 1e-12) return OR_ECFL;
+  const double dt = s->dt;
+  double lv_step = s->l_v; /* loss of the state the velocity advection acts on */
+  /* share of the step's dt carried by the boundary terms of f^n */
+  const double hn = s->scheme == 2 ? 0.5 * dt : dt;
+  half_wall w2 = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (s->scheme == 2)
+    strang_update(s, &lv_step, &w2);
+  else if (s->scheme == 1)
+    lie_update(s, &lv_step);
+  else
+    unsplit_update(s);
+  /* ledger: fluxes of state n times dt */
+  double inj = 0.0;
+  for (int k = 0; k < s->nx; k++)
+    for (int i = 0; i < s->nv1; i++)
+      for (int j = 0; j < s->nv2; j++) inj += source(s, k, i, j) * s->dx * s->dv1 * s->dv2;
+  s->cum_emit += hn * s->g_emit;
+  s->cum_see += hn * s->g_see;
+  s->cum_pe += hn * s->g_pe;
+  s->cum_vac += hn * s->g_vac;
+  s->cum_lv += dt * lv_step;
+  s->cum_inj += dt * inj;
+  /* Eq. 18: sigma^{n+1} = sigma^n + e dt sum_{v1<0} (delta - 1) dGamma_pe */
+  s->sigma += OR_QE * hn * wall_charge_rate(s);
+  if (s->scheme == 2) { /* the second x half-step's boundary terms (R14) */
+    s->cum_emit += hn * w2.emit;
+    s->cum_see += hn * w2.see;
+    s->cum_pe += hn * w2.pe;
+    s->cum_vac += hn * w2.vac;
+    s->sigma += OR_QE * hn * w2.dsig;
+  }
   double *t = s->f;
   s->f = s->f_next;
   s->f_next = t;

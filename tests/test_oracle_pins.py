@@ -725,3 +725,156 @@ def test_lie_ledger_closes():
     assert abs((L["N"] - L["N0"]) - rhs) < 1e-12 * scale
     dsig = o.surface_charge() - L["sigma0"]
     assert dsig / QE == pytest.approx(L["see"] - L["pe"], rel=1e-12)
+
+
+# ---- Strang splitting (x over dt/2, velocity over dt, x over dt/2)
+def test_strang_without_velocity_terms_is_two_half_steps():
+    """With no force, source or collisions the velocity step is the
+    identity, and a Strang step is two x-advection steps of dt/2, each with
+    the wall fluxes of its own input: exactly two unsplit steps of dt/2."""
+    h = 20e-6
+    nx, nv1, nv2 = 9, 10, 8
+    f0 = np.random.default_rng(4).uniform(size=(nx, nv1, nv2)) * 1e10
+    ref = Oracle(nx, nv1, nv2, h, -6e7, 6e7, -3e7, 3e7, cfl=0.4)
+    dt = ref.info()["dt"]
+    out = []
+    for scheme, step_dt, n in ((2, dt, 3), (0, 0.5 * dt, 6)):
+        o = Oracle(nx, nv1, nv2, h, -6e7, 6e7, -3e7, 3e7, dt=step_dt)
+        o.set_fields(0.0, False, 0.0)
+        o.set_see(3.0, 400.0, 1.0, 400.0)
+        o.set_reflection(0.3)
+        o.set_scheme(scheme)
+        o.set_state(f0, 1e-6)
+        o.step(n)
+        out.append((o.get_f(), o.surface_charge(), o.ledger()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+    for key in ("emit", "see", "pe", "vac"):
+        assert out[0][2][key] == out[1][2][key], key
+
+
+def _dense_generators(f, sigma, tabs, grid, p):
+    """Generators of the two sub-steps as matrices and a vector: the x pass
+    over h is f + h Ax f (Eq. 15 inflow built from the pass's own input), the
+    velocity pass over h is g + h (Av g + s) with the fields of f."""
+    nx, nv1, nv2 = f.shape
+    x, v1, v2 = grid
+    dx, dv1, dv2 = p["dx"], p["dv1"], p["dv2"]
+    delta, gse, gfe = tabs
+    N = f.size
+    L = lambda k, i, j: (k * nv1 + i) * nv2 + j
+    ne = f.sum(axis=(1, 2)) * dv1 * dv2
+    ex, _ = _poisson_fd(ne, sigma, dx)
+    a1 = -QE * ex / ME
+    a2 = -QE * p["Ey"] / ME
+    Ax = np.zeros((N, N))
+    Av = np.zeros((N, N))
+    s = np.zeros(N)
+    r_see = np.zeros(N)
+    for i in range(nv1):
+        for j in range(nv2):
+            if v1[i] < 0:
+                r_see[L(0, i, j)] = delta[i, j] * (-v1[i]) * dv1 * dv2
+
+    def add_face(A, lo, hi, row, scale):
+        if lo is not None:
+            A[lo] -= scale * row
+        if hi is not None:
+            A[hi] += scale * row
+
+    for kf in range(nx + 1):
+        for i in range(nv1):
+            for j in range(nv2):
+                row = np.zeros(N)
+                if v1[i] > 0:
+                    row = v1[i] * gse[i, j] * r_see if kf == 0 else _unit(N, L(kf - 1, i, j)) * v1[i]
+                elif v1[i] < 0 and kf < nx:
+                    row = _unit(N, L(kf, i, j)) * v1[i]
+                add_face(Ax, L(kf - 1, i, j) if kf > 0 else None, L(kf, i, j) if kf < nx else None,
+                         row, 1.0 / dx)
+    for k in range(nx):
+        for jf in range(nv2 + 1):
+            for i in range(nv1):
+                row = np.zeros(N)
+                if a2 > 0 and jf > 0:
+                    row = _unit(N, L(k, i, jf - 1)) * a2
+                elif a2 < 0 and jf < nv2:
+                    row = _unit(N, L(k, i, jf)) * a2
+                add_face(Av, L(k, i, jf - 1) if jf > 0 else None, L(k, i, jf) if jf < nv2 else None,
+                         row, 1.0 / dv2)
+        for iface in range(nv1 + 1):
+            for j in range(nv2):
+                row = np.zeros(N)
+                if a1[k] > 0 and iface > 0:
+                    row = _unit(N, L(k, iface - 1, j)) * a1[k]
+                elif a1[k] < 0 and iface < nv1:
+                    row = _unit(N, L(k, iface, j)) * a1[k]
+                add_face(Av, L(k, iface - 1, j) if iface > 0 else None,
+                         L(k, iface, j) if iface < nv1 else None, row, 1.0 / dv1)
+    band = [k for k in range(nx) if p["x_lo"] <= x[k] <= p["x_hi"]]
+    for k in band:
+        for i in range(nv1):
+            for j in range(nv2):
+                s[L(k, i, j)] += p["J"] / QE / (len(band) * dx) * gfe[i, j]
+    return Ax, Av, s
+
+
+def _wall_charge_rate(f, tabs, grid, p):
+    delta = tabs[0]
+    v1 = grid[1]
+    return sum((delta[i, j] - 1.0) * (-v1[i]) * f[0, i, j] * p["dv1"] * p["dv2"]
+               for i in range(f.shape[1]) if v1[i] < 0 for j in range(f.shape[2]))
+
+
+def test_strang_dense_matrix_brute_force():
+    o, f0, sigma, p = _strong_case(4, 4, 5, seed=7)
+    o.set_scheme(2)
+    o.set_state(f0, sigma)
+    assert o.courant_sum() <= 1.0
+    tabs, grid = o.tables(), o.grid()
+    dt = p["dt"]
+    f, s = f0.copy(), sigma
+    for _ in range(4):
+        Ax, Av, src = _dense_generators(f, s, tabs, grid, p)
+        f1 = f.ravel() + 0.5 * dt * (Ax @ f.ravel())
+        f2 = f1 + dt * (Av @ f1 + src)
+        f3 = f2 + 0.5 * dt * (Ax @ f2)
+        s = s + QE * 0.5 * dt * (_wall_charge_rate(f, tabs, grid, p) +
+                                 _wall_charge_rate(f2.reshape(f.shape), tabs, grid, p))
+        f = f3.reshape(f.shape)
+    o.step(4)
+    assert np.abs(o.get_f() - f).sum() / np.abs(f).sum() < 1e-13
+    assert o.surface_charge() == pytest.approx(s, rel=1e-12)
+    # a step that differs from both the unsplit and the Lie step
+    res = {}
+    for scheme in (0, 1, 2):
+        q = Oracle(4, 4, 5, 20e-6, -6e7, 6e7, -3e7, 3e7, cfl=0.4)
+        q.set_fields(p["Ey"], True, 0.0)
+        q.set_see(3.0, 400.0, 1.0, 400.0)
+        q.set_source(p["J"], p["x_lo"], p["x_hi"], 300.0)
+        q.set_scheme(scheme)
+        q.set_state(f0, sigma)
+        q.step(1)
+        res[scheme] = q.get_f()
+    for other in (0, 1):
+        assert np.abs(res[2] - res[other]).max() > 1e-6 * np.abs(res[other]).max()
+
+
+def test_strang_ledger_and_charge_close():
+    """Without collisions (whose split form uses the density of f^n on the
+    intermediate state, R13/R14) the electron and charge balance close."""
+    o, f0, sigma, p = _strong_case(14, 12, 10, seed=23)
+    o.set_reflection(0.25)
+    o.set_scheme(2)
+    o.set_state(f0, sigma)
+    assert o.courant_sum() <= 1.0
+    o.step(40)
+    L = o.ledger()
+    rhs = L["emit"] - L["pe"] - L["vac"] - L["lv"] + L["inj"]
+    scale = max(abs(L["emit"]), abs(L["pe"]), abs(L["vac"]), abs(L["lv"]), abs(L["inj"]), L["N"])
+    assert abs((L["N"] - L["N0"]) - rhs) < 1e-12 * scale
+    dsig = o.surface_charge() - L["sigma0"]
+    # R12: only the absorbed (1 - R_f) part of the incident flux deposits charge
+    assert dsig / QE == pytest.approx(L["see"] - 0.75 * L["pe"], rel=1e-10)
+    with pytest.raises(oracle.OracleError):
+        o.set_scheme(3)
