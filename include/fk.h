@@ -160,12 +160,19 @@ fk_status fk_set_reflection(fk_grid *grid, double R_f);
  * vacuum boundaries) over dt, then the velocity step (v1, v2 advection,
  * source, collisions) of that intermediate state over dt, both with the
  * fields of f^n; the surface charge and the wall ledger terms come from f^n
- * as in the unsplit step.  Sec. 2 states only an explicit upwind update;
- * the split form runs as two passes over f (the direct-load kernel and one
- * more buffer of f), and grids using it cannot join a batch.  FK_EINVAL for
- * another value; FK_ESTATE while the grid is in a batch. */
+ * as in the unsplit step.  FK_SCHEME_STRANG: Strang splitting --
+ * x-advection over dt/2, the velocity step over dt with the fields of f^n,
+ * x-advection over dt/2; each x half-step takes its wall fluxes (Eqs. 12-15)
+ * from its own input state, so the surface charge and the wall ledger terms
+ * take dt/2 of the fluxes of f^n and dt/2 of those of the state after the
+ * velocity step.  Sec. 2 states only an explicit upwind update; the split
+ * forms run as two (Lie) or three (Strang) passes over f (the direct-load
+ * kernel and one more buffer of f), and grids using them cannot join a
+ * batch.  FK_EINVAL for another value; FK_ESTATE while the grid is in a
+ * batch. */
 #define FK_SCHEME_UNSPLIT 0
 #define FK_SCHEME_LIE 1
+#define FK_SCHEME_STRANG 2
 fk_status fk_set_scheme(fk_grid *grid, int scheme);
 
 /* Convergence test of Sec. 2 (paragraph after Eq. 18): the run is saturated
@@ -294,9 +301,10 @@ fk_status fk_density_moment_noalloc(const double *f_dev, int32_t nx, int32_t nv1
 /* ---- Batched stepping of many grids (parameter sweeps) --------------------
  * The paper's design studies (Sec. 3: scans over E_y, delta_max, A_max and
  * T_se, each point a separate run) are many small independent runs.  A batch
- * steps a set of existing grids together: every batch step is ONE launch of
+ * steps a set of existing grids together: every batch step is one launch of
  * the streaming step kernel over the work units (v1-row tile x x-chunk) of
- * all grids, largest units first, followed by ONE launch of the finalize
+ * all grids, largest units first (a second launch runs the units of grids
+ * whose thin tiles go two to a CTA), followed by ONE launch of the finalize
  * kernel over all grids' planes, replayed 32 steps per CUDA graph.  Each
  * grid's arithmetic is exactly that of fk_step on the same grid: the x-chunk
  * split (the only thing the batch chooses) changes which CTA updates a cell,

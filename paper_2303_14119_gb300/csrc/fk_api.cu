@@ -148,6 +148,20 @@ cudaError_t enqueue_step(fk_grid* g, int cur, cudaStream_t s, cudaEvent_t ev0, c
       av.f_in = g->d_f3;
       e = launch_step_pass(ax, g->prec, kPassX, s);
       if (e == cudaSuccess) e = launch_step_pass(av, g->prec, kPassV, s);
+    } else if (g->scheme == kSchemeStrang) {
+      // x over dt/2 into the other state buffer, the velocity step of that
+      // into the third buffer, the wall fluxes of the result (and dt/2 of
+      // them into sigma and the ledger), x over dt/2 of it back into the
+      // other buffer with the inflow of those fluxes
+      StepArgs x1 = a, av = a, x2 = a;
+      av.f_in = a.f_out;
+      av.f_out = g->d_f3;
+      x2.f_in = g->d_f3;
+      x2.st = g->d_st_mid;
+      e = launch_step_pass(x1, g->prec, kPassXHalf, s);
+      if (e == cudaSuccess) e = launch_step_pass(av, g->prec, kPassV, s);
+      if (e == cudaSuccess) e = launch_strang_mid(av, g->d_st_mid, s);
+      if (e == cudaSuccess) e = launch_step_pass(x2, g->prec, kPassXHalfLast, s);
     } else {
       e = g->use_stream ? launch_step_stream(a, g->prec, g->prm.collisions != 0, s)
                         : launch_step(a, g->prec, 0, s);
@@ -155,7 +169,8 @@ cudaError_t enqueue_step(fk_grid* g, int cur, cudaStream_t s, cudaEvent_t ev0, c
   }
   if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
   if (e == cudaSuccess)
-    e = launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, g->fin, kModeStep, s);
+    e = launch_finalize(a, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist, g->fin,
+                        g->scheme == kSchemeStrang ? kModeStepStrang : kModeStep, s);
   return e;
 }
 
@@ -209,7 +224,8 @@ void free_grid(fk_grid* g) {
                   g->tab.m1_32, g->tab.m2_32, g->d_bgk, g->d_bgk32, g->part.n, g->part.lv,
                   g->part.pe, g->part.see,
                   g->part.vac, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist,
-                  g->d_stage, g->d_f3, g->fin.pre, g->fin.bsum, g->fin.blv, g->fin.counter};
+                  g->d_stage, g->d_f3, g->d_st_mid, g->fin.pre, g->fin.bsum, g->fin.blv,
+                  g->fin.counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->h_stage) cudaFreeHost(g->h_stage);
@@ -222,6 +238,18 @@ void free_grid(fk_grid* g) {
 template <typename P>
 cudaError_t dalloc(P** p, size_t bytes) {
   return cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16);
+}
+
+// The buffers a time scheme needs beyond the two state buffers: a third
+// buffer of f for the split steps, and the Strang step's second state block.
+fk_status split_buffers(fk_grid* g, int scheme) {
+  if (scheme != kSchemeUnsplit && !g->d_f3)
+    FK_CUDA(g, dalloc(&g->d_f3, (size_t)g->nx * g->nv1 * g->pitch * g->esize));
+  if (scheme == kSchemeStrang && !g->d_st_mid) {
+    FK_CUDA(g, dalloc(&g->d_st_mid, sizeof(DevState)));
+    FK_CUDA(g, cudaMemsetAsync(g->d_st_mid, 0, sizeof(DevState), g->stream));
+  }
+  return FK_OK;
 }
 
 fk_status build_graph(fk_grid* g, int parity) {
@@ -608,11 +636,14 @@ fk_status fk_set_reflection(fk_grid* g, double R_f) {
 fk_status fk_set_scheme(fk_grid* g, int scheme) {
   if (!g) return FK_EINVAL;
   FK_NOT_IN_BATCH(g);
-  if (scheme != FK_SCHEME_UNSPLIT && scheme != FK_SCHEME_LIE)
-    return fail(g, FK_EINVAL, "scheme must be FK_SCHEME_UNSPLIT or FK_SCHEME_LIE");
+  if (scheme != FK_SCHEME_UNSPLIT && scheme != FK_SCHEME_LIE && scheme != FK_SCHEME_STRANG)
+    return fail(g, FK_EINVAL,
+                "scheme must be FK_SCHEME_UNSPLIT, FK_SCHEME_LIE or FK_SCHEME_STRANG");
   FK_CUDA(g, cudaSetDevice(g->dev));
-  if (scheme == FK_SCHEME_LIE && !g->d_f3)
-    FK_CUDA(g, cudaMalloc(&g->d_f3, (size_t)g->nx * g->nv1 * g->pitch * g->esize));
+  {
+    const fk_status bs = split_buffers(g, scheme);
+    if (bs != FK_OK) return bs;
+  }
   if (scheme != g->scheme) {
     // the captured graphs hold the other scheme's kernels
     FK_CUDA(g, cudaStreamSynchronize(g->stream));
@@ -955,11 +986,15 @@ fk_status fk_set_state(fk_grid* g, const void* buf, size_t len) {
     return fail(g, FK_EINVAL,
                 "checkpoint of another grid (shape, precision or history capacity differ)");
   if (len < state_bytes(g)) return fail(g, FK_EINVAL, "checkpoint truncated");
+  if (h.scheme != kSchemeUnsplit && h.scheme != kSchemeLie && h.scheme != kSchemeStrang)
+    return fail(g, FK_EINVAL, "checkpoint with an unknown time scheme");
   DevState cur;
   fk_status s = sync_state(g, &cur);
   if (s != FK_OK) return s;
-  if (h.scheme == kSchemeLie && !g->d_f3)
-    FK_CUDA(g, cudaMalloc(&g->d_f3, f_bytes(g)));
+  {
+    const fk_status bs = split_buffers(g, h.scheme);
+    if (bs != FK_OK) return bs;
+  }
   // graphs were captured for the old kernel variants
   for (int q = 0; q < 2; q++)
     if (g->graph[q]) {

@@ -52,7 +52,8 @@ struct fk_grid {
   // batch that steps this grid: while set, calls that change the state are
   // refused and the getters wait for the batch's last enqueued step
   int scheme = 0;             // kSchemeUnsplit or kSchemeLie
-  void* d_f3 = nullptr;       // intermediate state of the Lie-split step
+  void* d_f3 = nullptr;       // intermediate state of the split steps
+  fk::DevState* d_st_mid = nullptr;  // Strang step: wall fluxes after the velocity pass
   fk_batch* batch = nullptr;
   cudaEvent_t batch_done = nullptr;
   std::string err;
@@ -61,13 +62,33 @@ struct fk_grid {
 namespace fk {
 
 // Passes of the direct-load step kernel: a whole step, the moments of f_in
-// only, and the two passes of the Lie-split step (x-advection with the wall
-// and vacuum boundaries; then v1, v2 advection, source and collisions).
-enum StepPass { kPassFull = 0, kPassMoments = 1, kPassX = 2, kPassV = 3 };
+// only, and the passes of the split steps: x-advection with the wall and
+// vacuum boundaries (over dt; over dt/2 without partial sums; over dt/2
+// writing every partial sum but the velocity-edge loss, the last pass of a
+// Strang step), and v1, v2 advection, source and collisions.
+enum StepPass {
+  kPassFull = 0,
+  kPassMoments = 1,
+  kPassX = 2,
+  kPassV = 3,
+  kPassXHalf = 4,
+  kPassXHalfLast = 5
+};
 cudaError_t launch_step_pass(const StepArgs& a, int precision, int mode, cudaStream_t s);
 
 // Time schemes of a grid (fk_set_scheme).
-enum Scheme { kSchemeUnsplit = 0, kSchemeLie = 1 };
+enum Scheme { kSchemeUnsplit = 0, kSchemeLie = 1, kSchemeStrang = 2 };
+
+// Finalize mode of a Strang step, beside the modes of FinalizeMode: the wall
+// and vacuum terms of f^n weigh dt/2 (the other half came from the state
+// after the velocity pass, folded by launch_strang_mid).
+constexpr int kModeStepStrang = 3;
+// Strang step, after the velocity pass: fold its wall and vacuum partial
+// sums (those of the state the second x half-pass acts on), add dt/2 of
+// them to the surface charge and the ledger in a.st, and write that state's
+// Gamma_see and the flags into *mid, the state block of the second x
+// half-pass.
+cudaError_t launch_strang_mid(const StepArgs& a, DevState* mid, cudaStream_t s);
 
 // Per-step arguments of the grid with f^n in buffer cur.
 StepArgs make_args(fk_grid* g, int cur);

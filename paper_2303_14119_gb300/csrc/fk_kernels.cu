@@ -275,9 +275,13 @@ step_direct_kernel(StepArgs a, int mode) {
   __syncthreads();
   // mode: kPassFull, kPassMoments (moments of f_in only), kPassX (x-advection
   // with the wall and vacuum boundaries only), kPassV (v1, v2 advection,
-  // source and collisions only); the last two make the Lie-split step
+  // source and collisions only): these two make the Lie-split step;
+  // kPassXHalf and kPassXHalfLast (x-advection over dt/2, the second one
+  // writing the partial sums of its output) with kPassV make the Strang step
   const bool moments_only = mode == kPassMoments;
-  const bool xpass = mode == kPassX, vpass = mode == kPassV;
+  const bool xlast = mode == kPassXHalfLast;
+  const bool xpass = mode == kPassX || mode == kPassXHalf || xlast, vpass = mode == kPassV;
+  const T xscale = (mode == kPassXHalf || xlast) ? (T)0.5 : (T)1;  // dt/2: exact halving
   if (!moments_only && s_flags) return;  // sticky error: freeze the state
   const T* __restrict__ fin = static_cast<const T*>(a.f_in);
   T* __restrict__ fout = static_cast<T*>(a.f_out);
@@ -307,7 +311,8 @@ step_direct_kernel(StepArgs a, int mode) {
     const T f = fin[idx];
     T fn = f;
     if (!moments_only) {
-      const T cx = vpass ? (T)0 : (sizeof(T) == 8 ? (T)a.tab.cx[i] : (T)a.tab.cx32[i]);
+      const T cx =
+          vpass ? (T)0 : xscale * (sizeof(T) == 8 ? (T)a.tab.cx[i] : (T)a.tab.cx32[i]);
       T fx = (T)0;
       if (cx > (T)0)
         fx = k > 0 ? fin[idx - plane]
@@ -347,7 +352,9 @@ step_direct_kernel(StepArgs a, int mode) {
     }
     if (k == nx - 1 && dir > 0) s_vac += a.tab.v1[i] * (double)fn;
   }
-  if (xpass) return;  // the velocity pass writes every partial sum (uniform)
+  // the velocity pass (and the last pass of a Strang step) writes the
+  // partial sums (uniform)
+  if (xpass && !xlast) return;
   const double n_tot = block_sum<kStepThreads>((double)s_n, sh);
   s_lv = block_sum<kStepThreads>(s_lv, sh);
   if (k == 0) {
@@ -357,7 +364,7 @@ step_direct_kernel(StepArgs a, int mode) {
   if (k == nx - 1) s_vac = block_sum<kStepThreads>(s_vac, sh);
   if (threadIdx.x == 0) {
     a.part.n[(size_t)k * nt + t] = n_tot;
-    a.part.lv[(size_t)k * nt + t] = s_lv;
+    if (!xlast) a.part.lv[(size_t)k * nt + t] = s_lv;  // Strang: the velocity pass's
     if (k == 0) {
       a.part.pe[t] = s_pe;
       a.part.see[t] = s_see;
@@ -389,6 +396,8 @@ cudaError_t launch_step(const StepArgs& a, int precision, int moments_only, cuda
 // fixed order, so the result does not depend on which block it is):
 //  - step mode: ledger += dt * (fluxes of f^n), sigma^{n+1} = sigma^n +
 //    e dt (Gamma_see^n - Gamma_pe^n)  (Eq. 18 summed with Eq. 14), step++;
+//    in the Strang step mode the wall and vacuum terms of f^n weigh dt/2
+//    (the other half was added after the velocity pass);
 //  - the fluxes of the new state (Eqs. 12-14), N, and the history row;
 //  - E_x from Gauss's law integrated from the wall, E_x(0) = sigma/(2 eps0)
 //    (the Poisson problem of Sec. 2), c_1 = -e E_x dt / (m_e dv1);
@@ -415,7 +424,8 @@ __device__ __forceinline__ void finalize_body(const StepArgs& a, const FinOut& o
   __shared__ double boff[kFinMaxBlocks];  // phase B: sum of n over blocks below
   const Params& p = *a.prm;
   DevState* st = a.st;
-  if (mode == kModeStep && st->flags) return;
+  const bool stepping = mode == kModeStep || mode == kModeStepStrang;
+  if (stepping && st->flags) return;
   const int nx = a.nx, nu = a.part.nu;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int k = blk * kFinThreads + t;
@@ -516,15 +526,16 @@ __device__ __forceinline__ void finalize_body(const StepArgs& a, const FinOut& o
       // with SEE off every absorbed primary is deposited
       see = p.see_enabled ? see * p.dvv * (1.0 - p.refl) : 0.0;
       vac *= p.dvv;
-      if (mode == kModeStep) {
+      if (stepping) {
         const double lv = l * p.lv_scale;
-        d.cum_emit += p.dt * (d.g_see + p.refl * d.g_pe);  // secondaries and reflected
-        d.cum_see += p.dt * d.g_see;
-        d.cum_pe += p.dt * d.g_pe;
-        d.cum_vac += p.dt * d.g_vac;
+        const double hw = mode == kModeStepStrang ? 0.5 * p.dt : p.dt;  // wall terms' share
+        d.cum_emit += hw * (d.g_see + p.refl * d.g_pe);  // secondaries and reflected
+        d.cum_see += hw * d.g_see;
+        d.cum_pe += hw * d.g_pe;
+        d.cum_vac += hw * d.g_vac;
         d.cum_lv += p.dt * lv;
         d.cum_inj += p.dt * p.inj;
-        d.sigma += kQe * p.dt * (d.g_see - (1.0 - p.refl) * d.g_pe);
+        d.sigma += kQe * hw * (d.g_see - (1.0 - p.refl) * d.g_pe);
         d.step += 1;
       }
       if (mode == kModeReset) {
@@ -583,7 +594,7 @@ __device__ __forceinline__ void finalize_body(const StepArgs& a, const FinOut& o
     double* r = hist + (size_t)(row % cap) * FK_HISTORY_COLS;
     for (int q = 0; q < FK_HISTORY_COLS; q++) r[q] = rr[q];
     if (row + 1 > d.hist_count) d.hist_count = row + 1;
-    if (mode == kModeStep && d.sat_step < 0 && row >= p.sat_window && p.sat_window < cap) {
+    if (stepping && d.sat_step < 0 && row >= p.sat_window && p.sat_window < cap) {
       const double* o = hist + (size_t)((row - p.sat_window) % cap) * FK_HISTORY_COLS;
       bool ok = true;
       for (int q = 2; q <= 4; q++)
@@ -612,6 +623,47 @@ finalize_batch_kernel(const BatchInst* __restrict__ inst, const int2* __restrict
   for (int w = threadIdx.x; w < (int)(sizeof(BatchInst) / 8); w += blockDim.x) dst[w] = src[w];
   __syncthreads();
   finalize_body(bi.a, bi.o, m.y, (bi.a.nx + kFinThreads - 1) / kFinThreads, kModeStep);
+}
+
+// Strang step, after the velocity pass (one warp): fold the wall and vacuum
+// partial sums of the velocity pass's output as the finalize kernel folds
+// those of a new state, add dt/2 of the resulting fluxes to the ledger and
+// the surface charge (Eqs. 12-14, 18), and hand Gamma_see of that state and
+// the sticky flags to the second x half-pass through *mid.
+__global__ void strang_mid_kernel(const __grid_constant__ StepArgs a, DevState* mid) {
+  const Params& p = *a.prm;
+  DevState* st = a.st;
+  const int lane = threadIdx.x;
+  const unsigned flags = st->flags;
+  double pe = 0.0, see = 0.0, vac = 0.0;
+  for (int u = lane; u < a.part.nu; u += 32) {
+    pe += a.part.pe[u];
+    see += a.part.see[u];
+    vac += a.part.vac[u];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    pe += __shfl_down_sync(0xffffffffu, pe, o);
+    see += __shfl_down_sync(0xffffffffu, see, o);
+    vac += __shfl_down_sync(0xffffffffu, vac, o);
+  }
+  if (lane != 0) return;
+  mid->flags = flags;
+  if (flags) return;  // frozen state: the passes do nothing either
+  pe *= p.dvv;
+  see = p.see_enabled ? see * p.dvv * (1.0 - p.refl) : 0.0;
+  vac *= p.dvv;
+  mid->g_see = see;
+  const double h = 0.5 * p.dt;
+  st->cum_emit += h * (see + p.refl * pe);
+  st->cum_see += h * see;
+  st->cum_pe += h * pe;
+  st->cum_vac += h * vac;
+  st->sigma += kQe * h * (see - (1.0 - p.refl) * pe);
+}
+
+cudaError_t launch_strang_mid(const StepArgs& a, DevState* mid, cudaStream_t s) {
+  strang_mid_kernel<<<1, 32, 0, s>>>(a, mid);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const StepArgs& a, double* ne, double* Ex, double* c1,

@@ -52,7 +52,7 @@ def assert_same(a, b):
 
 
 @pytest.mark.parametrize("prec", [fk.FK_F64, fk.FK_F32])
-@pytest.mark.parametrize("scheme", [fk.FK_SCHEME_UNSPLIT, fk.FK_SCHEME_LIE])
+@pytest.mark.parametrize("scheme", [fk.FK_SCHEME_UNSPLIT, fk.FK_SCHEME_LIE, fk.FK_SCHEME_STRANG])
 def test_restored_grid_continues_bitwise(prec, scheme):
     shape = (20, 32, 26)
     a = configured(shape, prec, scheme)
