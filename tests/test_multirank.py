@@ -55,15 +55,17 @@ def test_single_process_defaults():
     assert bench.job_throughput(1, 3, 10, 2, 1000.0) == pytest.approx(60.0)
 
 
-def test_reference_arm_prints_its_json_line():
+@pytest.mark.parametrize("workload", ["small_64x48x48", "surrogate_1536"])
+def test_reference_arm_prints_its_json_line(workload):
     """bench.py --impl reference times the CPU oracle and prints one JSON line
-    with the contract's keys (no GPU needed)."""
+    with the contract's keys (no GPU needed); on a batched workload it samples
+    the batch's first instance."""
     import json
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
-                          "--steps", "2", "--warmup", "1", "--workload", "small_64x48x48"],
+                          "--steps", "2", "--warmup", "1", "--workload", workload],
                          capture_output=True, text=True, timeout=300, cwd=root)
     assert out.returncode == 0, out.stderr[-2000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
