@@ -12,6 +12,9 @@ The paper has no surrogate; its error is always measured against the solver.
 
 ``python -m paper_2303_14119_gb300.surrogate --out DIR`` runs the whole
 pipeline (data, training, evaluation, warm starts) and writes a JSON report.
+The data can also be solved in parts, ``--solve-part I/P`` per call, and the
+part files merged by ``--data A.npz,B.npz,...``; a batch steps every run
+exactly as stepping it alone, so the labels do not depend on the split.
 """
 from __future__ import annotations
 
