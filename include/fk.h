@@ -359,7 +359,8 @@ fk_status fk_batch_scalars(fk_batch *batch, double *sigma, int64_t *step, int64_
  * largest bucket first, keeping the fastest.  The trials advance every grid
  * (bitwise as fk_batch_step would); *steps_taken (may be NULL) receives how
  * many steps they took.  The v1-row tile of each grid is fixed by its shared-
- * memory plan (the most rows for which two CTAs fit on an SM). */
+ * memory plan: the most rows for which two CTAs fit on an SM, or, where each
+ * sign half of the v1 rows fits a half-CTA unit, one such half per tile. */
 fk_status fk_batch_autotune(fk_batch *batch, int32_t steps_per_trial, int64_t *steps_taken);
 
 /* Read (chunk_len[n]) or set the planes per x-chunk of every grid.  Set:
