@@ -7,7 +7,11 @@ does, and the oracle never imports the CUDA package.
 The oracle advances the electron distribution f(x, v1, v2) of the 1D2V
 flashover model (Sec. 2 of arXiv 2303.14119) one explicit upwind step at a
 time, in FP64, with serial sums.  ``build()`` compiles the C source with gcc
-(``-O2 -ffp-contract=off`` so that x86 and Arm hosts give the same bits).
+(``-O2 -ffp-contract=off`` so that x86 and Arm hosts give the same bits)
+twice: the serial checker ``liboracle_fk.so`` and an OpenMP build
+``liboracle_fk_omp.so`` whose loops over x-planes run on several threads and
+whose sums over planes are added in plane order, so that both give the same
+bits (``Oracle(..., threads=n)`` selects the threaded build).
 """
 from __future__ import annotations
 
@@ -21,8 +25,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fk_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle_fk.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_fk_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 HIST_COLS = 8  # step, t, sigma, gamma_pe, gamma_see, gamma_vac, N, Ex(0)
 OK, EINVAL, ENOMEM, ECFL = 0, 1, 2, 4
@@ -34,23 +39,25 @@ EPS0 = 8.8541878128e-12
 
 
 def build(force: bool = False) -> str:
-    """Compile ``fk_oracle.c`` into ``liboracle_fk.so`` if it is stale."""
+    """Compile ``fk_oracle.c`` into ``liboracle_fk.so`` (serial) and
+    ``liboracle_fk_omp.so`` (OpenMP) where stale."""
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-            tmp = _LIB + ".tmp%d" % os.getpid()
-            subprocess.check_call(
-                ["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared",
-                 _SRC, "-o", tmp, "-lm"])
-            os.replace(tmp, _LIB)
+        for lib, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+            if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+                tmp = lib + ".tmp%d" % os.getpid()
+                subprocess.check_call(
+                    ["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared", *extra,
+                     _SRC, "-o", tmp, "-lm"])
+                os.replace(tmp, lib)
     return _LIB
 
 
-def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
+def _load(omp: bool = False):
+    key = bool(omp)
+    if key in _libs:
+        return _libs[key]
     build()
-    lib = C.CDLL(_LIB)
+    lib = C.CDLL(_LIB_OMP if omp else _LIB)
     P, D, I, I64 = C.c_void_p, C.c_double, C.c_int, C.c_int64
     dp = C.POINTER(C.c_double)
     sig = {
@@ -85,13 +92,19 @@ def _load():
         "oracle_set_collisions": (I, [P, D, D, I]),
         "oracle_set_reflection": (I, [P, D]),
         "oracle_set_scheme": (I, [P, I]),
+        "oracle_threads": (I, [I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
+    _libs[key] = lib
     return lib
+
+
+def threads(n: int = 0) -> int:
+    """Set (n >= 1) and return the thread count of the OpenMP build."""
+    return _load(True).oracle_threads(int(n))
 
 
 def _ptr(a: np.ndarray):
@@ -144,8 +157,14 @@ class OracleError(RuntimeError):
 class Oracle:
     """One oracle grid.  Method names follow the C-ABI of the CUDA library."""
 
-    def __init__(self, nx, nv1, nv2, h_max, v1_min, v1_max, v2_min, v2_max, dt=0.0, cfl=0.4):
-        lib = _load()
+    def __init__(self, nx, nv1, nv2, h_max, v1_min, v1_max, v2_min, v2_max, dt=0.0, cfl=0.4,
+                 threads=None):
+        """threads: None for the serial build (the checker); n >= 1 for the
+        OpenMP build on n threads (0: its default count)."""
+        lib = _load(threads is not None)
+        if threads is not None:
+            lib.oracle_threads(int(threads))
+        self.threads = 1 if threads is None else lib.oracle_threads(0)
         self._lib = lib
         self._h = lib.oracle_create(int(nx), int(nv1), int(nv2), float(h_max), float(v1_min),
                                     float(v1_max), float(v2_min), float(v2_max), float(dt),

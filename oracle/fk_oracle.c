@@ -11,6 +11,9 @@
  * It is written to be read against the paper, not to be fast: every face
  * flux is evaluated on its own from its definition (each interior face is
  * evaluated twice), every sum is a serial loop, every number is a double.
+ * Built with -fopenmp, the loops over x-planes run on several threads; a
+ * sum over planes is then taken from per-plane partials added in plane
+ * order, as the serial build does, so both builds give the same bits.
  *
  * One step n -> n+1, in the order of Sec. 2:
  *   1. fields from the current state: the density moment n_k, the normal
@@ -81,6 +84,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* CODATA 2018 values (SI). */
 #define OR_QE 1.602176634e-19    /* elementary charge, C */
@@ -127,6 +133,7 @@ typedef struct {
   int64_t step;
   /* quantities evaluated on the current state */
   double *ne, *Ex, *a1;
+  double *plane_sum; /* per-plane partials of sums over planes */
   double a2;
   double g_pe, g_see, g_emit, g_vac, l_v, n_tot;
   /* ledger */
@@ -273,6 +280,7 @@ static double source(const or_state *s, int k, int i, int j) {
 /* ------------------------------------------------------------------ */
 /* Step 1: density moment and fields of the current state. */
 static void evaluate_fields(or_state *s) {
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < s->nx; k++) {
     double n = 0.0;
     for (int i = 0; i < s->nv1; i++)
@@ -351,13 +359,17 @@ static double flux_v2(const or_state *s, int k, int i, int jface) {
 /* Boundary fluxes of the current state used by the ledger. */
 /* Outflow through the velocity-grid edges (R9) of the state in s->f. */
 static double edge_loss(const or_state *s) {
-  double lv = 0.0;
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < s->nx; k++) {
+    double p = 0.0;
     for (int j = 0; j < s->nv2; j++)
-      lv += (flux_v1(s, k, s->nv1, j) - flux_v1(s, k, 0, j)) * s->dx * s->dv2;
+      p += (flux_v1(s, k, s->nv1, j) - flux_v1(s, k, 0, j)) * s->dx * s->dv2;
     for (int i = 0; i < s->nv1; i++)
-      lv += (flux_v2(s, k, i, s->nv2) - flux_v2(s, k, i, 0)) * s->dx * s->dv1;
+      p += (flux_v2(s, k, i, s->nv2) - flux_v2(s, k, i, 0)) * s->dx * s->dv1;
+    s->plane_sum[k] = p;
   }
+  double lv = 0.0;
+  for (int k = 0; k < s->nx; k++) lv += s->plane_sum[k];
   return lv;
 }
 
@@ -441,7 +453,7 @@ void oracle_destroy(or_state *s) {
   free(s->x); free(s->v1); free(s->v2);
   free(s->f); free(s->f_next); free(s->f_tmp);
   free(s->delta); free(s->g_se); free(s->g_fe); free(s->g_e0);
-  free(s->ne); free(s->Ex); free(s->a1);
+  free(s->ne); free(s->Ex); free(s->a1); free(s->plane_sum);
   free(s->hist);
   free(s);
 }
@@ -478,7 +490,8 @@ or_state *oracle_create(int nx, int nv1, int nv2, double h_max, double v1_min,
   s->ne = (double *)calloc(nx, sizeof(double));
   s->Ex = (double *)calloc(nx, sizeof(double));
   s->a1 = (double *)calloc(nx, sizeof(double));
-  if (!s->x || !s->v1 || !s->v2 || !s->f || !s->f_next || !s->f_tmp || !s->delta || !s->g_se ||
+  s->plane_sum = (double *)calloc(nx, sizeof(double));
+  if (!s->plane_sum || !s->x || !s->v1 || !s->v2 || !s->f || !s->f_next || !s->f_tmp || !s->delta || !s->g_se ||
       !s->g_fe || !s->g_e0 || !s->ne || !s->Ex || !s->a1) {
     oracle_destroy(s);
     return NULL;
@@ -581,6 +594,7 @@ double oracle_courant_sum(const or_state *s) {
 /* Step 3 (R1): every cell of f^n updated with all face fluxes from f^n. */
 static void unsplit_update(or_state *s) {
   const double dt = s->dt;
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < s->nx; k++) {
     const double nu = nu_plane(s, k);
     for (int i = 0; i < s->nv1; i++)
@@ -600,6 +614,7 @@ static void unsplit_update(or_state *s) {
 /* x-advection over h of the state in s->f into out, with the wall inflow of
  * Eq. 15 from s->g_see (the wall fluxes of that state). */
 static void x_pass(or_state *s, double h, double *out) {
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < s->nx; k++)
     for (int i = 0; i < s->nv1; i++)
       for (int j = 0; j < s->nv2; j++) {
@@ -611,6 +626,7 @@ static void x_pass(or_state *s, double h, double *out) {
 /* Velocity step over h of the state in s->f into out, with the fields and
  * collision rates of f^n (s->a1, s->ne). */
 static void v_pass(or_state *s, double h, double *out) {
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < s->nx; k++) {
     const double nu = nu_plane(s, k);
     for (int i = 0; i < s->nv1; i++)
@@ -703,10 +719,15 @@ static int one_step(or_state *s) {
   else
     unsplit_update(s);
   /* ledger: fluxes of state n times dt */
-  double inj = 0.0;
-  for (int k = 0; k < s->nx; k++)
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < s->nx; k++) {
+    double p = 0.0;
     for (int i = 0; i < s->nv1; i++)
-      for (int j = 0; j < s->nv2; j++) inj += source(s, k, i, j) * s->dx * s->dv1 * s->dv2;
+      for (int j = 0; j < s->nv2; j++) p += source(s, k, i, j) * s->dx * s->dv1 * s->dv2;
+    s->plane_sum[k] = p;
+  }
+  double inj = 0.0;
+  for (int k = 0; k < s->nx; k++) inj += s->plane_sum[k];
   s->cum_emit += hn * s->g_emit;
   s->cum_see += hn * s->g_see;
   s->cum_pe += hn * s->g_pe;
@@ -739,6 +760,18 @@ int oracle_step(or_state *s, int64_t n) {
     if (rc != OR_OK) return rc;
   }
   return OR_OK;
+}
+
+/* Threads of the OpenMP build (n >= 1 sets the count); returns the count
+ * the loops over planes use.  The serial build always returns 1. */
+int oracle_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------ */

@@ -878,3 +878,36 @@ def test_strang_ledger_and_charge_close():
     assert dsig / QE == pytest.approx(L["see"] - 0.75 * L["pe"], rel=1e-10)
     with pytest.raises(oracle.OracleError):
         o.set_scheme(3)
+
+
+# ------------------------------------------------------- threaded oracle build
+@pytest.mark.parametrize("scheme", [0, 1, 2])
+def test_openmp_build_equals_serial_build_bitwise(scheme):
+    """The OpenMP build runs the loops over x-planes on several threads and
+    adds per-plane partials in plane order, as the serial build does: both
+    give the same bits for f, sigma, the ledger and the history, for every
+    time scheme, with every term of the step active."""
+    shape = (12, 10, 12)
+    f0 = synth.random_f(shape, 5, 1e3)
+    # Coulomb logarithm scaled so that dt nu_ee is about 2 % on the densest plane
+    probe = Oracle(*shape, 20e-6, -6e7, 6e7, -3e7, 3e7, cfl=0.4)
+    probe.set_state(f0, 0.0)
+    n_max, dt = probe.moments()[0].max(), probe.info()["dt"]
+    ln_lambda = 10.0 * 0.02 / (dt * oracle.nu_ee(n_max, 2.0, 10.0))
+    runs = []
+    for th in (None, 3):
+        o = Oracle(*shape, 20e-6, -6e7, 6e7, -3e7, 3e7, cfl=0.4, threads=th)
+        o.set_fields(-1e6)
+        o.set_see(3.0, 400.0, 1.0, 2.0)
+        o.set_source(1e7, 10e-6, 15e-6, 4.0)
+        o.set_collisions(2.0, ln_lambda, True)
+        o.set_scheme(scheme)
+        o.set_state(f0, 2e-6)
+        o.step(25)
+        runs.append((o.get_f(), o.surface_charge(), o.ledger(), o.history()))
+        assert o.threads == (1 if th is None else 3)
+    (fa, sa, la, ha), (fb, sb, lb, hb) = runs
+    assert np.array_equal(fa, fb)
+    assert sa == sb
+    assert la == lb
+    assert np.array_equal(ha, hb)
