@@ -83,6 +83,16 @@ WORKLOADS = {
     # parameter sweep: 256 independent instances of uneven size, each run
     # 5000 steps, every size and parameter drawn from one seed (sweep_instances)
     "sweep_256": dict(BASE, sweep=256, steps=5000, seed=2023),
+    # a run to saturation (the convergence test of Sec. 2, window 1e4 steps,
+    # tolerance 1e-3) on a grid that resolves the secondaries' hop height:
+    # an 8 um gap in 64 cells (dx = 0.125 um), v1 in +-4e6 m/s (24 cells),
+    # v2 in +-3e7 m/s (32 cells), the source band [5, 7] um at 1e5 A/m^2,
+    # f0 = 0 and sigma0 = 0 (Sec. 2: no electron in the domain at first);
+    # two applied fields above the SEEA threshold of this geometry
+    "saturation_64x24x32": dict(BASE, nx=64, nv1=24, nv2=32, h_max=8e-6, v1_span=4e6,
+                                v2_span=3e7, J=1e5, x_lo=5e-6, x_hi=7e-6, noise_rel=0.0,
+                                Ey=-6e6, Ey_sweep=(-4e6, -6e6), sat_window=10000,
+                                sat_tol=1e-3, steps=120000),
     # the surrogate's training data: 1536 runs of 64 x 48 x 48 (surrogate_runs)
     # stepped as one batch; 750 000 steps reach a 1.25 ns horizon at the
     # smallest gap (h_max = 16 um: dt = 0.4 (h_max / 64) / 6e7 m/s)
