@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the batched parameter sweep (sweep_256) in the default line")
+    ap.add_argument("--sweep-steps", type=int, default=200,
+                    help="timed batch steps of the sweep_256 measurement")
     ap.add_argument("--no-batch", action="store_true",
                     help="step each instance alone instead of as one batch")
     return ap.parse_args()
@@ -173,11 +177,15 @@ def make_grids(fk, w, precision, stream):
     return grids
 
 
-def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=True):
-    """Time `steps` steps of the workload's instances after `warmup` steps.
-    batch: the instances step together (one step-kernel launch and one
-    finalize launch per step for all of them, x-chunks autotuned during the
-    warm-up); else each instance is stepped alone."""
+def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=True,
+             kernel_steps=50):
+    """Time `steps` steps of the workload's instances after `warmup` steps,
+    as users run them: each step a CUDA-graph replay (batch: one step-kernel
+    launch per unit layout and one finalize launch for all instances, x-chunks
+    autotuned before the warm-up; else each instance's own graph).  The
+    step kernel's own launch durations (CUDA events around each launch,
+    direct launches) are taken in a separate pass of `kernel_steps` steps
+    after the timed region, for the roofline."""
     # every grid runs on torch's current stream (a created stream, not the
     # legacy default), so the events below bracket exactly the grids' work
     stream = torch.cuda.current_stream().cuda_stream
@@ -187,19 +195,20 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
         g.set_f(f0)
     b = fk.Batch(grids, stream) if batch else None
     tuned = b.autotune(2) if b is not None else 0
-    for _ in range(warmup):
+
+    def advance(n):
         if b is not None:
-            b.step(1)
+            b.step(n)
         else:
             for g in grids:
-                g.step(1)
+                g.step(n)
+
+    advance(warmup)
     if b is not None:
         assert b.sync() == [fk.FK_OK] * len(grids)
-        b.set_kernel_timing(True)
     else:
         for g in grids:
             g.sync()
-            g.set_kernel_timing(True)
     clocks = ClockSampler(device)
     clocks.start()
     if dist is not None:
@@ -208,10 +217,10 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(steps):
-        if b is not None:
-            b.step(1)
-        else:
+    if b is not None:
+        b.step(steps)
+    else:
+        for _ in range(steps):
             for g in grids:
                 g.step(1)
     e1.record()
@@ -220,6 +229,13 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
         dist.barrier()
     ms = e0.elapsed_time(e1)
     ck = clocks.stop()
+    # the step kernel's launch durations, in a pass of their own
+    if b is not None:
+        b.set_kernel_timing(True)
+    else:
+        for g in grids:
+            g.set_kernel_timing(True)
+    advance(kernel_steps)
     cells = w["nx"] * w["nv1"] * w["nv2"]
     if b is not None:
         launches, kms = b.kernel_timing()
@@ -228,7 +244,10 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
         info = b.info()
         plan = dict(mode="batch", units=info["units"], smem_bytes=info["smem_bytes"],
                     ctas_per_sm=info["ctas_per_sm"], chunk_len=b.chunks(),
-                    n_tiles=grids[0].info()["n_tiles"], autotune_steps=tuned)
+                    n_tiles=grids[0].info()["n_tiles"], autotune_steps=tuned,
+                    timed="CUDA-graph replay (32 steps per graph)",
+                    kernel_times="CUDA events around each step-kernel launch, separate "
+                                 "pass of %d direct-launched steps" % kernel_steps)
         cells_per_launch = cells * len(grids)
         gpu_launches = (info["step_launches"] + 1) * steps  # step kernel(s) + finalize
         b.close()
@@ -241,7 +260,7 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
             g.set_kernel_timing(False)
             g.sync()
         info = grids[0].info()
-        plan = dict(mode="per-instance",
+        plan = dict(mode="per-instance", timed="CUDA-graph replay per instance",
                     **{k: info[k] for k in ("kernel", "n_tiles", "n_chunks", "chunk_len")})
         cells_per_launch = cells
         gpu_launches = 2 * steps * len(grids)
@@ -278,14 +297,19 @@ def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True):
         else:
             g.set_f(f_host)
     b = fk.Batch(grids, stream) if batch else None
+    ne_all = np.empty(nx * len(grids))
+    ex_all = np.empty(nx * len(grids))
     for _ in range(steps):
         if b is not None:
+            # one step of every instance, then every instance's n_e, E_x,
+            # sigma and wall fluxes read back with one wait
             b.step(1)
-        for g in grids:
-            if b is None:
+            b.moments(ne_all, ex_all)
+        else:
+            for g in grids:
                 g.step(1)
-            fk.fk_moments(g.h, nx, ne, ex)
-            g.surface_charge()
+                fk.fk_moments(g.h, nx, ne, ex)
+                g.surface_charge()
     for g in grids:
         if f32:
             g.get_f32(out_f)
@@ -300,19 +324,19 @@ def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True):
     cells = w["nx"] * w["nv1"] * w["nv2"]
     n = len(grids)
     h2d = n * f_host.nbytes / steps
-    d2h = n * (2 * nx * 8 + 2 * 8 + 8) + n * out_f.nbytes / steps
+    d2h = n * (2 * nx * 8 + 3 * 8) + n * out_f.nbytes / steps
     return dict(value=n * cells * steps / dt, unit=UNIT, h2d_bytes_per_step=int(h2d),
                 d2h_bytes_per_step=int(d2h), steps=steps)
 
 
-def cpu_baseline(w, seconds=15.0):
-    """The FP64 oracle as it stands, single thread, on a bounded sample: as
-    many whole steps of one field instance of the workload as fit in about
-    `seconds` (at least one)."""
+def oracle_rate(w, threads, seconds):
+    """Cell-updates/s of the FP64 oracle on `threads` host threads (None: the
+    serial checker build), over as many whole steps of one field instance
+    of the workload as fit in about `seconds` (at least one)."""
     import oracle
     shape = (w["nx"], w["nv1"], w["nv2"])
     o = oracle.Oracle(*shape, w["h_max"], -w["v1_span"], w["v1_span"], -w["v2_span"],
-                      w["v2_span"], cfl=w["cfl"])
+                      w["v2_span"], cfl=w["cfl"], threads=threads)
     o.set_fields(w["Ey"])
     o.set_see(w["delta_max"], w["A_max"], w["k_s"], w["T_se"])
     o.set_source(w["J"], w["x_lo"], w["x_hi"], w["T_fe"])
@@ -324,12 +348,27 @@ def cpu_baseline(w, seconds=15.0):
         o.step(1)
         t += time.perf_counter() - t0
         n += 1
-        if n * cells > 2e9:
+        if n * cells > 4e9:
             break
+    used = o.threads
     o.close()
-    return {"value": n * cells / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d step(s) of one %dx%dx%d field instance (E_y=%g V/m), FP64, 1 thread"
-                      % (n, *shape, w["Ey"])}
+    return n * cells / t, n, used
+
+
+def cpu_baseline(w, seconds=10.0):
+    """The FP64 oracle as it stands on the host: its OpenMP build on every
+    host core (loops over x-planes threaded, sums in plane order) and its
+    serial build on one core, each on a bounded sample of the workload."""
+    shape = (w["nx"], w["nv1"], w["nv2"])
+    cores = os.cpu_count() or 1
+    v_all, n_all, used = oracle_rate(w, cores, seconds)
+    v_one, n_one, _ = oracle_rate(w, None, seconds)
+    return {"value": v_all, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": "%d step(s) of one %dx%dx%d field instance (E_y=%g V/m), FP64, %d threads "
+                      "(OpenMP over x-planes) of %d host cores"
+                      % (n_all, *shape, w["Ey"], used, cores),
+            "one_core": {"value": v_one, "unit": UNIT, "cores": 1,
+                         "sample": "%d step(s), serial build" % n_one}}
 
 
 # GB300 FP64 FMA peak derived from unit counts and clock: 152 SMs x 2 FP64
@@ -417,6 +456,16 @@ def run_ours(args):
         e2e = e2e_arm(fk, torch, w, prec, f0, args.e2e_steps, batch=not args.no_batch)
         e2e["value"] = reduce_over_ranks(e2e["value"], dist, "sum")
         line["e2e"] = e2e
+    if not args.no_sweep:
+        # the second half of the metric: batched instances/hr of the sweep
+        # against the same instances stepped one after another
+        sw = measure_sweep(fk, torch, "sweep_256", args.precision, args.sweep_steps,
+                           max(3, min(args.warmup, 10)), dist, local, world)
+        line["batched_sweep"] = {k: sw[k] for k in (
+            "metric", "value", "unit", "ms_per_step", "steps", "config", "cell_updates_per_s",
+            "sequential", "speedup_vs_sequential", "equal_accuracy", "autotune", "roofline",
+            "clocks")}
+        line["gpu_launches_batched_sweep"] = sw["gpu_launches"]
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
@@ -440,30 +489,19 @@ def make_sweep_grids(fk, instances, precision, stream):
     return grids
 
 
-def run_sweep(args):
+def measure_sweep(fk, torch, workload, precision, steps, warmup, dist, local, world=1):
     """Batched workload: every instance of the parameter sweep
     (synth.sweep_instances) or of the surrogate's training runs
     (synth.surrogate_runs) stepped as one batch (x-chunks autotuned per size
     bucket), against the same instances stepped one after another with
     fk_step (each instance's steps as CUDA-graph replays).  Both arms give
     bitwise identical states; the metric is instances per hour at the
-    workload's steps per instance, from the timed per-step rate."""
-    rank, world, local = dist_env()
-    import torch
-    from paper_2303_14119_gb300 import fk
-    fk.load()
-    torch.cuda.set_device(local)
-    torch.cuda.set_stream(torch.cuda.Stream())
-    dist = None
-    if world > 1:
-        import torch.distributed as td
-        td.init_process_group("gloo")
-        dist = td
+    workload's steps per instance, from the timed per-step rate.  Returns
+    the JSON object of the measurement."""
     stream = torch.cuda.current_stream().cuda_stream
-    w = synth.WORKLOADS[args.workload]
+    w = synth.WORKLOADS[workload]
     ins = synth.batch_instances(w)
-    prec = fk.FK_F32 if args.precision == "f32" else fk.FK_F64
-    steps = args.steps
+    prec = fk.FK_F32 if precision == "f32" else fk.FK_F64
     grids = make_sweep_grids(fk, ins, prec, stream)
     twins = make_sweep_grids(fk, ins, prec, stream)
     cells = float(sum(p["nx"] * p["nv1"] * p["nv2"] for p in ins))
@@ -471,14 +509,14 @@ def run_sweep(args):
     t0 = time.perf_counter()
     tuned = b.autotune(2)
     tune_s = time.perf_counter() - t0
-    b.step(args.warmup)
+    b.step(warmup)
     # kernel durations for the roofline (direct launches with event pairs)
     kt_steps = 8
     b.set_kernel_timing(True)
     b.step(kt_steps)
     launches, kms = b.kernel_timing()
     b.set_kernel_timing(False)
-    pre = tuned + args.warmup + kt_steps
+    pre = tuned + warmup + kt_steps
     assert b.sync() == [fk.FK_OK] * len(ins)
     # batched arm: graph replay
     clocks = ClockSampler(local)
@@ -526,20 +564,20 @@ def run_sweep(args):
     if "sweep" in w:
         workload_text = ("%s: %d instances, nx 128-512, nv1 = nv2 64-192, E_y log-uniform "
                          "3e5-5e6 V/m, delta_max 2-4, A_max 250-600 eV, T_se 1-5 eV, one seed "
-                         "(%d); f0 = 0" % (args.workload, len(ins), w["seed"]))
+                         "(%d); f0 = 0" % (workload, len(ins), w["seed"]))
     else:
         workload_text = ("%s: %d surrogate training runs of 64 x 48 x 48, E_y log-uniform "
                          "3e5-5e6 V/m, delta_max 2-4, A_max 250-600 eV, T_se 1-5 eV, J "
                          "log-uniform 1e5-1e7 A/m^2, h_max 16-24 um, one seed (%d); f0 = 0; "
                          "%d steps reach the 1.25 ns horizon at the smallest gap"
-                         % (args.workload, len(ins), w["seed"], per_inst))
+                         % (workload, len(ins), w["seed"], per_inst))
     ms_step_b = ms_b / steps
     ms_step_s = ms_s / steps
     value = world * len(ins) * 3600.0 / (ms_step_b * per_inst / 1e3)
     seq = world * len(ins) * 3600.0 / (ms_step_s * per_inst / 1e3)
     peak, peak_kind = measured_peaks()
     res = dict(launches=launches, kernel_ms=kms, cells_per_launch=cells)
-    roof = roofline(res, args.precision, peak, peak_kind)
+    roof = roofline(res, precision, peak, peak_kind)
     if roof is not None:
         if info["step_launches"] == 1:
             roof["kernel"] = "batched fused upwind step (all %d instances per launch)" % len(ins)
@@ -548,11 +586,11 @@ def run_sweep(args):
                               "of whole-CTA units, one of half-CTA units, timed together)"
                               % len(ins))
         roof["traffic"] = None
-    line = {
+    return {
         "metric": "batched instances/hr (%d steps per instance)" % per_inst, "value": value,
-        "unit": "instances/hr", "n_gpus": world, "steps": steps, "warmup": args.warmup,
+        "unit": "instances/hr", "n_gpus": world, "steps": steps, "warmup": warmup,
         "ms_per_step": ms_step_b, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "vs_baseline": None, "dtype": precision, "data": "synthetic",
         "config": {"workload": workload_text,
                    "cells_all_instances": cells, "steps_per_instance": per_inst,
                    "rate": "instances/hr from the timed per-step time x %d steps" % per_inst,
@@ -573,6 +611,23 @@ def run_sweep(args):
         "gpu_launches": (info["step_launches"] + 1) * steps,  # step kernel(s) + finalize
         "clocks": ck,
     }
+
+
+def run_sweep(args):
+    """A batched workload as the benchmark's own line (--workload)."""
+    rank, world, local = dist_env()
+    import torch
+    from paper_2303_14119_gb300 import fk
+    fk.load()
+    torch.cuda.set_device(local)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("gloo")
+        dist = td
+    line = measure_sweep(fk, torch, args.workload, args.precision, args.steps, args.warmup,
+                         dist, local, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -581,7 +636,9 @@ def run_sweep(args):
 
 def run_reference(args):
     """The oracle arm: each step is one FP64 oracle step of one field
-    instance of the workload (a bounded sample), on one host thread."""
+    instance of the workload (a bounded sample), on every host core (the
+    oracle's OpenMP build: loops over x-planes threaded, sums in plane
+    order, bitwise equal to its serial build)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -590,8 +647,9 @@ def run_reference(args):
     if "sweep" in w or "runs" in w:  # the sampled instance: the batch's first
         w = synth.batch_instances(w)[0]
     shape = (w["nx"], w["nv1"], w["nv2"])
+    cores = os.cpu_count() or 1
     o = oracle.Oracle(*shape, w["h_max"], -w["v1_span"], w["v1_span"], -w["v2_span"],
-                      w["v2_span"], cfl=w["cfl"])
+                      w["v2_span"], cfl=w["cfl"], threads=cores)
     o.set_fields(w["Ey"])
     o.set_see(w["delta_max"], w["A_max"], w["k_s"], w["T_se"])
     o.set_source(w["J"], w["x_lo"], w["x_hi"], w["T_fe"])
@@ -604,13 +662,16 @@ def run_reference(args):
     t = time.perf_counter() - t0
     cells = int(np.prod(shape))
     value = cells * steps / t
-    sample = "%d FP64 oracle step(s) of one %dx%dx%d field instance, 1 thread" % (steps, *shape)
+    used = o.threads
+    o.close()
+    sample = ("%d FP64 oracle step(s) of one %dx%dx%d field instance, %d threads (OpenMP over "
+              "x-planes) of %d host cores" % (steps, *shape, used, cores))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": warm, "ms_per_step": t / steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "cells_per_instance": cells},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)

@@ -292,6 +292,9 @@ fk_status fk_kernel_timing(fk_grid *grid, int64_t *launches, double *total_ms);
  * sharing one context) race on it and must be ordered by the caller.
  * The first call on each device looks up the array's device address with
  * that device current; make that first call before any stream capture.
+ * The address is kept for the life of the process: after a reset of the
+ * device's primary context (cudaDeviceReset) the entry point must not be
+ * called again in that process.
  * Errors: FK_EINVAL (NULL pointer, non-positive size or spacing, nx above
  * the limit), FK_ECUDA (no current device, lookup or launch failure). */
 #define FK_NOALLOC_MAX_PARTIALS 131072
@@ -351,6 +354,16 @@ fk_status fk_batch_sync(fk_batch *batch, int32_t *status);
  * array may be NULL.  Frozen grids report their last valid state. */
 fk_status fk_batch_scalars(fk_batch *batch, double *sigma, int64_t *step, int64_t *sat_step,
                            int32_t *status);
+
+/* Moments of every grid's current state after the batch's enqueued work,
+ * read with one synchronisation for all grids (the batch form of
+ * fk_moments and fk_surface_charge): sigma[i] (C/m^2, Eq. 18),
+ * gamma_pe[i] and gamma_see[i] (m^-2 s^-1, Eqs. 13-14), and n_e and E_x at
+ * the cell centres of every grid in batch order, grid i's nx_i values
+ * starting at offset nx_0 + ... + nx_{i-1} of n_e and Ex.  Any pointer may
+ * be NULL.  Frozen grids report their last valid state. */
+fk_status fk_batch_moments(fk_batch *batch, double *sigma, double *gamma_pe, double *gamma_see,
+                           double *n_e, double *Ex);
 
 /* Autotuner: picks the x-chunk length (planes per work unit) of every size
  * bucket of the batch -- grids grouped by plane size and nx, each a power of

@@ -503,6 +503,38 @@ fk_status fk_batch_scalars(fk_batch* b, double* sigma, int64_t* step, int64_t* s
   return FK_OK;
 }
 
+fk_status fk_batch_moments(fk_batch* b, double* sigma, double* gamma_pe, double* gamma_see,
+                           double* n_e, double* Ex) {
+  if (!b) return FK_EINVAL;
+  BK_CUDA(b, cudaSetDevice(b->dev));
+  // every copy lands in its grid's pinned buffer (DevState, n_e, E_x), all
+  // enqueued on the batch's stream; one wait for all of them
+  for (int i = 0; i < b->n; i++) {
+    fk_grid* g = b->grids[i];
+    DevState* hst = static_cast<DevState*>(g->h_stage);
+    double* hv = reinterpret_cast<double*>(hst + 1);
+    const size_t vb = (size_t)g->nx * sizeof(double);
+    BK_CUDA(b, cudaMemcpyAsync(hst, g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
+    if (n_e) BK_CUDA(b, cudaMemcpyAsync(hv, g->d_ne, vb, cudaMemcpyDeviceToHost, b->stream));
+    if (Ex) BK_CUDA(b, cudaMemcpyAsync(hv + g->nx, g->d_Ex, vb, cudaMemcpyDeviceToHost, b->stream));
+  }
+  BK_CUDA(b, cudaStreamSynchronize(b->stream));
+  size_t off = 0;
+  for (int i = 0; i < b->n; i++) {
+    fk_grid* g = b->grids[i];
+    const DevState* hst = static_cast<const DevState*>(g->h_stage);
+    const double* hv = reinterpret_cast<const double*>(hst + 1);
+    const size_t vb = (size_t)g->nx * sizeof(double);
+    if (sigma) sigma[i] = hst->sigma;
+    if (gamma_pe) gamma_pe[i] = hst->g_pe;
+    if (gamma_see) gamma_see[i] = hst->g_see;
+    if (n_e) memcpy(n_e + off, hv, vb);
+    if (Ex) memcpy(Ex + off, hv + g->nx, vb);
+    off += g->nx;
+  }
+  return FK_OK;
+}
+
 fk_status fk_batch_get_chunks(const fk_batch* b, int32_t* chunk_len) {
   if (!b || !chunk_len) return FK_EINVAL;
   for (int i = 0; i < b->n; i++) chunk_len[i] = b->chunk_len[i];

@@ -255,12 +255,28 @@ __device__ __forceinline__ float update_cell<float>(float f, float fx, float fv,
   return f + inc;
 }
 
+// Per-thread accumulator of the density moment: FP64 grids add in FP64;
+// FP32 grids keep a compensated FP32 sum (TwoSum: the running sum and its
+// rounding errors), converted to FP64 once per thread.
 template <typename T>
-struct Acc;  // per-thread accumulator type of the density moment
+struct DensityAcc;
 template <>
-struct Acc<double> { using type = double; };
+struct DensityAcc<double> {
+  double s = 0.0;
+  __device__ void add(double x) { s += x; }
+  __device__ double value() const { return s; }
+};
 template <>
-struct Acc<float> { using type = float; };
+struct DensityAcc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ double value() const { return (double)s + (double)c; }
+};
 
 template <typename T>
 __global__ void __launch_bounds__(kStepThreads)
@@ -301,7 +317,7 @@ step_direct_kernel(StepArgs a, int mode) {
   const T ca = coll ? (sizeof(T) == 8 ? (T)a.bgk[k] : (T)a.bgk32[k]) : (T)0;
   const T cs = coll ? (sizeof(T) == 8 ? (T)a.bgk[nx + k] : (T)a.bgk32[nx + k]) : (T)0;
   const int ncell = (i1 - i0) * nv2;
-  typename Acc<T>::type s_n = 0;
+  DensityAcc<T> s_n;
   double s_lv = 0.0, s_pe = 0.0, s_see = 0.0, s_vac = 0.0;
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
     const int i = i0 + c / nv2;
@@ -344,7 +360,7 @@ step_direct_kernel(StepArgs a, int mode) {
       if ((c1 > (T)0 && i == nv1 - 1) || (c1 < (T)0 && i == 0)) s_lv += (double)a1 * (double)f;
       if ((c2 > (T)0 && j == nv2 - 1) || (c2 < (T)0 && j == 0)) s_lv += (double)a2 * (double)f;
     }
-    s_n += fn;
+    s_n.add(fn);
     if (k == 0 && dir < 0) {
       const double g = -a.tab.v1[i] * (double)fn;  // Eq. 13 without dv1 dv2
       s_pe += g;
@@ -355,7 +371,7 @@ step_direct_kernel(StepArgs a, int mode) {
   // the velocity pass (and the last pass of a Strang step) writes the
   // partial sums (uniform)
   if (xpass && !xlast) return;
-  const double n_tot = block_sum<kStepThreads>((double)s_n, sh);
+  const double n_tot = block_sum<kStepThreads>(s_n.value(), sh);
   s_lv = block_sum<kStepThreads>(s_lv, sh);
   if (k == 0) {
     s_pe = block_sum<kStepThreads>(s_pe, sh);

@@ -57,6 +57,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// Order this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) accesses to the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
@@ -159,11 +164,13 @@ __host__ __device__ constexpr size_t tail_bytes(int pitch) {
          tail_main_bytes<T>(pitch) + tail_bgk_bytes<T>(pitch) + 16;
 }
 
-// Exact split of a double x >= 2^-126 into hi + lo floats: hi keeps the top
-// 24 significant bits (truncated), lo the remaining 29 rounded to 24 bits,
-// so hi + lo = x to about 2^-47 relative.  Integer and FP32 operations only:
-// none of this runs on GB300's narrow FP64 pipe.  Smaller magnitudes (and
-// zero) give 0 + 0, negligible in a sum of phase-space densities.
+// Exact split of a double x with 2^-126 <= |x| < 2^128 into hi + lo floats:
+// hi keeps the top 24 significant bits (truncated), lo the remaining 29
+// rounded to 24 bits, so hi + lo = x to about 2^-47 relative.  Integer and
+// FP32 operations only: none of this runs on GB300's narrow FP64 pipe.
+// Smaller magnitudes (and zero) give 0 + 0, negligible in a sum of
+// phase-space densities; |x| >= 2^128, infinities and NaN give a NaN hi, so
+// the sum they enter is flagged as non-finite.
 __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned int h32 = (unsigned int)(b >> 32);
@@ -171,7 +178,8 @@ __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
   const unsigned int sign = h32 & 0x80000000u;
   const unsigned int m23 = (unsigned int)(b >> 29) & 0x7FFFFFu;
   const bool ok = E >= 897 && E <= 1150;  // hi is a normal float
-  hi = __int_as_float(ok ? (sign | ((unsigned int)(E - 896) << 23) | m23) : 0u);
+  const unsigned int out_of_range = E > 1150 ? 0x7FC00000u : 0u;  // quiet NaN
+  hi = __int_as_float(ok ? (sign | ((unsigned int)(E - 896) << 23) | m23) : out_of_range);
   const unsigned int r29 = (unsigned int)b & 0x1FFFFFFFu;
   // scale 2^(E-1075) as a float: exponent field E - 948 (0 below 2^-74)
   const float scale = __int_as_float(E >= 949 ? ((unsigned int)(E - 948) << 23) : 0u);
@@ -184,6 +192,35 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
   const float bp = t - s;
   c += (s - (t - bp)) + (x - bp);
   s = t;
+}
+// Exact float -> double with integer operations (no FP64 instruction):
+// normal floats map exactly; zero and subnormals (|f| < 2^-126) give a
+// signed zero; infinities and NaN stay infinities and NaN.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int sign = u & 0x80000000u;
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned int m = u & 0x7FFFFFu;
+  const unsigned int ehi = e == 255u ? 0x7FF00000u : ((e + 896u) << 20);
+  const unsigned int hi = e == 0u ? sign : (sign | ehi | (m >> 3));
+  const unsigned int lo = e == 0u ? 0u : (m << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+// The sum of a (hi, lo) pair of floats as a double: one FP64 add.
+__device__ __forceinline__ double pair_to_double(float2 p) {
+  return f2d_exact(p.x) + f2d_exact(p.y);
+}
+// Fold the (hi, lo) pairs of the lanes of a warp into lane 0 in FP32:
+// TwoSum on hi, low parts and rounding errors added in lo.
+__device__ __forceinline__ float2 warp_pair_sum(float hi, float lo) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_down_sync(0xffffffffu, hi, o);
+    const float ol = __shfl_down_sync(0xffffffffu, lo, o);
+    float c = 0.f;
+    two_sum_acc(hi, c, oh);
+    lo += ol + c;
+  }
+  return make_float2(hi, lo);
 }
 
 // Wall (x = 0, v1 < 0: Eqs. 12-14) or vacuum (x = h_max, v1 > 0) sums of
@@ -352,6 +389,9 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         float4* z = reinterpret_cast<float4*>(stage + (size_t)zrow * pitch);
         const int n16 = pitch * (int)sizeof(T) / 16;
         for (int c = lane; c < n16; c += 32) z[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        // a later bulk copy (async proxy) may land on these bytes when c_1
+        // changes sign: order the zero stores (generic proxy) before it
+        fence_proxy_async_smem();
       }
       if (sizeof(T) == 8) {
         // FP64 diagonal of the convex update per tile row, once per plane
@@ -383,12 +423,14 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
     struct Gathered {
       int k;       // plane (-1: the prime item, no sums)
       T lvt;       // this lane's share of the velocity-edge outflow
-      double ws[kWs];  // lane w < NW: warp w's sums (all four on a wall plane)
+      float2 wn;   // lane w < NW: warp w's density sum as a (hi, lo) pair
+      double ws[kWs];  // lane w < NW: warp w's wall and vacuum sums (slots 1-3)
     };
     auto gather = [&](int q) -> Gathered {
       Gathered g;
       g.k = -1;
       g.lvt = (T)0;
+      g.wn = make_float2(0.f, 0.f);
 #pragma unroll
       for (int i = 0; i < kWs; i++) g.ws[i] = 0.0;
       if (prime && q == 0) return g;
@@ -412,7 +454,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         for (int r = lane; r < rows; r += 32) g.lvt += a2t * sb[(size_t)(r + rb) * pitch + nv2 - 1];
       if (lane < NW) {
         const double* ws = wsum + (st * kWarps + lane) * kWs;
-        g.ws[0] = ws[0];
+        g.wn = *reinterpret_cast<const float2*>(ws);
         if (k == 0 || k == nx - 1) {
 #pragma unroll
           for (int i = 1; i < kWs; i++) g.ws[i] = ws[i];
@@ -424,20 +466,29 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
     auto finish = [&](const Gathered& g) {
       if (g.k < 0) return;
       const int k = g.k;
-      const double lv = (double)warp_sum(g.lvt);
+      const T lvs = warp_sum(g.lvt);
       double sum[kWs] = {0.0, 0.0, 0.0, 0.0};
       const bool wall = k == 0 || k == nx - 1;
+      // the warps' density pairs in warp order, in FP32 (TwoSum)
+      float nh = 0.f, nl = 0.f;
 #pragma unroll
       for (int w = 0; w < NW; w++) {
-        sum[0] += __shfl_sync(0xffffffffu, g.ws[0], w);
+        const float h = __shfl_sync(0xffffffffu, g.wn.x, w);
+        const float l = __shfl_sync(0xffffffffu, g.wn.y, w);
+        float c = 0.f;
+        two_sum_acc(nh, c, h);
+        nl += l + c;
         if (wall) {
 #pragma unroll
           for (int i = 1; i < kWs; i++) sum[i] += __shfl_sync(0xffffffffu, g.ws[i], w);
         }
       }
       if (lane == 0) {
-        a.part.n[(size_t)k * nt + t] = sum[0];
-        a.part.lv[(size_t)k * nt + t] = lv;
+        a.part.n[(size_t)k * nt + t] = pair_to_double(make_float2(nh, nl));
+        if constexpr (sizeof(T) == 4)
+          a.part.lv[(size_t)k * nt + t] = f2d_exact((float)lvs);
+        else
+          a.part.lv[(size_t)k * nt + t] = (double)lvs;
         if (k == 0) {
           a.part.pe[t] = sum[1];
           a.part.see[t] = sum[2];
@@ -564,8 +615,9 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       // row read is always one that was copied or zero-filled
       const int nboff = c1f > 0.f ? -pitch : (c1f < 0.f ? pitch : 0);
       const double* dg = dgl + st * kMaxTileRows;
-      T sum_n = (T)0;
-      float sh_ = 0.f, sc_ = 0.f, sl_ = 0.f;  // FP64 grids: compensated FP32 sum
+      // density of f^{n+1}: a compensated FP32 sum (hi sh_, error sc_;
+      // FP64 grids add the low parts of their values in sl_)
+      float sh_ = 0.f, sc_ = 0.f, sl_ = 0.f;
       T* oplane = fout + (size_t)k * plane;
 #pragma unroll
       for (int m = 0; m < M; m++) {
@@ -626,35 +678,26 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
           if (PADDED && (so % pitch) + e >= nv2) fn = (T)0;  // row padding stays zero
           out.e[e] = fn;
           xr[m][e] = f;  // x-upwind value for the next plane is f^n here
-          if (sizeof(T) == 4) {
-            sum_n += fn;
-          } else {
+          if constexpr (sizeof(T) == 8) {
             float h, l;
             split_double((double)fn, h, l);
             two_sum_acc(sh_, sc_, h);
             sl_ += l;
           }
         }
+        if constexpr (sizeof(T) == 4)  // the vector's four values pairwise
+          two_sum_acc(sh_, sc_, ((float)out.e[0] + (float)out.e[1]) +
+                                     ((float)out.e[2] + (float)out.e[3]));
         __stcs(reinterpret_cast<float4*>(oplane + so + gbase),
                *reinterpret_cast<const float4*>(&out));
       }
-      // warp sum of this plane's f^{n+1} (an FP32 grid sums its 32 lanes in
-      // FP32; everything above a warp is FP64)
+      // warp sum of this plane's f^{n+1}: the lanes' (hi, error) pairs folded
+      // in FP32 with TwoSum; the producer folds the warps' pairs the same
+      // way and converts once per plane
       double* wsl = wsum + (st * kWarps + warp) * kWs;
-      if (sizeof(T) == 4) {
-        const T ws = warp_sum(sum_n);
-        if (lane == 0) wsl[0] = (double)ws;
-      } else {
-        // fold the lanes' (hi, error) pairs in FP32 with TwoSum, convert once
-        float lo = sc_ + sl_;
-        for (int o = 16; o > 0; o >>= 1) {
-          const float oh = __shfl_down_sync(0xffffffffu, sh_, o);
-          const float ol = __shfl_down_sync(0xffffffffu, lo, o);
-          float c = 0.f;
-          two_sum_acc(sh_, c, oh);
-          lo += ol + c;
-        }
-        if (lane == 0) wsl[0] = (double)sh_ + (double)lo;
+      {
+        const float2 ws = warp_pair_sum(sh_, sc_ + sl_);
+        if (lane == 0) *reinterpret_cast<float2*>(wsl) = ws;
       }
       const bool wall = k == 0 && dir < 0, vout = k == nx - 1 && dir > 0;
       if (wall || vout) {  // uniform over the block

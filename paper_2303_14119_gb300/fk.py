@@ -107,6 +107,7 @@ def load(build_if_missing: bool = True):
         "fk_batch_set_chunks": [P, C.POINTER(C.c_int32)],
         "fk_batch_info": [P, dp],
         "fk_batch_scalars": [P, dp, i64p, i64p, C.POINTER(C.c_int32)],
+        "fk_batch_moments": [P, dp, dp, dp, dp, dp],
         "fk_batch_set_kernel_timing": [P, I],
         "fk_batch_kernel_timing": [P, i64p, dp],
         "fk_gemm_bf16_tn": [P, I64, P, I64, P, I64, C.c_int32, C.c_int32, C.c_int32, P, P],
@@ -619,6 +620,20 @@ def fk_batch_scalars(b, n):
     return sig, st, sat, status
 
 
+def fk_batch_moments(b, n, n_e=None, Ex=None, sigma=None, gamma_pe=None, gamma_see=None):
+    """Every grid's sigma, Gamma_pe, Gamma_see (arrays of n) and n_e, E_x
+    (concatenated in batch order) with one synchronisation; output arrays
+    may be passed in (FP64, C-contiguous) to avoid allocation."""
+    sigma = np.empty(n) if sigma is None else sigma
+    gamma_pe = np.empty(n) if gamma_pe is None else gamma_pe
+    gamma_see = np.empty(n) if gamma_see is None else gamma_see
+    _bcheck(load().fk_batch_moments(b, _dp(sigma), _dp(gamma_pe), _dp(gamma_see),
+                                    _dp(n_e) if n_e is not None else None,
+                                    _dp(Ex) if Ex is not None else None),
+            "fk_batch_moments", b)
+    return sigma, gamma_pe, gamma_see, n_e, Ex
+
+
 def fk_batch_autotune(b, steps_per_trial=2):
     taken = C.c_int64()
     _bcheck(load().fk_batch_autotune(b, int(steps_per_trial), C.byref(taken)),
@@ -695,6 +710,11 @@ class Batch:
 
     def scalars(self):
         return fk_batch_scalars(self.h, len(self.grids))
+
+    def moments(self, n_e=None, Ex=None, sigma=None, gamma_pe=None, gamma_see=None):
+        """(sigma, gamma_pe, gamma_see, n_e, Ex) of every grid, one wait;
+        n_e and Ex are filled only when given (length sum of nx)."""
+        return fk_batch_moments(self.h, len(self.grids), n_e, Ex, sigma, gamma_pe, gamma_see)
 
     def chunks(self):
         return fk_batch_get_chunks(self.h, len(self.grids))

@@ -237,3 +237,29 @@ def test_batch_scalars_equal_the_grid_getters():
             assert sig[q] == g.surface_charge()
             assert (step[q], sat[q]) == g.step_count()
             assert status[q] == fk.FK_OK
+
+
+@pytest.mark.parametrize("prec", [fk.FK_F32, fk.FK_F64])
+def test_batch_moments_one_wait_equals_each_grids_getters(prec):
+    """fk_batch_moments reads every grid's sigma, wall fluxes, n_e and E_x
+    with one wait; the values equal each grid's own getters bit for bit."""
+    a, _ = twins(prec)
+    with fk.Batch(a) as b:
+        b.step(5)
+        nxs = [g.shape[0] for g in a]
+        n_e = np.full(sum(nxs), np.nan)
+        ex = np.full(sum(nxs), np.nan)
+        sig, pe, see, _, _ = b.moments(n_e, ex)
+        off = 0
+        for q, g in enumerate(a):
+            ne_g, ex_g, pe_g, see_g = g.moments()
+            nx = g.shape[0]
+            assert np.array_equal(n_e[off:off + nx], ne_g)
+            assert np.array_equal(ex[off:off + nx], ex_g)
+            assert sig[q] == g.surface_charge() and pe[q] == pe_g and see[q] == see_g
+            off += nx
+        # scalars only
+        sig2, _, _, _, _ = b.moments()
+        assert np.array_equal(sig2, sig)
+    for g in a:
+        g.close()

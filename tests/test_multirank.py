@@ -73,5 +73,5 @@ def test_reference_arm_prints_its_json_line(workload):
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
                 "higher_is_better", "cpu_baseline", "e2e", "config"):
         assert key in line, key
-    assert line["value"] > 0 and line["cpu_baseline"]["cores"] == 1
+    assert line["value"] > 0 and line["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
     assert line["e2e"]["h2d_bytes_per_step"] == 0
