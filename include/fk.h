@@ -25,9 +25,23 @@
  *    (copies complete before the call returns).
  *  - Work is ordered on the grid's CUDA stream.  fk_step only enqueues;
  *    the getters synchronise that stream.  Errors detected on the device
- *    (CFL violation, non-finite sums, a pipeline wait that ran out) are
- *    sticky: the step that meets one leaves f at the last valid state, later
- *    steps do nothing, and the next getter or fk_sync returns the status.
+ *    (CFL violation, non-finite sums, a pipeline wait that ran out, negative
+ *    f) are sticky: the step that meets one leaves f at the last valid
+ *    state, later steps do nothing, and the next getter or fk_sync returns
+ *    the status.  Where f is checked for negative values: every cell of a
+ *    state set with fk_set_f / fk_set_f32 (the call returns FK_ENEGATIVE),
+ *    every cell a direct-load or split-scheme pass writes, and the wall and
+ *    vacuum planes of every streaming step.  The interior of a
+ *    streaming step is not checked per cell: with f >= 0 and the Courant sum
+ *    (checked every step) at most 1, its update is a sum of non-negative
+ *    terms.
+ *  - Failure-detection test knobs (off by default, read at fk_create_grid):
+ *    FK_TEST_WAIT_CYCLES=<n> sets the limit of the streaming kernel's bounded
+ *    waits to n cycles (default about 2 s); FK_TEST_WITHHOLD_COPY=<q> makes
+ *    the work unit of tile 0, chunk 0 skip the plane copy of its pipeline
+ *    item q, so that the waits on it run out and the step reports
+ *    FK_ETIMEOUT (every copy that was issued still lands before the kernel
+ *    leaves).
  *  - Calls on one grid must not run concurrently from several threads.
  *    Distinct grids are independent.
  */
@@ -53,7 +67,9 @@ typedef enum {
                       upwind step would not keep f >= 0 */
   FK_ENUMERIC = 5, /* a moment or flux became NaN or infinite */
   FK_ETIMEOUT = 6, /* a bounded wait inside a kernel ran out */
-  FK_ESTATE = 7    /* call not valid in the grid's current state */
+  FK_ESTATE = 7,   /* call not valid in the grid's current state */
+  FK_ENEGATIVE = 8 /* f has a negative value: a state set with one, or a
+                      step that produced one beyond rounding */
 } fk_status;
 
 typedef enum {

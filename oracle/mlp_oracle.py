@@ -109,3 +109,17 @@ class MLPOracle:
         grads.reverse()
         flat = np.concatenate([np.concatenate([dW.ravel(), db]) for dW, db in grads])
         return loss, flat
+
+
+def adam_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One step of Adam (Kingma and Ba, "Adam: A method for stochastic
+    optimization", ICLR 2015, Algorithm 1) in FP64: the moment estimates
+    m <- beta1 m + (1 - beta1) g and v <- beta2 v + (1 - beta2) g^2, their
+    bias corrections by 1 - beta^t, and p <- p - lr mhat / (sqrt(vhat) + eps).
+    t counts steps from 1.  Returns (p, m, v) as new arrays."""
+    p, g, m, v = (np.asarray(a, dtype=np.float64) for a in (p, g, m, v))
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m, v

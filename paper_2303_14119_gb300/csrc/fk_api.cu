@@ -56,6 +56,8 @@ fk_status cuda_fail(fk_grid* g, cudaError_t e, const char* what) {
 
 fk_status fk::flags_status(fk_grid* g, unsigned flags) {
   if (flags & kFlagTimeout) return fail(g, FK_ETIMEOUT, "a bounded wait inside the step kernel ran out");
+  if (flags & kFlagNegative)
+    return fail(g, FK_ENEGATIVE, "f has a negative value (the state set, or a step beyond rounding)");
   if (flags & kFlagNumeric) return fail(g, FK_ENUMERIC, "a moment or flux became non-finite");
   if (flags & kFlagCfl)
     return fail(g, FK_ECFL, "|c_x| + |c_1| + |c_2| exceeds 1: the explicit upwind step is unstable");
@@ -200,6 +202,20 @@ fk_status rebuild_tables(fk_grid* g) {
                            g->dv1, g->dv2, g->dt, g->dx, g->delta_max, g->A_max, g->k_s,
                            g->T_se, g->T_fe, j_over_ew, g->T_e, g->stream));
   return FK_OK;
+}
+
+// The failure-detection test knobs from the environment (off by default).
+void test_knobs(Params* p) {
+  p->wait_limit = kWaitLimitCycles;
+  p->withhold_item = -1;
+  if (const char* w = getenv("FK_TEST_WAIT_CYCLES")) {
+    const long long v = atoll(w);
+    if (v > 0) p->wait_limit = v;
+  }
+  if (const char* q = getenv("FK_TEST_WITHHOLD_COPY")) {
+    const int v = atoi(q);
+    if (v >= 0) p->withhold_item = v;
+  }
 }
 
 // Parameters changed: rebuild tables, re-evaluate the current state and
@@ -405,6 +421,7 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   p.refl = 0.0;
   p.band_lo = p.band_hi = 0;
   if (p.sat_window >= p.hist_cap) p.sat_window = p.hist_cap - 1;
+  test_knobs(&p);
   if (cx_max > 1.0 + 1e-12) {
     delete g;
     return fail(nullptr, FK_ECFL, "max |v1| dt / dx exceeds 1");
@@ -1016,7 +1033,14 @@ fk_status fk_set_state(fk_grid* g, const void* buf, size_t len) {
   g->ln_lambda = h.ln_lambda;
   g->self_consistent = h.self_consistent;
   g->see_enabled = h.see_enabled;
-  memcpy(&g->prm, &h.prm, sizeof(Params));
+  {
+    // the test knobs are the grid's own, not the checkpoint's
+    const long long wl = g->prm.wait_limit;
+    const int wi = g->prm.withhold_item;
+    memcpy(&g->prm, &h.prm, sizeof(Params));
+    g->prm.wait_limit = wl;
+    g->prm.withhold_item = wi;
+  }
   if ((s = upload_params(g)) != FK_OK) return s;
   if ((s = rebuild_tables(g)) != FK_OK) return s;
   const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof h;

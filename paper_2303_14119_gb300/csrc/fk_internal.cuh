@@ -22,7 +22,11 @@ enum : unsigned {
   kFlagCfl = 1u,
   kFlagNumeric = 2u,
   kFlagTimeout = 4u,
+  kFlagNegative = 8u,
 };
+
+// Default limit of a bounded wait inside a kernel: cycles (about 2 s).
+constexpr long long kWaitLimitCycles = 4000000000LL;
 
 // Run parameters read by the kernels from device memory, so that captured
 // CUDA graphs stay valid when a setter changes them.
@@ -49,6 +53,12 @@ struct Params {
   int self_consistent;
   int see_enabled;
   int band_lo, band_hi; // source planes [band_lo, band_hi)
+  // failure-detection test knobs, read from the environment at grid
+  // creation (off by default): the limit of the streaming kernel's bounded
+  // waits (cycles), and a pipeline item (>= 0) whose plane copy the unit of
+  // tile 0, chunk 0 does not issue, so that the waits on it run out
+  int withhold_item;
+  long long wait_limit;
 };
 
 // Mutable per-run scalars, device resident.

@@ -319,6 +319,7 @@ step_direct_kernel(StepArgs a, int mode) {
   const int ncell = (i1 - i0) * nv2;
   DensityAcc<T> s_n;
   double s_lv = 0.0, s_pe = 0.0, s_see = 0.0, s_vac = 0.0;
+  int neg = 0;  // a value written (or, moments only, read) is negative
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
     const int i = i0 + c / nv2;
     const int j = c - (c / nv2) * nv2;
@@ -361,6 +362,7 @@ step_direct_kernel(StepArgs a, int mode) {
       if ((c2 > (T)0 && j == nv2 - 1) || (c2 < (T)0 && j == 0)) s_lv += (double)a2 * (double)f;
     }
     s_n.add(fn);
+    neg |= fn < (T)0;
     if (k == 0 && dir < 0) {
       const double g = -a.tab.v1[i] * (double)fn;  // Eq. 13 without dv1 dv2
       s_pe += g;
@@ -368,6 +370,7 @@ step_direct_kernel(StepArgs a, int mode) {
     }
     if (k == nx - 1 && dir > 0) s_vac += a.tab.v1[i] * (double)fn;
   }
+  if (__syncthreads_or(neg) && threadIdx.x == 0) atomicOr(&a.st->flags, kFlagNegative);
   // the velocity pass (and the last pass of a Strang step) writes the
   // partial sums (uniform)
   if (xpass && !xlast) return;

@@ -11,7 +11,8 @@
 // registers: the x-neighbour never comes from memory twice.
 //
 // Pipeline.  Planes arrive in shared memory through cp.async.bulk copies
-// (the TMA engine) into a ring of kStages stages.  Each stage holds the
+// (the TMA engine) into a ring of stages (kStages for a whole-CTA unit,
+// kHalfStages for a half-CTA unit, whose planes are small).  Each stage holds the
 // tile's rows plus the one v1 halo row on the upwind side of that plane's
 // c_1.  Warp roles:
 //  - consumer warps (kWarps): wait until a stage is full, update their cells
@@ -43,9 +44,13 @@ constexpr int kBlock = kThreads + 32;
 constexpr int kHalfThreads = 96;
 constexpr int kHalfBlock = kHalfThreads + 32;
 static_assert(2 * kHalfBlock == kBlock, "two half units fill one CTA");
-constexpr int kStages = 4;
+constexpr int kStages = 4;      // stages of a whole-CTA unit
+constexpr int kHalfStages = 4;  // stages of a half-CTA unit
+static_assert(kHalfStages <= 32, "a producer lane per stage");
+// stages of a unit on NT consumer threads
+template <int NT>
+__host__ __device__ constexpr int unit_stages() { return NT == kThreads ? kStages : kHalfStages; }
 constexpr int kVecPerThread = 8;         // 16-byte vectors per consumer thread and plane
-constexpr long long kWaitLimit = 4000000000LL;  // cycles (~2 s) before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -89,12 +94,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Wait for the phase with the given parity; false if it did not complete
-// within kWaitLimit cycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// within *limit cycles (read only when the first try fails).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const long long* limit) {
   if (mbar_try_wait(bar, parity)) return true;
+  const long long lim = *limit;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitLimit) return false;
+    if (clock64() - t0 > lim) return false;
   return true;
 }
 
@@ -133,35 +139,36 @@ __host__ __device__ constexpr size_t stage_bytes(int stage_elems) {
 // The dynamic shared memory of both kernels starts with a slot for the
 // unit's StepArgs (filled by the batched kernel), so that one tile plan fits
 // a grid stepped alone or in a batch.  After the slot and the stages come:
-// mbarriers full[kStages], empty[kStages]; warp sums [kStages][kWarps][4]
+// mbarriers full[NS], empty[NS] (NS stages); warp sums [NS][kWarps][4]
 // (a half unit uses the first 3 warps of each stage)
 // (density, wall primary flux, wall secondary flux, vacuum outflow); for
 // FP64 grids the per-stage diagonal 1 - |c_x| - |c_1| - |c_2| (- dt nu) of
-// every tile row [kStages][kMaxTileRows] double, for FP32 grids the
+// every tile row [NS][kMaxTileRows] double, for FP32 grids the
 // separable source factors of the tile rows [kMaxTileRows] and of the row
 // cells [pitch] (float); the BGK equilibrium factors of Eq. 5 (FP32 grids:
 // m1 of the tile rows [kMaxTileRows] and m2 [pitch], float; FP64 grids:
-// dt nu_k n_k m1 per stage and tile row [kStages][kMaxTileRows] and m2
-// [pitch], double); two control ints.
+// dt nu_k n_k m1 per stage and tile row [NS][kMaxTileRows] and m2
+// [pitch], double); control words: the sticky flags and a withheld
+// pipeline item (ints), the wait limit (long long, at byte 8).
 constexpr int kArgsBytes = 384;  // a multiple of 128: the stages stay 128-byte aligned
 static_assert(sizeof(StepArgs) <= kArgsBytes && sizeof(StepArgs) % 8 == 0,
               "StepArgs must fit its shared-memory slot");
 constexpr int kWs = 4;
 constexpr int kMaxTileRows = 64;  // also bounds the per-stage row tables
-template <typename T>
+template <typename T, int NS>
 __host__ __device__ constexpr size_t tail_main_bytes(int pitch) {
-  return sizeof(T) == 8 ? kStages * kMaxTileRows * sizeof(double)
+  return sizeof(T) == 8 ? NS * kMaxTileRows * sizeof(double)
                         : ((size_t)(kMaxTileRows + pitch) * sizeof(float) + 15) / 16 * 16;
 }
-template <typename T>
+template <typename T, int NS>
 __host__ __device__ constexpr size_t tail_bgk_bytes(int pitch) {
-  return sizeof(T) == 8 ? (kStages * kMaxTileRows + (size_t)pitch) * sizeof(double)
+  return sizeof(T) == 8 ? (NS * kMaxTileRows + (size_t)pitch) * sizeof(double)
                         : ((size_t)(kMaxTileRows + pitch) * sizeof(float) + 15) / 16 * 16;
 }
-template <typename T>
+template <typename T, int NS>
 __host__ __device__ constexpr size_t tail_bytes(int pitch) {
-  return kArgsBytes + 2 * kStages * sizeof(uint64_t) + kStages * kWarps * kWs * sizeof(double) +
-         tail_main_bytes<T>(pitch) + tail_bgk_bytes<T>(pitch) + 16;
+  return kArgsBytes + 2 * NS * sizeof(uint64_t) + NS * kWarps * kWs * sizeof(double) +
+         tail_main_bytes<T, NS>(pitch) + tail_bgk_bytes<T, NS>(pitch) + 16;
 }
 
 // Exact split of a double x with 2^-126 <= |x| < 2^128 into hi + lo floats:
@@ -193,47 +200,20 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
   c += (s - (t - bp)) + (x - bp);
   s = t;
 }
-// Exact float -> double with integer operations (no FP64 instruction):
-// normal floats map exactly; zero and subnormals (|f| < 2^-126) give a
-// signed zero; infinities and NaN stay infinities and NaN.
-__device__ __forceinline__ double f2d_exact(float f) {
-  const unsigned int u = __float_as_uint(f);
-  const unsigned int sign = u & 0x80000000u;
-  const unsigned int e = (u >> 23) & 0xFFu;
-  const unsigned int m = u & 0x7FFFFFu;
-  const unsigned int ehi = e == 255u ? 0x7FF00000u : ((e + 896u) << 20);
-  const unsigned int hi = e == 0u ? sign : (sign | ehi | (m >> 3));
-  const unsigned int lo = e == 0u ? 0u : (m << 29);
-  return __hiloint2double((int)hi, (int)lo);
-}
-// The sum of a (hi, lo) pair of floats as a double: one FP64 add.
-__device__ __forceinline__ double pair_to_double(float2 p) {
-  return f2d_exact(p.x) + f2d_exact(p.y);
-}
-// Fold the (hi, lo) pairs of the lanes of a warp into lane 0 in FP32:
-// TwoSum on hi, low parts and rounding errors added in lo.
-__device__ __forceinline__ float2 warp_pair_sum(float hi, float lo) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const float oh = __shfl_down_sync(0xffffffffu, hi, o);
-    const float ol = __shfl_down_sync(0xffffffffu, lo, o);
-    float c = 0.f;
-    two_sum_acc(hi, c, oh);
-    lo += ol + c;
-  }
-  return make_float2(hi, lo);
-}
 
 // Wall (x = 0, v1 < 0: Eqs. 12-14) or vacuum (x = h_max, v1 > 0) sums of
 // f^{n+1} over this consumer thread's cells of one plane, read back from
-// its own stores.  Called only on those two planes of a march, so the main
-// loop carries no FP64 instruction for them.
+// its own stores; returns whether one of those cells is negative.  Called
+// only on those two planes of a march, so the main loop carries no FP64
+// instruction for them.
 template <typename T>
-__device__ __noinline__ void wall_terms(const T* oplane, const double* v1tab,
+__device__ __noinline__ bool wall_terms(const T* oplane, const double* v1tab,
                                         const double* delta, int tid, int nthreads, int i0,
                                         int rows, int nv2, int pitch, bool wall, double* out3) {
   constexpr int VEC = 16 / sizeof(T);
   const int QV = pitch / VEC;
   double pe = 0.0, see = 0.0, vac = 0.0;
+  bool neg = false;
   for (int m = 0; m < kVecPerThread; m++) {
     const int v = tid + nthreads * m;
     if (v >= rows * QV) break;
@@ -243,6 +223,7 @@ __device__ __noinline__ void wall_terms(const T* oplane, const double* v1tab,
     for (int e = 0; e < VEC && q * VEC + e < nv2; e++) {
       const size_t c = (size_t)i * pitch + q * VEC + e;
       const double fn = (double)oplane[c];
+      neg = neg || fn < 0.0;
       if (wall) {
         const double g = -v1 * fn;  // Eq. 13 without dv1 dv2
         pe += g;
@@ -255,6 +236,7 @@ __device__ __noinline__ void wall_terms(const T* oplane, const double* v1tab,
   out3[0] = pe;
   out3[1] = see;
   out3[2] = vac;
+  return neg;  // a value of the plane is negative
 }
 
 // Barrier over the threads of one unit: the whole CTA (barrier 0), or one
@@ -277,23 +259,24 @@ template <typename T, bool PADDED, bool BGK, int NT>
 __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, const int chunk,
                                             unsigned char* smem, const int tid, const int bar) {
   constexpr int NW = NT / 32;  // consumer warps
+  constexpr int NS = unit_stages<NT>();  // stages of the ring
   constexpr int VEC = Vec<T>::N;
   constexpr int M = kVecPerThread;
   const Geom& gm = a.geom;
   const size_t sbytes = stage_bytes<T>(gm.stage_elems);
   unsigned char* stage_base = smem;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * sbytes);
-  uint64_t* empty = full + kStages;
-  double* wsum = reinterpret_cast<double*>(empty + kStages);  // [kStages][kWarps][kWs]
-  double* dgl = wsum + kStages * kWarps * kWs;  // [kStages][kMaxTileRows], FP64
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * sbytes);
+  uint64_t* empty = full + NS;
+  double* wsum = reinterpret_cast<double*>(empty + NS);  // [NS][kWarps][kWs]
+  double* dgl = wsum + NS * kWarps * kWs;  // [NS][kMaxTileRows], FP64
   float* srow_s = reinterpret_cast<float*>(dgl);  // [kMaxTileRows], FP32
   float* scol_s = srow_s + kMaxTileRows;          // [pitch], FP32
-  unsigned char* bgk_base = reinterpret_cast<unsigned char*>(dgl) + tail_main_bytes<T>(a.pitch);
-  double* dgs = reinterpret_cast<double*>(bgk_base);  // [kStages][kMaxTileRows], FP64
-  double* m2d = dgs + kStages * kMaxTileRows;         // [pitch], FP64
+  unsigned char* bgk_base = reinterpret_cast<unsigned char*>(dgl) + tail_main_bytes<T, NS>(a.pitch);
+  double* dgs = reinterpret_cast<double*>(bgk_base);  // [NS][kMaxTileRows], FP64
+  double* m2d = dgs + NS * kMaxTileRows;         // [pitch], FP64
   float* m1_s = reinterpret_cast<float*>(bgk_base);   // [kMaxTileRows], FP32
   float* m2_s = m1_s + kMaxTileRows;                  // [pitch], FP32
-  int* ctl = reinterpret_cast<int*>(bgk_base + tail_bgk_bytes<T>(a.pitch));
+  int* ctl = reinterpret_cast<int*>(bgk_base + tail_bgk_bytes<T, NS>(a.pitch));
 
   const int lane = tid & 31, warp = tid >> 5;
   const int nt = gm.n_tiles;
@@ -328,9 +311,13 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       for (int j = tid; j < pitch; j += NT + 32) m2d[j] = a.tab.m2[j];
     }
   }
+  long long* wlim = reinterpret_cast<long long*>(ctl + 2);  // bounded waits' limit (cycles)
   if (tid == 0) {
     ctl[0] = (int)a.st->flags;
-    for (int s = 0; s < kStages; s++) {
+    // test knob: the pipeline item whose copy this unit does not issue
+    ctl[1] = (t == 0 && chunk == 0) ? a.prm->withhold_item : -1;
+    *wlim = a.prm->wait_limit;
+    for (int s = 0; s < NS; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NT);
     }
@@ -349,9 +336,9 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   if (warp == NW) {
     // ============================ producer warp ============================
     // Per item q: wait until every consumer released the stage of item
-    // q - kStages, read what its partial sums need from that stage and from
+    // q - NS, read what its partial sums need from that stage and from
     // the warp sums (gather), refill the stage with item q (issue), then
-    // reduce and store the partial sums of item q - kStages (finish): the
+    // reduce and store the partial sums of item q - NS (finish): the
     // reductions run while the copy is in flight.
     //
     // c_1 (FP32 copy) of item q sits in lane q % 32 of c1w (items wbase ..
@@ -377,7 +364,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       }
       const int k = item_plane(q);
       const float c1 = __shfl_sync(0xffffffffu, c1w, q & 31);
-      const int st = q % kStages;
+      const int st = q % NS;
       if (lane == st) c1slot = c1;
       T* stage = reinterpret_cast<T*>(stage_base + st * sbytes);
       // stage layout: the tile's rows start at row 1 when the halo lies
@@ -407,7 +394,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         }
       }
       __syncwarp();
-      if (lane == 0) {
+      if (lane == 0 && q != ctl[1]) {  // ctl[1]: a withheld item (test knob), else -1
         int lo = i0, hi = i1;
         if (c1 > 0.f && i0 > 0) lo = i0 - 1;  // v1 halo row on the upwind side
         if (c1 < 0.f && i1 < nv1) hi = i1 + 1;
@@ -423,19 +410,17 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
     struct Gathered {
       int k;       // plane (-1: the prime item, no sums)
       T lvt;       // this lane's share of the velocity-edge outflow
-      float2 wn;   // lane w < NW: warp w's density sum as a (hi, lo) pair
-      double ws[kWs];  // lane w < NW: warp w's wall and vacuum sums (slots 1-3)
+      double ws[kWs];  // lane w < NW: warp w's sums (all four on a wall plane)
     };
     auto gather = [&](int q) -> Gathered {
       Gathered g;
       g.k = -1;
       g.lvt = (T)0;
-      g.wn = make_float2(0.f, 0.f);
 #pragma unroll
       for (int i = 0; i < kWs; i++) g.ws[i] = 0.0;
       if (prime && q == 0) return g;
       const int k = item_plane(q);
-      const int st = q % kStages;
+      const int st = q % NS;
       g.k = k;
       const T* sb = reinterpret_cast<const T*>(stage_base + st * sbytes);
       const float c1f = __shfl_sync(0xffffffffu, c1slot, st);
@@ -454,7 +439,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         for (int r = lane; r < rows; r += 32) g.lvt += a2t * sb[(size_t)(r + rb) * pitch + nv2 - 1];
       if (lane < NW) {
         const double* ws = wsum + (st * kWarps + lane) * kWs;
-        g.wn = *reinterpret_cast<const float2*>(ws);
+        g.ws[0] = ws[0];
         if (k == 0 || k == nx - 1) {
 #pragma unroll
           for (int i = 1; i < kWs; i++) g.ws[i] = ws[i];
@@ -466,29 +451,20 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
     auto finish = [&](const Gathered& g) {
       if (g.k < 0) return;
       const int k = g.k;
-      const T lvs = warp_sum(g.lvt);
+      const double lv = (double)warp_sum(g.lvt);
       double sum[kWs] = {0.0, 0.0, 0.0, 0.0};
       const bool wall = k == 0 || k == nx - 1;
-      // the warps' density pairs in warp order, in FP32 (TwoSum)
-      float nh = 0.f, nl = 0.f;
 #pragma unroll
       for (int w = 0; w < NW; w++) {
-        const float h = __shfl_sync(0xffffffffu, g.wn.x, w);
-        const float l = __shfl_sync(0xffffffffu, g.wn.y, w);
-        float c = 0.f;
-        two_sum_acc(nh, c, h);
-        nl += l + c;
+        sum[0] += __shfl_sync(0xffffffffu, g.ws[0], w);
         if (wall) {
 #pragma unroll
           for (int i = 1; i < kWs; i++) sum[i] += __shfl_sync(0xffffffffu, g.ws[i], w);
         }
       }
       if (lane == 0) {
-        a.part.n[(size_t)k * nt + t] = pair_to_double(make_float2(nh, nl));
-        if constexpr (sizeof(T) == 4)
-          a.part.lv[(size_t)k * nt + t] = f2d_exact((float)lvs);
-        else
-          a.part.lv[(size_t)k * nt + t] = (double)lvs;
+        a.part.n[(size_t)k * nt + t] = sum[0];
+        a.part.lv[(size_t)k * nt + t] = lv;
         if (k == 0) {
           a.part.pe[t] = sum[1];
           a.part.see[t] = sum[2];
@@ -501,27 +477,28 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
     for (int q = 0; q < n_items; q++) {
       Gathered g{};
       g.k = -1;
-      if (q >= kStages) {
-        // stage reuse: wait until every consumer thread released item q - kStages
+      if (q >= NS) {
+        // stage reuse: wait until every consumer thread released item q - NS
         ok = __all_sync(0xffffffffu,
-                        mbar_wait(&empty[q % kStages], (uint32_t)(((q / kStages) - 1) & 1)));
+                        mbar_wait(&empty[q % NS], (uint32_t)(((q / NS) - 1) & 1), wlim));
         if (!ok) break;
-        g = gather(q - kStages);
+        g = gather(q - NS);
         __syncwarp();  // the stage is read by every lane before it is refilled
       }
       issue(q);
       issued = q + 1;
       finish(g);
     }
-    for (int q = max(0, issued - kStages); q < issued && ok; q++) {
-      ok = __all_sync(0xffffffffu, mbar_wait(&empty[q % kStages], (uint32_t)((q / kStages) & 1)));
+    for (int q = max(0, issued - NS); q < issued && ok; q++) {
+      ok = __all_sync(0xffffffffu, mbar_wait(&empty[q % NS], (uint32_t)((q / NS) & 1), wlim));
       if (ok) finish(gather(q));
     }
     if (!ok && lane == 0) {
       atomicOr(&a.st->flags, kFlagTimeout);
-      // copies still in flight land before the CTA leaves
-      for (int q = max(0, issued - kStages); q < issued; q++)
-        mbar_wait(&full[q % kStages], (uint32_t)((q / kStages) & 1));
+      // copies still in flight land before the CTA leaves (a withheld
+      // item's copy was never issued: nothing to wait for)
+      for (int q = max(0, issued - NS); q < issued; q++)
+        if (q != ctl[1]) mbar_wait(&full[q % NS], (uint32_t)((q / NS) & 1), wlim);
     }
     return;
   }
@@ -576,7 +553,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   const T* srcbase = sizeof(T) == 8 ? (const T*)a.tab.src : (const T*)a.tab.src32;
 
   for (int q = 0; q < n_items; q++) {
-    const int st = q % kStages;
+    const int st = q % NS;
     const bool compute = !(prime && q == 0);
     const int k = item_plane(q);
     // per-plane values and the source row (L2-resident table) are fetched
@@ -593,7 +570,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       bgk_a = (T)a.bgk32[k];
       bgk_s = (T)a.bgk32[nx + k];
     }
-    const bool ok = mbar_wait(&full[st], (uint32_t)((q / kStages) & 1));
+    const bool ok = mbar_wait(&full[st], (uint32_t)((q / NS) & 1), wlim);
     if (__any_sync(0xffffffffu, !ok)) {
       if (lane == 0) atomicOr(&a.st->flags, kFlagTimeout);
       return;
@@ -615,9 +592,8 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       // row read is always one that was copied or zero-filled
       const int nboff = c1f > 0.f ? -pitch : (c1f < 0.f ? pitch : 0);
       const double* dg = dgl + st * kMaxTileRows;
-      // density of f^{n+1}: a compensated FP32 sum (hi sh_, error sc_;
-      // FP64 grids add the low parts of their values in sl_)
-      float sh_ = 0.f, sc_ = 0.f, sl_ = 0.f;
+      T sum_n = (T)0;
+      float sh_ = 0.f, sc_ = 0.f, sl_ = 0.f;  // FP64 grids: compensated FP32 sum
       T* oplane = fout + (size_t)k * plane;
 #pragma unroll
       for (int m = 0; m < M; m++) {
@@ -678,31 +654,42 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
           if (PADDED && (so % pitch) + e >= nv2) fn = (T)0;  // row padding stays zero
           out.e[e] = fn;
           xr[m][e] = f;  // x-upwind value for the next plane is f^n here
-          if constexpr (sizeof(T) == 8) {
+          if (sizeof(T) == 4) {
+            sum_n += fn;
+          } else {
             float h, l;
             split_double((double)fn, h, l);
             two_sum_acc(sh_, sc_, h);
             sl_ += l;
           }
         }
-        if constexpr (sizeof(T) == 4)  // the vector's four values pairwise
-          two_sum_acc(sh_, sc_, ((float)out.e[0] + (float)out.e[1]) +
-                                     ((float)out.e[2] + (float)out.e[3]));
         __stcs(reinterpret_cast<float4*>(oplane + so + gbase),
                *reinterpret_cast<const float4*>(&out));
       }
-      // warp sum of this plane's f^{n+1}: the lanes' (hi, error) pairs folded
-      // in FP32 with TwoSum; the producer folds the warps' pairs the same
-      // way and converts once per plane
+      // warp sum of this plane's f^{n+1} (an FP32 grid sums its 32 lanes in
+      // FP32; everything above a warp is FP64)
       double* wsl = wsum + (st * kWarps + warp) * kWs;
-      {
-        const float2 ws = warp_pair_sum(sh_, sc_ + sl_);
-        if (lane == 0) *reinterpret_cast<float2*>(wsl) = ws;
+      if (sizeof(T) == 4) {
+        const T ws = warp_sum(sum_n);
+        if (lane == 0) wsl[0] = (double)ws;
+      } else {
+        // fold the lanes' (hi, error) pairs in FP32 with TwoSum, convert once
+        float lo = sc_ + sl_;
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_down_sync(0xffffffffu, sh_, o);
+          const float ol = __shfl_down_sync(0xffffffffu, lo, o);
+          float c = 0.f;
+          two_sum_acc(sh_, c, oh);
+          lo += ol + c;
+        }
+        if (lane == 0) wsl[0] = (double)sh_ + (double)lo;
       }
       const bool wall = k == 0 && dir < 0, vout = k == nx - 1 && dir > 0;
       if (wall || vout) {  // uniform over the block
         double b3[3];
-        wall_terms<T>(oplane, a.tab.v1, a.tab.delta, tid, NT, i0, rows, nv2, pitch, wall, b3);
+        const bool neg =
+            wall_terms<T>(oplane, a.tab.v1, a.tab.delta, tid, NT, i0, rows, nv2, pitch, wall, b3);
+        if (__any_sync(0xffffffffu, neg) && lane == 0) atomicOr(&a.st->flags, kFlagNegative);
         const double w1 = warp_sum(b3[0]), w2 = warp_sum(b3[1]), w3 = warp_sum(b3[2]);
         if (lane == 0) {
           wsl[1] = w1;
@@ -719,13 +706,13 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
 
 // Shared memory of one unit: argument slot, stages and tail.  A CTA of two
 // half units holds two such regions, each rounded up to 128 bytes.
-template <typename T>
+template <typename T, int NS>
 __host__ __device__ constexpr size_t unit_smem_bytes(int stage_elems, int pitch) {
-  return kStages * stage_bytes<T>(stage_elems) + tail_bytes<T>(pitch);
+  return NS * stage_bytes<T>(stage_elems) + tail_bytes<T, NS>(pitch);
 }
 template <typename T>
 __host__ __device__ constexpr size_t half_region_bytes(int stage_elems, int pitch) {
-  return (unit_smem_bytes<T>(stage_elems, pitch) + 127) / 128 * 128;
+  return (unit_smem_bytes<T, kHalfStages>(stage_elems, pitch) + 127) / 128 * 128;
 }
 
 // One grid, whole-CTA units: CTA b runs tile b % n_tiles of chunk
@@ -805,21 +792,26 @@ int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per
   if (pitch > cells) return 0;
   int rows = cells / pitch;
   if (rows > kMaxTileRows) rows = kMaxTileRows;
-  // two CTAs per SM: each unit holds kStages stages of (rows + 1) * pitch
-  // elements (a half unit gets half of its CTA, less the region's rounding)
+  // two CTAs per SM: each unit holds its stages (kStages, or kHalfStages for
+  // a half unit) of (rows + 1) * pitch elements (a half unit gets half of
+  // its CTA, less the region's rounding)
+  const int ns = half ? kHalfStages : kStages;
   const long tail =
-      (long)(precision == FK_F32 ? tail_bytes<float>(pitch) : tail_bytes<double>(pitch));
+      (long)(precision == FK_F32
+                 ? (half ? tail_bytes<float, kHalfStages>(pitch) : tail_bytes<float, kStages>(pitch))
+                 : (half ? tail_bytes<double, kHalfStages>(pitch)
+                         : tail_bytes<double, kStages>(pitch)));
   const long cta = (long)smem_per_sm / 2 - reserved_per_block;
   const long budget = (half ? cta / 2 - 127 : cta) - tail;
-  const long stage = budget / kStages / 128 * 128;
+  const long stage = budget / ns / 128 * 128;
   const long fit = stage / ((long)pitch * esize) - 1;  // one halo slot per stage
   if (fit < rows) rows = (int)fit;
   return rows > 0 ? rows : 0;
 }
 
 size_t stream_smem_bytes(int precision, int stage_elems, int pitch) {
-  return precision == FK_F32 ? unit_smem_bytes<float>(stage_elems, pitch)
-                             : unit_smem_bytes<double>(stage_elems, pitch);
+  return precision == FK_F32 ? unit_smem_bytes<float, kStages>(stage_elems, pitch)
+                             : unit_smem_bytes<double, kStages>(stage_elems, pitch);
 }
 
 size_t stream_half_bytes(int precision, int stage_elems, int pitch) {

@@ -19,13 +19,14 @@ import numpy as np
 
 from . import _build
 
-FK_OK, FK_EINVAL, FK_ENOMEM, FK_ECUDA, FK_ECFL, FK_ENUMERIC, FK_ETIMEOUT, FK_ESTATE = range(8)
+(FK_OK, FK_EINVAL, FK_ENOMEM, FK_ECUDA, FK_ECFL, FK_ENUMERIC, FK_ETIMEOUT, FK_ESTATE,
+ FK_ENEGATIVE) = range(9)
 FK_F64, FK_F32 = 0, 1
 FK_SCHEME_UNSPLIT, FK_SCHEME_LIE, FK_SCHEME_STRANG = 0, 1, 2
 FK_HISTORY_COLS = 8
 FK_LEDGER_LEN = 9
 STATUS_NAMES = {0: "FK_OK", 1: "FK_EINVAL", 2: "FK_ENOMEM", 3: "FK_ECUDA", 4: "FK_ECFL",
-                5: "FK_ENUMERIC", 6: "FK_ETIMEOUT", 7: "FK_ESTATE"}
+                5: "FK_ENUMERIC", 6: "FK_ETIMEOUT", 7: "FK_ESTATE", 8: "FK_ENEGATIVE"}
 
 
 class fk_grid_desc(C.Structure):

@@ -97,6 +97,52 @@ def solve(runs, horizon=HORIZON, sample_every=5000, sigma0=None, precision=fk.FK
                 cells=float(sum(p["nx"] * p["nv1"] * p["nv2"] for p in runs)))
 
 
+def solve_to_saturation(runs, max_steps, sigma0=None, sample_every=5000, precision=fk.FK_F32,
+                        stream=None, autotune=True):
+    """Like solve(), but stops once every run has passed the convergence test
+    of Sec. 2 (or after max_steps batch steps): the runs of a finer grid,
+    whose horizon would cost several times their saturation time.  The
+    history after a run's saturation is flat to the test's tolerance, so
+    labels() extends each sampled history with its last value."""
+    grids, status0 = [], []
+    for q, p in enumerate(runs):
+        g = make_grid(p, precision, stream)
+        st = fk.FK_OK
+        if sigma0 is not None and sigma0[q] != 0.0:
+            try:
+                g.set_surface_charge(float(sigma0[q]))
+            except fk.FkError as e:  # the warm-start field breaks the CFL bound
+                st = e.status
+        grids.append(g)
+        status0.append(st)
+    dt = np.array([g.info()["dt"] for g in grids])
+    t0 = time.perf_counter()
+    with fk.Batch(grids, stream) as b:
+        done = b.autotune(2) if autotune else 0
+        steps, sig = [], []
+        s0, st0, _, _ = b.scalars()
+        steps.append(st0.copy())
+        sig.append(s0.copy())
+        while done < max_steps:
+            k = min(sample_every, max_steps - done)
+            b.step(k)
+            done += k
+            s, st, sat, status = b.scalars()
+            steps.append(st.copy())
+            sig.append(s.copy())
+            live = (status == fk.FK_OK) & (np.array(status0) == fk.FK_OK)
+            if np.all((sat >= 0) | ~live):
+                break
+        _, _, sat, status = b.scalars()
+    seconds = time.perf_counter() - t0
+    for g in grids:
+        g.close()
+    status = np.where(np.array(status0) != fk.FK_OK, np.array(status0), status)
+    return dict(dt=dt, steps=np.array(steps), sigma=np.array(sig), sat_step=sat,
+                status=status, seconds=seconds, batch_steps=done,
+                cells=float(sum(p["nx"] * p["nv1"] * p["nv2"] for p in runs)))
+
+
 def labels(res, horizon=HORIZON):
     """Targets of each run: sigma at t_k = (k + 1) horizon / N_PROFILE
     (linear interpolation of the sampled history, C/m^2), the saturation
@@ -155,12 +201,14 @@ class Surrogate:
         Y = self.net.forward(Xn).astype(np.float64) * self.y_std + self.y_mean
         return Y[:, :N_PROFILE] * SIGMA_SCALE, T_UNIT * 10.0 ** Y[:, N_PROFILE]
 
-    def save(self, path):
+    def save(self, path, **extra):
+        """Weights and normalisation; `extra` arrays (e.g. the held-out
+        labels the network was evaluated on) are stored beside them."""
         np.savez(path, params=self.net.get_params(), x_mean=self.x_mean, x_std=self.x_std,
                  y_mean=self.y_mean, y_std=self.y_std, w=self.w,
                  meta=json.dumps(dict(n_profile=N_PROFILE, horizon=HORIZON,
                                       sigma_scale=SIGMA_SCALE, width=WIDTH, depth=DEPTH,
-                                      features=FEATURES)))
+                                      features=FEATURES)), **extra)
 
     @classmethod
     def load(cls, path, max_batch=512, stream=None):
@@ -226,38 +274,60 @@ def warm_start(sur, runs, prof_cold, res_cold, horizon=HORIZON, stream=None, pre
     }
 
 
-def fine_warm_start(weights, n_runs=4, nx=512, nv=128, horizon=HORIZON, stream=None,
-                    precision=fk.FK_F32):
-    """Warm starts on a finer grid than the network was trained on: the
-    first n_runs held-out parameter points of `weights` whose coarse run
-    saturated, solved on nx x nv x nv cold and from the network's
-    end-of-horizon charge, all in one batch."""
-    d = np.load(weights)
-    n_train, n_test, seed = int(d["n_train"]), int(d["n_test"]), int(d["seed"])
-    held = synth.surrogate_runs(n_train + n_test, seed)[n_train:]
-    sel = np.flatnonzero(d["test_ok"] & (d["test_sat_step"] >= 0) & (d["test_tsat"] < HORIZON))
-    sel = sel[:n_runs]
-    runs = [dict(held[q], nx=nx, nv1=nv, nv2=nv) for q in sel]
-    sur = Surrogate.load(weights, stream=stream)
-    pp, pt = sur.predict(runs)
-    sur.close()
-    sigma0 = np.concatenate([np.zeros(len(runs)), pp[:, -1]])
-    res = solve(runs + runs, horizon=horizon, sigma0=sigma0, stream=stream, precision=precision)
-    prof, _, ok = labels(res, horizon)
-    n = len(runs)
-    cold, warm = res["sat_step"][:n], res["sat_step"][n:]
-    end_c, end_w = prof[:n, -1], prof[n:, -1]
-    both = (cold >= 0) & (warm >= 0)
+def fine_points(ok, sat_step, tsat, n_train, n_fine_train, n_fine_test):
+    """Indices of the parameter points solved on the fine grid: the first
+    n_fine_train training draws and the first n_fine_test held-out draws
+    whose coarse run is valid and saturates within the horizon."""
+    good = ok & (sat_step >= 0) & (tsat < HORIZON)
+    tr = np.flatnonzero(good[:n_train])[:n_fine_train]
+    te = n_train + np.flatnonzero(good[n_train:])[:n_fine_test]
+    return tr, te
+
+
+def fine_solve(runs, idx, nx, nv, max_steps, stream=None):
+    """Cold runs of the draws idx on an nx x nv x nv grid, to saturation."""
+    fine = [dict(runs[q], nx=nx, nv1=nv, nv2=nv) for q in idx]
+    res = solve_to_saturation(fine, max_steps, stream=stream)
+    prof, tsat, ok = labels(res)
+    ok = ok & (res["sat_step"] >= 0)  # a label needs the saturated charge
+    return fine, res, prof, tsat, ok
+
+
+def fine_tune(sur, runs, Y, epochs=200, lr=2e-4, batch=64, seed=1):
+    """Continue training the network on the fine-grid labels, keeping the
+    input and output normalisation of its coarse training."""
+    Xn = (features(runs) - sur.x_mean) / sur.x_std
+    Yn = (Y - sur.y_mean) / sur.y_std
+    sur.net.set_params(sur.net.get_params())  # fresh Adam state
+    return sur.net.train(Xn, Yn, sur.w, batch=batch, epochs=epochs, lr=lr, seed=seed)
+
+
+def fine_warm_start_vs_cold(sur, fine_runs, cold, max_steps, stream=None):
+    """Warm starts of fine-grid runs from the network's end-of-horizon
+    charge, to saturation, against their stored cold runs (cold: sat_step
+    and the saturated charge sigma_sat of each run)."""
+    pp, pt = sur.predict(fine_runs)
+    res = solve_to_saturation(fine_runs, max_steps, sigma0=pp[:, -1], stream=stream)
+    prof_w, _, ok_w = labels(res)
+    warm = res["sat_step"]
+    cs, cw = cold["sat_step"], warm
+    both = (cs >= 0) & (cw >= 0) & ok_w
+    end_c = cold["sigma_sat"]
+    # the charge each warm run saturates at (flat from its saturated step on)
+    end_w = prof_w[:, -1]
     return {
-        "grid": [nx, nv, nv], "runs": n, "held_out_index": [int(q) for q in sel],
-        "cells_per_run": nx * nv * nv, "batch_steps": res["batch_steps"],
-        "solver_seconds": res["seconds"], "valid": [bool(x) for x in ok],
-        "sat_step_cold": [int(x) for x in cold], "sat_step_warm": [int(x) for x in warm],
-        "steps_saved_fraction": float(1.0 - warm[both].sum() / cold[both].sum()) if both.any() else None,
-        "sigma_end_cold": [float(x) for x in end_c], "sigma_end_warm": [float(x) for x in end_w],
+        "runs": len(fine_runs), "grid": [fine_runs[0]["nx"], fine_runs[0]["nv1"], fine_runs[0]["nv2"]],
+        "warm_valid": int(ok_w.sum()), "warm_saturated": int((cw >= 0).sum()),
+        "sat_step_cold": [int(x) for x in cs], "sat_step_warm": [int(x) for x in cw],
+        "steps_saved_fraction": float(1.0 - cw[both].sum() / cs[both].sum()) if both.any() else None,
+        "runs_faster": int(((cs - cw) > 0)[both].sum()),
         "sigma_warm_start": [float(x) for x in pp[:, -1]],
-        "sigma_end_rel_diff": [float(abs(w - c) / max(abs(c), 1e-30)) for w, c in zip(end_w, end_c)],
-        "predicted_tsat_s": [float(x) for x in pt],
+        "sigma_sat_cold": [float(x) for x in end_c],
+        "sigma_sat_warm": [float(x) for x in end_w],
+        "start_rel_err": [float(abs(a - c) / max(abs(c), 1e-30)) for a, c in zip(pp[:, -1], end_c)],
+        "sigma_sat_rel_diff_warm_vs_cold": [float(abs(a - c) / max(abs(c), 1e-30))
+                                            for a, c in zip(end_w, end_c)],
+        "batch_steps": int(res["batch_steps"]), "solver_seconds": res["seconds"],
     }
 
 
@@ -333,23 +403,24 @@ def main(argv=None):
     ap.add_argument("--solve-part", default=None, metavar="I/P",
                     help="only solve part I of P of the draws and save its data_partIofP.npz")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-start runs")
-    ap.add_argument("--fine", default=None, metavar="WEIGHTS",
-                    help="only run fine-grid warm starts with these trained weights")
-    ap.add_argument("--fine-runs", type=int, default=4)
     ap.add_argument("--fine-nx", type=int, default=512)
     ap.add_argument("--fine-nv", type=int, default=128)
+    ap.add_argument("--fine-solve", default=None, metavar="NTR,NTE",
+                    help="with --data: solve NTR training and NTE held-out points (valid, "
+                         "saturating on the coarse grid) cold on the fine grid to saturation and "
+                         "save data_fine_NXxNVxNV.npz")
+    ap.add_argument("--fine-data", default=None, metavar="FILE",
+                    help="with --data: after the coarse training, fine-tune the network on the "
+                         "training points of FILE (from --fine-solve), evaluate it on its held-out "
+                         "points and warm-start their fine-grid runs")
+    ap.add_argument("--fine-max-steps", type=int, default=1600000)
+    ap.add_argument("--fine-epochs", type=int, default=200)
+    ap.add_argument("--fine-lr", type=float, default=2e-4)
     args = ap.parse_args(argv)
     import torch
     torch.cuda.set_stream(torch.cuda.Stream())
     stream = torch.cuda.current_stream().cuda_stream
     os.makedirs(args.out, exist_ok=True)
-    if args.fine:
-        rep = fine_warm_start(args.fine, args.fine_runs, args.fine_nx, args.fine_nv, args.horizon,
-                              stream)
-        with open(os.path.join(args.out, "fine_report.json"), "w") as fh:
-            json.dump(rep, fh, indent=1)
-        print(json.dumps(rep))
-        return
     runs = synth.surrogate_runs(args.n_train + args.n_test, args.seed)
     if args.solve_part:
         idx = part_slice(len(runs), args.solve_part)
@@ -376,6 +447,23 @@ def main(argv=None):
         prof, tsat, ok = labels(res, args.horizon)
         save_data(os.path.join(args.out, "data.npz"), np.arange(len(runs)), runs, res, prof,
                   tsat, ok)
+    grid_tag = "%dx%dx%d" % (args.fine_nx, args.fine_nv, args.fine_nv)
+    if args.fine_solve:
+        ntr, nte = (int(v) for v in args.fine_solve.split(","))
+        itr, ite = fine_points(ok, res["sat_step"], tsat, args.n_train, ntr, nte)
+        idx = np.concatenate([itr, ite])
+        fine, fres, fprof, ftsat, fok = fine_solve(runs, idx, args.fine_nx, args.fine_nv,
+                                                   args.fine_max_steps, stream)
+        path = os.path.join(args.out, "data_fine_%s.npz" % grid_tag)
+        np.savez(path, idx_train=itr, idx_test=ite, prof=fprof, tsat=ftsat, ok=fok,
+                 status=fres["status"], sat_step=fres["sat_step"], dt=fres["dt"],
+                 sigma_sat=fprof[:, -1], seconds=fres["seconds"], batch_steps=fres["batch_steps"],
+                 cells=fres["cells"])
+        print(json.dumps({"fine_solve": grid_tag, "train": int(itr.size), "test": int(ite.size),
+                          "saturated": int((fres["sat_step"] >= 0).sum()), "valid": int(fok.sum()),
+                          "batch_steps": int(fres["batch_steps"]),
+                          "solver_seconds": fres["seconds"], "file": path}))
+        return
     tr = np.arange(args.n_train)
     te = np.arange(args.n_train, args.n_train + args.n_test)
     tr_ok = tr[ok[tr]]
@@ -384,7 +472,10 @@ def main(argv=None):
     hist = sur.fit([runs[q] for q in tr_ok], targets(prof[tr_ok], tsat[tr_ok]),
                    epochs=args.epochs, lr=args.lr, batch=args.batch, seed=args.seed)
     train_s = time.perf_counter() - t0
-    sur.save(os.path.join(args.out, "surrogate.npz"))
+    coarse_tag = "%dx%dx%d" % (runs[0]["nx"], runs[0]["nv1"], runs[0]["nv2"])
+    sur.save(os.path.join(args.out, "surrogate_%s.npz" % coarse_tag), seed=args.seed,
+             n_train=args.n_train, n_test=args.n_test, test_prof=prof[te], test_tsat=tsat[te],
+             test_ok=ok[te], test_sat_step=res["sat_step"][te], test_dt=res["dt"][te])
     test_runs = [runs[q] for q in te]
     ev_test = evaluate(sur, test_runs, prof[te], tsat[te], ok[te])
     ev_train = evaluate(sur, [runs[q] for q in tr], prof[tr], tsat[tr], ok[tr])
@@ -410,8 +501,43 @@ def main(argv=None):
         "test_eval": ev_test,
         "warm_start": ws,
     }
-    with open(os.path.join(args.out, "report.json"), "w") as fh:
-        json.dump(report, fh, indent=1)
+    if args.fine_data:
+        fd = np.load(args.fine_data)
+        itr, ite = fd["idx_train"], fd["idx_test"]
+        ntr = itr.size
+        fprof, ftsat, fok = fd["prof"], fd["tsat"], fd["ok"]
+        fine_tr = [dict(runs[q], nx=args.fine_nx, nv1=args.fine_nv, nv2=args.fine_nv) for q in itr]
+        fine_te = [dict(runs[q], nx=args.fine_nx, nv1=args.fine_nv, nv2=args.fine_nv) for q in ite]
+        # before fine-tuning: the coarse network on the fine held-out points
+        ev_fine_before = evaluate(sur, fine_te, fprof[ntr:], ftsat[ntr:], fok[ntr:])
+        keep = np.flatnonzero(fok[:ntr])
+        t0 = time.perf_counter()
+        fh = fine_tune(sur, [fine_tr[q] for q in keep], targets(fprof[keep], ftsat[keep]),
+                       epochs=args.fine_epochs, lr=args.fine_lr, seed=args.seed + 1)
+        tune_s = time.perf_counter() - t0
+        ev_fine = evaluate(sur, fine_te, fprof[ntr:], ftsat[ntr:], fok[ntr:])
+        sur.save(os.path.join(args.out, "surrogate_%s.npz" % grid_tag), seed=args.seed,
+                 n_train=args.n_train, n_test=args.n_test, fine_idx_train=itr, fine_idx_test=ite,
+                 test_prof=fprof[ntr:], test_tsat=ftsat[ntr:], test_ok=fok[ntr:],
+                 test_sat_step=fd["sat_step"][ntr:], test_dt=fd["dt"][ntr:],
+                 grid=np.array([args.fine_nx, args.fine_nv, args.fine_nv]))
+        sel = np.flatnonzero(fok[ntr:])
+        cold = {"sat_step": fd["sat_step"][ntr:][sel], "sigma_sat": fd["sigma_sat"][ntr:][sel]}
+        fws = fine_warm_start_vs_cold(sur, [fine_te[q] for q in sel], cold, args.fine_max_steps,
+                                      stream)
+        report["fine"] = {
+            "grid": [args.fine_nx, args.fine_nv, args.fine_nv],
+            "train_points": int(ntr), "train_valid": int(keep.size),
+            "test_points": int(ite.size), "test_valid": int(fok[ntr:].sum()),
+            "cold_solver_seconds": float(fd["seconds"]), "cold_batch_steps": int(fd["batch_steps"]),
+            "fine_tune": {"epochs": args.fine_epochs, "lr": args.fine_lr, "seconds": tune_s,
+                          "loss_first": float(fh[0]), "loss_last": float(fh[-1])},
+            "test_eval_coarse_network": ev_fine_before,
+            "test_eval_fine_tuned": ev_fine,
+            "warm_start": fws,
+        }
+    with open(os.path.join(args.out, "report.json"), "w") as fh_:
+        json.dump(report, fh_, indent=1)
     print(json.dumps(report))
     sur.close()
 

@@ -187,3 +187,36 @@ def test_training_reduces_loss_and_is_deterministic():
         loss, _ = m.loss_grad(X, T, grad=False)
     lo = o.loss(runs[0][1].astype(np.float64), X.astype(np.float64), T.astype(np.float64), bf16=True)
     assert abs(loss - lo) <= 1e-3 * lo
+
+
+def test_adam_steps_match_the_fp64_restatement():
+    """Two training steps (fk_mlp_train, one batch of one sample per epoch,
+    so the batch order is fixed) against Adam (Kingma and Ba 2015) written
+    out in FP64 (oracle.mlp_oracle.adam_step), fed the gradients the library
+    itself reports at the starting point and after the first step
+    (fk_mlp_loss_grad): the parameter changes agree to FP32 rounding."""
+    from oracle.mlp_oracle import adam_step
+    rng = np.random.default_rng(12)
+    dims = (6, 32, 2, 5)
+    with fk.Mlp(*dims, max_batch=128) as m:
+        p0 = rng.normal(0.0, 0.3, m.param_count()).astype(np.float32)
+        x = rng.normal(size=(1, 6)).astype(np.float32)
+        t = rng.normal(size=(1, 5)).astype(np.float32)
+        lr = 1e-3
+        m.set_params(p0)
+        _, g0 = m.loss_grad(x, t)
+        m.train(x, t, batch=1, epochs=1, lr=lr, seed=3)
+        p1 = m.get_params()
+        _, g1 = m.loss_grad(x, t)
+        m.train(x, t, batch=1, epochs=1, lr=lr, seed=4)
+        p2 = m.get_params()
+    z = np.zeros(p0.size)
+    r1, m1, v1 = adam_step(p0, g0, z, z, 1, lr)
+    r2, _, _ = adam_step(p1, g1, m1, v1, 2, lr)
+    d1, d1r = p1.astype(np.float64) - p0, r1 - p0
+    d2, d2r = p2.astype(np.float64) - p1, r2 - p1.astype(np.float64)
+    # FP32 parameters: the stored update is rounded to p's ulp
+    tol = lambda p: 4 * np.spacing(np.abs(p).astype(np.float32)).astype(np.float64) + 1e-6 * lr
+    assert np.all(np.abs(d1 - d1r) <= tol(p1)), np.abs(d1 - d1r).max()
+    assert np.all(np.abs(d2 - d2r) <= tol(p2)), np.abs(d2 - d2r).max()
+    assert np.abs(d1r).max() > 0.5 * lr  # a real step was taken

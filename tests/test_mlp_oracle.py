@@ -92,3 +92,32 @@ def test_zero_residual_gives_zero_loss_and_gradient():
     Y, _ = o.forward(p, X, bf16=True)
     loss, g = o.loss_grad(p, X, Y, w, bf16=True)
     assert loss == 0.0 and not g.any()
+
+
+def test_adam_step_against_its_closed_forms():
+    """Adam's first step moves each parameter by lr * g / (|g| + eps) (the
+    bias corrections undo the zero initial moments); with a constant
+    gradient every later step does the same; with eps = 0 the step is
+    invariant to scaling the gradient."""
+    from oracle.mlp_oracle import adam_step
+    rng = np.random.default_rng(5)
+    p0 = rng.normal(size=50)
+    g = rng.normal(size=50)
+    z = np.zeros(50)
+    lr = 1e-3
+    p1, m1, v1 = adam_step(p0, g, z, z, 1, lr)
+    assert np.allclose(p1 - p0, -lr * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    p, m, v = p1, m1, v1
+    for t in range(2, 6):
+        q, m, v = adam_step(p, g, m, v, t, lr)
+        assert np.allclose(q - p, -lr * g / (np.abs(g) + 1e-8), rtol=1e-9, atol=0)
+        p = q
+    a, _, _ = adam_step(p0, g, z, z, 1, lr, eps=0.0)
+    b, _, _ = adam_step(p0, 1e3 * g, z, z, 1, lr, eps=0.0)
+    assert np.allclose(a, b, rtol=1e-14, atol=0)
+    # two different gradients: the second step mixes them as the algorithm states
+    g2 = rng.normal(size=50)
+    q2, _, _ = adam_step(p1, g2, m1, v1, 2, lr)
+    mh = (0.9 * 0.1 * g + 0.1 * g2) / (1 - 0.9 ** 2)
+    vh = (0.999 * 0.001 * g * g + 0.001 * g2 * g2) / (1 - 0.999 ** 2)
+    assert np.allclose(q2 - p1, -lr * mh / (np.sqrt(vh) + 1e-8), rtol=1e-12, atol=0)
