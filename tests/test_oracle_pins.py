@@ -911,3 +911,38 @@ def test_openmp_build_equals_serial_build_bitwise(scheme):
     assert sa == sb
     assert la == lb
     assert np.array_equal(ha, hb)
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_split_schemes_agree_with_the_unsplit_step_to_first_order(scheme):
+    """Lie (R13) and Strang (R14) splitting with the self-consistent field,
+    SEE and the source on: one step differs from the unsplit step by O(dt^2)
+    (halving dt quarters the difference) and a fixed time by O(dt) (halving
+    dt halves it).  Every sub-step is a forward-Euler step, so all three
+    schemes are first order in time; the velocity pass taking E_x from f^n
+    does not lower that order."""
+    shape = (12, 16, 14)
+    f0 = synth.random_f(shape, 3, 1e4)
+
+    def run(s, dt, n):
+        o = Oracle(*shape, 20e-6, -6e7, 6e7, -3e7, 3e7, dt=dt)
+        o.set_fields(-2e6, True, 0.0)
+        o.set_see(3.0, 400.0, 1.0, 2.0)
+        o.set_source(1e7, 4e-6, 14e-6, 4.0)
+        o.set_scheme(s)
+        o.set_state(f0, 2e-6)
+        o.step(n)
+        return o.get_f()
+
+    dt0 = Oracle(*shape, 20e-6, -6e7, 6e7, -3e7, 3e7, cfl=0.4).info()["dt"]
+    per_step, fixed_time = [], []
+    for k in range(3):
+        dt = dt0 / 2 ** k
+        fs, fu = run(scheme, dt, 1), run(0, dt, 1)
+        per_step.append(np.abs(fs - fu).sum() / np.abs(fu).sum())
+        fs, fu = run(scheme, dt, 8 * 2 ** k), run(0, dt, 8 * 2 ** k)
+        fixed_time.append(np.abs(fs - fu).sum() / np.abs(fu).sum())
+    for a, b in zip(per_step, per_step[1:]):
+        assert 3.6 < a / b < 4.4
+    for a, b in zip(fixed_time, fixed_time[1:]):
+        assert 1.8 < a / b < 2.4
