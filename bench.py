@@ -272,8 +272,9 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
 def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True):
     """The user's loop through the C ABI with host buffers: upload f0 from
     pinned host memory, then per step advance (the instances as one batch,
-    or each alone) and read sigma and the wall fluxes back, finally read f
-    back; all inside the timed region."""
+    or each alone) and read n_e, E_x, sigma and the wall fluxes back (the
+    batch: queued into pinned slots, step n's read while step n + 1 runs),
+    finally read f back; all inside the timed region."""
     stream = torch.cuda.current_stream().cuda_stream
     assert stream, "e2e_arm needs a non-default current stream"
     grids = make_grids(fk, w, precision, stream)
@@ -299,17 +300,24 @@ def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True):
     b = fk.Batch(grids, stream) if batch else None
     ne_all = np.empty(nx * len(grids))
     ex_all = np.empty(nx * len(grids))
-    for _ in range(steps):
+    slot = 0
+    for q in range(steps):
         if b is not None:
             # one step of every instance, then every instance's n_e, E_x,
-            # sigma and wall fluxes read back with one wait
+            # sigma and wall fluxes queued for read-back into a pinned slot;
+            # the previous step's are collected while this step runs
             b.step(1)
-            b.moments(ne_all, ex_all)
+            b.moments_enqueue(slot)
+            if q > 0:
+                b.moments_collect(slot ^ 1, ne_all, ex_all)
+            slot ^= 1
         else:
             for g in grids:
                 g.step(1)
                 fk.fk_moments(g.h, nx, ne, ex)
                 g.surface_charge()
+    if b is not None and steps > 0:
+        b.moments_collect(slot ^ 1, ne_all, ex_all)  # the last step's
     for g in grids:
         if f32:
             g.get_f32(out_f)

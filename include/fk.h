@@ -381,6 +381,20 @@ fk_status fk_batch_scalars(fk_batch *batch, double *sigma, int64_t *step, int64_
 fk_status fk_batch_moments(fk_batch *batch, double *sigma, double *gamma_pe, double *gamma_see,
                            double *n_e, double *Ex);
 
+/* Pipelined form of fk_batch_moments, so that a loop can read the moments
+ * of step n while step n + 1 runs.  fk_batch_moments_enqueue queues, on the
+ * batch's stream after the work enqueued so far, copies of every grid's
+ * sigma, Gamma_pe, Gamma_see, n_e and E_x into one of two pinned host slots
+ * the batch owns (slot 0 or 1; allocated on its first use) and returns at
+ * once.  fk_batch_moments_collect waits for that slot's copies only (not
+ * for later work) and unpacks them as fk_batch_moments does.  A slot holds
+ * one set: enqueue on a full slot, or collect from an empty one, returns
+ * FK_ESTATE.  The values are those of the state the copies were queued
+ * after; sticky device errors are reported by fk_batch_sync. */
+fk_status fk_batch_moments_enqueue(fk_batch *batch, int32_t slot);
+fk_status fk_batch_moments_collect(fk_batch *batch, int32_t slot, double *sigma,
+                                   double *gamma_pe, double *gamma_see, double *n_e, double *Ex);
+
 /* Autotuner: picks the x-chunk length (planes per work unit) of every size
  * bucket of the batch -- grids grouped by plane size and nx, each a power of
  * two -- by timing real steps: one trial of steps_per_trial >= 1 batch steps

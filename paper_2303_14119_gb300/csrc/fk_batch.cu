@@ -60,6 +60,12 @@ struct fk_batch {
   bool timing = false;
   std::vector<cudaEvent_t> ev; // pairs around the step kernel
   int ev_used = 0;
+  // pipelined moment read-back (fk_batch_moments_enqueue / _collect): two
+  // pinned slots, each the grids' DevState then n_e and E_x of every grid
+  void* h_slot[2] = {nullptr, nullptr};
+  cudaEvent_t slot_ev[2] = {nullptr, nullptr};
+  bool slot_full[2] = {false, false};
+  size_t sum_nx = 0;
   std::string err;
 };
 
@@ -331,6 +337,10 @@ void free_batch(fk_batch* b) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   if (b->done) cudaEventDestroy(b->done);
+  for (int q = 0; q < 2; q++) {
+    if (b->h_slot[q]) cudaFreeHost(b->h_slot[q]);
+    if (b->slot_ev[q]) cudaEventDestroy(b->slot_ev[q]);
+  }
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -532,6 +542,57 @@ fk_status fk_batch_moments(fk_batch* b, double* sigma, double* gamma_pe, double*
     if (Ex) memcpy(Ex + off, hv + g->nx, vb);
     off += g->nx;
   }
+  return FK_OK;
+}
+
+fk_status fk_batch_moments_enqueue(fk_batch* b, int32_t slot) {
+  if (!b) return FK_EINVAL;
+  if (slot != 0 && slot != 1) return bfail(b, FK_EINVAL, "slot must be 0 or 1");
+  BK_CUDA(b, cudaSetDevice(b->dev));
+  if (!b->h_slot[slot]) {  // first use of the slot: its pinned buffer and event
+    size_t nx = 0;
+    for (const fk_grid* g : b->grids) nx += g->nx;
+    b->sum_nx = nx;
+    BK_CUDA(b, cudaMallocHost(&b->h_slot[slot], b->n * sizeof(DevState) + 2 * nx * sizeof(double)));
+    BK_CUDA(b, cudaEventCreateWithFlags(&b->slot_ev[slot], cudaEventDisableTiming));
+  }
+  if (b->slot_full[slot]) return bfail(b, FK_ESTATE, "slot holds uncollected moments");
+  DevState* hst = static_cast<DevState*>(b->h_slot[slot]);
+  double* hne = reinterpret_cast<double*>(hst + b->n);
+  double* hex = hne + b->sum_nx;
+  size_t off = 0;
+  for (int i = 0; i < b->n; i++) {
+    const fk_grid* g = b->grids[i];
+    const size_t vb = (size_t)g->nx * sizeof(double);
+    BK_CUDA(b, cudaMemcpyAsync(hst + i, g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                               b->stream));
+    BK_CUDA(b, cudaMemcpyAsync(hne + off, g->d_ne, vb, cudaMemcpyDeviceToHost, b->stream));
+    BK_CUDA(b, cudaMemcpyAsync(hex + off, g->d_Ex, vb, cudaMemcpyDeviceToHost, b->stream));
+    off += g->nx;
+  }
+  BK_CUDA(b, cudaEventRecord(b->slot_ev[slot], b->stream));
+  b->slot_full[slot] = true;
+  return FK_OK;
+}
+
+fk_status fk_batch_moments_collect(fk_batch* b, int32_t slot, double* sigma, double* gamma_pe,
+                                   double* gamma_see, double* n_e, double* Ex) {
+  if (!b) return FK_EINVAL;
+  if (slot != 0 && slot != 1) return bfail(b, FK_EINVAL, "slot must be 0 or 1");
+  if (!b->slot_full[slot]) return bfail(b, FK_ESTATE, "nothing enqueued in this slot");
+  BK_CUDA(b, cudaSetDevice(b->dev));
+  BK_CUDA(b, cudaEventSynchronize(b->slot_ev[slot]));
+  b->slot_full[slot] = false;
+  const DevState* hst = static_cast<const DevState*>(b->h_slot[slot]);
+  const double* hne = reinterpret_cast<const double*>(hst + b->n);
+  const double* hex = hne + b->sum_nx;
+  for (int i = 0; i < b->n; i++) {
+    if (sigma) sigma[i] = hst[i].sigma;
+    if (gamma_pe) gamma_pe[i] = hst[i].g_pe;
+    if (gamma_see) gamma_see[i] = hst[i].g_see;
+  }
+  if (n_e) memcpy(n_e, hne, b->sum_nx * sizeof(double));
+  if (Ex) memcpy(Ex, hex, b->sum_nx * sizeof(double));
   return FK_OK;
 }
 

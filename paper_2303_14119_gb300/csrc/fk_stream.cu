@@ -597,6 +597,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       T* oplane = fout + (size_t)k * plane;
 #pragma unroll
       for (int m = 0; m < M; m++) {
+        if (NT * m >= rows * QV) break;  // no thread of the unit has vector m (uniform)
         const int so = soff[m] & 0xFFFFFF;
         Vec<T> own;
         if (valid >> m & 1)

@@ -109,6 +109,8 @@ def load(build_if_missing: bool = True):
         "fk_batch_info": [P, dp],
         "fk_batch_scalars": [P, dp, i64p, i64p, C.POINTER(C.c_int32)],
         "fk_batch_moments": [P, dp, dp, dp, dp, dp],
+        "fk_batch_moments_enqueue": [P, C.c_int32],
+        "fk_batch_moments_collect": [P, C.c_int32, dp, dp, dp, dp, dp],
         "fk_batch_set_kernel_timing": [P, I],
         "fk_batch_kernel_timing": [P, i64p, dp],
         "fk_gemm_bf16_tn": [P, I64, P, I64, P, I64, C.c_int32, C.c_int32, C.c_int32, P, P],
@@ -635,6 +637,25 @@ def fk_batch_moments(b, n, n_e=None, Ex=None, sigma=None, gamma_pe=None, gamma_s
     return sigma, gamma_pe, gamma_see, n_e, Ex
 
 
+def fk_batch_moments_enqueue(b, slot):
+    _bcheck(load().fk_batch_moments_enqueue(b, int(slot)), "fk_batch_moments_enqueue", b)
+
+
+def fk_batch_moments_collect(b, n, slot, n_e=None, Ex=None, sigma=None, gamma_pe=None,
+                             gamma_see=None):
+    """The moments queued in `slot` by fk_batch_moments_enqueue (waits for
+    those copies only); arrays as fk_batch_moments."""
+    sigma = np.empty(n) if sigma is None else sigma
+    gamma_pe = np.empty(n) if gamma_pe is None else gamma_pe
+    gamma_see = np.empty(n) if gamma_see is None else gamma_see
+    _bcheck(load().fk_batch_moments_collect(b, int(slot), _dp(sigma), _dp(gamma_pe),
+                                            _dp(gamma_see),
+                                            _dp(n_e) if n_e is not None else None,
+                                            _dp(Ex) if Ex is not None else None),
+            "fk_batch_moments_collect", b)
+    return sigma, gamma_pe, gamma_see, n_e, Ex
+
+
 def fk_batch_autotune(b, steps_per_trial=2):
     taken = C.c_int64()
     _bcheck(load().fk_batch_autotune(b, int(steps_per_trial), C.byref(taken)),
@@ -716,6 +737,14 @@ class Batch:
         """(sigma, gamma_pe, gamma_see, n_e, Ex) of every grid, one wait;
         n_e and Ex are filled only when given (length sum of nx)."""
         return fk_batch_moments(self.h, len(self.grids), n_e, Ex, sigma, gamma_pe, gamma_see)
+
+    def moments_enqueue(self, slot):
+        fk_batch_moments_enqueue(self.h, slot)
+
+    def moments_collect(self, slot, n_e=None, Ex=None, sigma=None, gamma_pe=None,
+                        gamma_see=None):
+        return fk_batch_moments_collect(self.h, len(self.grids), slot, n_e, Ex, sigma,
+                                        gamma_pe, gamma_see)
 
     def chunks(self):
         return fk_batch_get_chunks(self.h, len(self.grids))

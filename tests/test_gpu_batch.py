@@ -263,3 +263,40 @@ def test_batch_moments_one_wait_equals_each_grids_getters(prec):
         assert np.array_equal(sig2, sig)
     for g in a:
         g.close()
+
+
+def test_pipelined_moments_equal_the_blocking_getter_step_by_step():
+    """fk_batch_moments_enqueue / _collect (two pinned slots, the moments of
+    step n read while step n + 1 runs) give, step by step, the same values
+    as fk_batch_moments on a twin batch stepped the same way."""
+    a, b = twins(fk.FK_F32)
+    nx = sum(g.shape[0] for g in a)
+    got, ref = [], []
+    with fk.Batch(a) as ba, fk.Batch(b) as bb:
+        with pytest.raises(fk.FkError) as ei:
+            ba.moments_collect(0)
+        assert ei.value.status == fk.FK_ESTATE
+        slot = 0
+        for step in range(6):
+            ba.step(1)
+            ba.moments_enqueue(slot)
+            if step > 0:
+                ne, ex = np.empty(nx), np.empty(nx)
+                sig, pe, see, _, _ = ba.moments_collect(slot ^ 1, ne, ex)
+                got.append((sig, pe, see, ne, ex))
+            slot ^= 1
+            bb.step(1)
+            ne, ex = np.empty(nx), np.empty(nx)
+            sig, pe, see, _, _ = bb.moments(ne, ex)
+            ref.append((sig, pe, see, ne, ex))
+        with pytest.raises(fk.FkError) as ei:
+            ba.moments_enqueue(slot ^ 1)  # still full
+        assert ei.value.status == fk.FK_ESTATE
+        ne, ex = np.empty(nx), np.empty(nx)
+        got.append(ba.moments_collect(slot ^ 1, ne, ex)[:3] + (ne, ex))
+    assert len(got) == len(ref) == 6
+    for g_, r_ in zip(got, ref):
+        for x, y in zip(g_, r_):
+            assert np.array_equal(x, y)
+    for g in a + b:
+        g.close()
