@@ -293,7 +293,10 @@ cudaError_t launch_loss_reduce(const double* loss_rows, int n, double scale, dou
 
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long count, float lr,
                         float b1, float b2, float eps, int t, cudaStream_t s) {
-  const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+  // bias corrections 1 - beta^t in FP64: in FP32, 1 - 0.999^t loses about
+  // nine bits to cancellation at small t
+  const float c1 = (float)(1.0 - pow((double)b1, (double)t));
+  const float c2 = (float)(1.0 - pow((double)b2, (double)t));
   adam_kernel<<<ew_blocks(count), kEwThreads, 0, s>>>(p, g, m, v, count, lr, b1, b2, eps, c1, c2);
   return cudaGetLastError();
 }

@@ -215,8 +215,10 @@ def test_adam_steps_match_the_fp64_restatement():
     r2, _, _ = adam_step(p1, g1, m1, v1, 2, lr)
     d1, d1r = p1.astype(np.float64) - p0, r1 - p0
     d2, d2r = p2.astype(np.float64) - p1, r2 - p1.astype(np.float64)
-    # FP32 parameters: the stored update is rounded to p's ulp
-    tol = lambda p: 4 * np.spacing(np.abs(p).astype(np.float32)).astype(np.float64) + 1e-6 * lr
+    # the kernel's moments and update are FP32 (relative rounding of a few
+    # 1e-7 per operation, bias corrections formed in FP64), and the stored
+    # parameter is rounded to its own ulp
+    tol = lambda p: 2 * np.spacing(np.abs(p).astype(np.float32)).astype(np.float64) + 1e-5 * lr
     assert np.all(np.abs(d1 - d1r) <= tol(p1)), np.abs(d1 - d1r).max()
     assert np.all(np.abs(d2 - d2r) <= tol(p2)), np.abs(d2 - d2r).max()
     assert np.abs(d1r).max() > 0.5 * lr  # a real step was taken
