@@ -52,13 +52,18 @@ def parse():
     ap.add_argument("--no-side", action="store_true", help="skip the side-by-side precision")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
-    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="steps of the end-to-end run (0: the workload's own step count, "
+                         "at most 20000)")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the batched parameter sweep (sweep_256) in the default line")
     ap.add_argument("--sweep-steps", type=int, default=200,
                     help="timed batch steps of the sweep_256 measurement")
     ap.add_argument("--no-batch", action="store_true",
                     help="step each instance alone instead of as one batch")
+    ap.add_argument("--chunk-len", type=int, default=0,
+                    help="planes per x-chunk of every instance instead of the autotuner's choice "
+                         "(for profiling runs, where the tuner's timing trials are distorted)")
     return ap.parse_args()
 
 
@@ -178,7 +183,7 @@ def make_grids(fk, w, precision, stream):
 
 
 def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=True,
-             kernel_steps=50):
+             kernel_steps=50, chunk_len=0):
     """Time `steps` steps of the workload's instances after `warmup` steps,
     as users run them: each step a CUDA-graph replay (batch: one step-kernel
     launch per unit layout and one finalize launch for all instances, x-chunks
@@ -194,7 +199,12 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
     for g in grids:
         g.set_f(f0)
     b = fk.Batch(grids, stream) if batch else None
-    tuned = b.autotune(2) if b is not None else 0
+    tuned = 0
+    if b is not None:
+        if chunk_len > 0:
+            b.set_chunks([chunk_len] * len(grids))
+        else:
+            tuned = b.autotune(2)
 
     def advance(n):
         if b is not None:
@@ -429,7 +439,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     prec = fk.FK_F32 if args.precision == "f32" else fk.FK_F64
     res = time_arm(fk, torch, w, prec, f0, args.steps, args.warmup, dist, local,
-                   batch=not args.no_batch)
+                   batch=not args.no_batch, chunk_len=args.chunk_len)
     for g in res.pop("grids"):
         g.close()
     ms = reduce_over_ranks(res["ms"], dist, "max")
@@ -461,7 +471,8 @@ def run_ours(args):
             "ms_per_step": r2["ms"] / osteps, "steps": osteps,
             "roofline": roofline(r2, other, peak, peak_kind), "clocks": r2["clocks"]}}
     if not args.no_e2e:
-        e2e = e2e_arm(fk, torch, w, prec, f0, args.e2e_steps, batch=not args.no_batch)
+        e2e_steps = args.e2e_steps or min(int(w.get("steps", 100)), 20000)
+        e2e = e2e_arm(fk, torch, w, prec, f0, e2e_steps, batch=not args.no_batch)
         e2e["value"] = reduce_over_ranks(e2e["value"], dist, "sum")
         line["e2e"] = e2e
     if not args.no_sweep:

@@ -398,8 +398,10 @@ fk_status fk_batch_moments_collect(fk_batch *batch, int32_t slot, double *sigma,
 /* Autotuner: picks the x-chunk length (planes per work unit) of every size
  * bucket of the batch -- grids grouped by plane size and nx, each a power of
  * two -- by timing real steps: one trial of steps_per_trial >= 1 batch steps
- * per candidate length (4 planes up to the whole x range), bucket by bucket,
- * largest bucket first, keeping the fastest.  The trials advance every grid
+ * per candidate length (powers of two from 4 planes up to the whole x range,
+ * and the lengths that give the bucket about 1 to 12 whole waves of the
+ * GPU's unit slots), bucket by bucket, largest bucket first, keeping the
+ * fastest.  The trials advance every grid
  * (bitwise as fk_batch_step would); *steps_taken (may be NULL) receives how
  * many steps they took.  The v1-row tile of each grid is fixed by its shared-
  * memory plan: the most rows for which two CTAs fit on an SM, or, where each

@@ -681,8 +681,29 @@ fk_status fk_batch_autotune(fk_batch* b, int32_t steps_per_trial, int64_t* steps
   std::vector<int> keep = b->chunk_len;
   for (size_t oi = 0; oi < order.size() && s == FK_OK; oi++) {
     const int q = order[oi];
-    for (int L = kMinChunk; s == FK_OK; L *= 2) {
-      const int Lc = std::min(L, bmax_nx[q]);
+    // candidate chunk lengths: powers of two from kMinChunk up to the
+    // bucket's largest x range, and the lengths whose chunk count gives the
+    // bucket about a whole number k of waves of unit slots (equal units
+    // otherwise leave the last wave part-empty)
+    std::vector<int> cand;
+    for (int L = kMinChunk;; L *= 2) {
+      cand.push_back(std::min(L, bmax_nx[q]));
+      if (L >= bmax_nx[q]) break;
+    }
+    double row_units = 0.0;  // units of one chunk of every grid in the bucket
+    for (int i = 0; i < b->n; i++)
+      if (b->bucket[i] == q)
+        row_units += b->grids[i]->geom.n_tiles * (b->grids[i]->geom.half ? 0.5 : 1.0);
+    const double slots = (double)b->sms * b->per_sm;
+    for (int k = 1; k <= 12 && row_units > 0.0; k++) {
+      const int c = std::max(1, (int)std::lround(k * slots / row_units));
+      const int L = (bmax_nx[q] + c - 1) / c;
+      if (L >= kMinChunk && L <= bmax_nx[q]) cand.push_back(L);
+    }
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    for (size_t ci = 0; ci < cand.size() && s == FK_OK; ci++) {
+      const int Lc = cand[ci];
       bool changed = false;
       for (int i = 0; i < b->n; i++)
         if (b->bucket[i] == q) {
@@ -700,7 +721,6 @@ fk_status fk_batch_autotune(fk_batch* b, int32_t steps_per_trial, int64_t* steps
       }
       b->chunk_len = keep;
       b->dirty = true;
-      if (Lc >= bmax_nx[q]) break;
     }
   }
   cudaEventDestroy(e0);

@@ -51,6 +51,12 @@ static_assert(kHalfStages <= 32, "a producer lane per stage");
 template <int NT>
 __host__ __device__ constexpr int unit_stages() { return NT == kThreads ? kStages : kHalfStages; }
 constexpr int kVecPerThread = 8;         // 16-byte vectors per consumer thread and plane
+constexpr int kHalfVecPerThread32 = 4;   // the same for half units of FP32 grids
+// vectors per consumer thread and plane of a unit on NT threads, element size E
+template <int NT, int E>
+__host__ __device__ constexpr int unit_vectors() {
+  return (NT == kHalfThreads && E == 4) ? kHalfVecPerThread32 : kVecPerThread;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -261,7 +267,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   constexpr int NW = NT / 32;  // consumer warps
   constexpr int NS = unit_stages<NT>();  // stages of the ring
   constexpr int VEC = Vec<T>::N;
-  constexpr int M = kVecPerThread;
+  constexpr int M = unit_vectors<NT, (int)sizeof(T)>();
   const Geom& gm = a.geom;
   const size_t sbytes = stage_bytes<T>(gm.stage_elems);
   unsigned char* stage_base = smem;
@@ -410,12 +416,14 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
     struct Gathered {
       int k;       // plane (-1: the prime item, no sums)
       T lvt;       // this lane's share of the velocity-edge outflow
+      float wsf;   // lane w < NW, FP32 grids: warp w's density sum
       double ws[kWs];  // lane w < NW: warp w's sums (all four on a wall plane)
     };
     auto gather = [&](int q) -> Gathered {
       Gathered g;
       g.k = -1;
       g.lvt = (T)0;
+      g.wsf = 0.f;
 #pragma unroll
       for (int i = 0; i < kWs; i++) g.ws[i] = 0.0;
       if (prime && q == 0) return g;
@@ -439,7 +447,9 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         for (int r = lane; r < rows; r += 32) g.lvt += a2t * sb[(size_t)(r + rb) * pitch + nv2 - 1];
       if (lane < NW) {
         const double* ws = wsum + (st * kWarps + lane) * kWs;
-        g.ws[0] = ws[0];
+        // FP32 grids hand over their warp's density sum as a float
+        g.ws[0] = sizeof(T) == 4 ? (double)0 : ws[0];
+        if constexpr (sizeof(T) == 4) g.wsf = *reinterpret_cast<const float*>(ws);
         if (k == 0 || k == nx - 1) {
 #pragma unroll
           for (int i = 1; i < kWs; i++) g.ws[i] = ws[i];
@@ -454,14 +464,19 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       const double lv = (double)warp_sum(g.lvt);
       double sum[kWs] = {0.0, 0.0, 0.0, 0.0};
       const bool wall = k == 0 || k == nx - 1;
+      float sumf = 0.f;  // FP32 grids: the warps' density sums, added in FP32
 #pragma unroll
       for (int w = 0; w < NW; w++) {
-        sum[0] += __shfl_sync(0xffffffffu, g.ws[0], w);
+        if constexpr (sizeof(T) == 4)
+          sumf += __shfl_sync(0xffffffffu, g.wsf, w);
+        else
+          sum[0] += __shfl_sync(0xffffffffu, g.ws[0], w);
         if (wall) {
 #pragma unroll
           for (int i = 1; i < kWs; i++) sum[i] += __shfl_sync(0xffffffffu, g.ws[i], w);
         }
       }
+      if constexpr (sizeof(T) == 4) sum[0] = (double)sumf;  // one conversion per plane
       if (lane == 0) {
         a.part.n[(size_t)k * nt + t] = sum[0];
         a.part.lv[(size_t)k * nt + t] = lv;
@@ -672,7 +687,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       double* wsl = wsum + (st * kWarps + warp) * kWs;
       if (sizeof(T) == 4) {
         const T ws = warp_sum(sum_n);
-        if (lane == 0) wsl[0] = (double)ws;
+        if (lane == 0) *reinterpret_cast<float*>(wsl) = ws;  // the producer converts once
       } else {
         // fold the lanes' (hi, error) pairs in FP32 with TwoSum, convert once
         float lo = sc_ + sl_;
@@ -789,7 +804,9 @@ int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per
                      bool half) {
   const int esize = precision == FK_F32 ? 4 : 8;
   const int vec = 16 / esize;
-  const int cells = (half ? kHalfThreads : kThreads) * kVecPerThread * vec;
+  const int cells = half ? kHalfThreads * (esize == 4 ? unit_vectors<kHalfThreads, 4>()
+                                                    : unit_vectors<kHalfThreads, 8>()) * vec
+                         : kThreads * kVecPerThread * vec;
   if (pitch > cells) return 0;
   int rows = cells / pitch;
   if (rows > kMaxTileRows) rows = kMaxTileRows;

@@ -2,11 +2,12 @@
 
 An FP32 grid stores and advects f in FP32; its moments, fluxes, surface
 charge and ledger are FP64 (Sec. 2, Eqs. 12-14, 18).  The streaming step
-kernel sums f^{n+1} in FP32 up to a warp: each thread adds its cells of a
-plane (at most 8 vectors of 4) in sequence, the 32 lanes fold in a 5-level
-tree, and everything above a warp is FP64.  All terms are >= 0, so the
-relative error per plane is at most (31 + 5) * 2^-24 (about 2.1e-6); the
-direct-load kernel keeps a compensated FP32 sum per thread.  Here n_e(x) of
+kernel sums f^{n+1} in FP32: each thread adds its cells of a plane (at
+most 8 vectors of 4) in sequence, the 32 lanes fold in a 5-level tree, the
+producer warp adds the (at most 7) warps' sums, and the plane's sum is
+converted to FP64 once.  All terms are >= 0, so the relative error per plane
+is at most (31 + 5 + 6) * 2^-24 (about 2.5e-6); the direct-load kernel
+keeps a compensated FP32 sum per thread.  Here n_e(x) of
 fk_moments and the ledger's N are compared with FP64 numpy sums of the same
 FP32 state read back with fk_get_f32.  The FP32 ledger (every cumulative
 term, and its closure) is compared with the FP64 oracle over 300 strongly
@@ -23,7 +24,7 @@ from test_gpu_parity import make_pair, strong_physics
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
-BOUND = 36 * U32  # 31 sequential additions per thread, 5 tree levels per warp
+BOUND = 42 * U32  # 31 additions per thread, 5 tree levels per warp, 6 over warps
 
 
 @pytest.fixture(scope="module", autouse=True)
