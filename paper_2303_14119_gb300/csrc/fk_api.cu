@@ -335,7 +335,8 @@ fk_status plan_geometry(fk_grid* g) {
   m.n_chunks = 1;
   m.chunk_len = g->nx;
   if (g->use_stream) {
-    const int per_sm = stream_ctas_per_sm(g->prec, stream_cta_smem_bytes(g->prec, m, g->pitch));
+    const int per_sm = stream_ctas_per_sm(g->prec, stream_cta_smem_bytes(g->prec, m, g->pitch),
+                                          m.half ? kLayoutHalf : kLayoutWhole);
     if (per_sm <= 0) {
       g->use_stream = false;
       m.half = 0;

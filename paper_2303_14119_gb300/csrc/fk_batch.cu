@@ -53,7 +53,8 @@ struct fk_batch {
   int n_fblk = 0;
   size_t smem = 0;             // dynamic shared memory per CTA (whole-CTA units)
   int half_bytes = 0;          // shared memory of one half unit's region
-  int per_sm = 0, sms = 0;
+  int per_sm = 0, sms = 0;      // CTAs per SM (the smaller of the two layouts), SMs
+  int per_sm_whole = 0, per_sm_half = 0;  // CTAs per SM of each unit layout's launch
   bool dirty = true;           // units / arguments must be re-uploaded
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaEvent_t done = nullptr;  // recorded after the last enqueued batch step
@@ -168,7 +169,8 @@ void split_units(const fk_batch* b, const std::vector<int2>& units, std::vector<
 void default_chunks(fk_batch* b) {
   bool all_half = true;
   for (const fk_grid* g : b->grids) all_half = all_half && g->geom.half;
-  const double slots = (double)b->sms * b->per_sm * (all_half ? 2 : 1);  // unit slots
+  const double slots =
+      (double)b->sms * (all_half ? 2.0 * b->per_sm_half : (double)b->per_sm_whole);  // unit slots
   const double target = b->cells / (kDefaultWaves * slots);
   for (int i = 0; i < b->n; i++) {
     const fk_grid* g = b->grids[i];
@@ -439,7 +441,14 @@ fk_status fk_batch_create(fk_grid* const* grids, int32_t n, void* cuda_stream, f
     }
     b->cur0[i] = g->enq_cur;
   }
-  b->per_sm = stream_ctas_per_sm(b->prec, std::max(b->smem, 2 * (size_t)b->half_bytes));
+  {
+    bool any_whole = false, any_half = false;
+    for (const fk_grid* g : b->grids) (g->geom.half ? any_half : any_whole) = true;
+    b->per_sm_whole = any_whole ? stream_ctas_per_sm(b->prec, b->smem, kLayoutWhole) : 1 << 30;
+    b->per_sm_half =
+        any_half ? stream_ctas_per_sm(b->prec, 2 * (size_t)b->half_bytes, kLayoutHalf) : 1 << 30;
+    b->per_sm = std::min(b->per_sm_whole, b->per_sm_half);
+  }
   if (b->per_sm <= 0) {
     free_batch(b);
     return bfail(nullptr, FK_EINVAL, "the grids' shared-memory plans do not fit an SM");
@@ -691,10 +700,15 @@ fk_status fk_batch_autotune(fk_batch* b, int32_t steps_per_trial, int64_t* steps
       if (L >= bmax_nx[q]) break;
     }
     double row_units = 0.0;  // units of one chunk of every grid in the bucket
+    bool half_bucket = true;
     for (int i = 0; i < b->n; i++)
-      if (b->bucket[i] == q)
-        row_units += b->grids[i]->geom.n_tiles * (b->grids[i]->geom.half ? 0.5 : 1.0);
-    const double slots = (double)b->sms * b->per_sm;
+      if (b->bucket[i] == q) {
+        row_units += b->grids[i]->geom.n_tiles;
+        half_bucket = half_bucket && b->grids[i]->geom.half;
+      }
+    // unit slots of the launch the bucket's units run in
+    const double slots =
+        (double)b->sms * (half_bucket ? 2.0 * b->per_sm_half : (double)b->per_sm_whole);
     for (int k = 1; k <= 12 && row_units > 0.0; k++) {
       const int c = std::max(1, (int)std::lround(k * slots / row_units));
       const int L = (bmax_nx[q] + c - 1) / c;

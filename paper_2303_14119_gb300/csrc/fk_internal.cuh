@@ -194,13 +194,15 @@ cudaError_t launch_step_stream(const StepArgs& a, int precision, bool bgk, cudaS
 // Rows per tile of the streaming kernel for this precision and row pitch
 // so that two CTAs fit on an SM (half: a unit on half a CTA, two units per
 // CTA; 0 if a row does not fit); the shared memory of one unit, of one
-// half-CTA region and of a CTA of grid geometry gm; resident CTAs per SM.
+// half-CTA region and of a CTA of grid geometry gm; resident CTAs per SM of
+// the kernels of a unit layout (kLayoutWhole, kLayoutHalf) or of all.
 int stream_tile_rows(int precision, int pitch, int smem_per_sm, int reserved_per_block,
                      bool half);
 size_t stream_smem_bytes(int precision, int stage_elems, int pitch);
 size_t stream_half_bytes(int precision, int stage_elems, int pitch);
 size_t stream_cta_smem_bytes(int precision, const Geom& gm, int pitch);
-int stream_ctas_per_sm(int precision, size_t smem_bytes);
+enum StreamLayout { kLayoutAll = 0, kLayoutWhole = 1, kLayoutHalf = 2 };
+int stream_ctas_per_sm(int precision, size_t smem_bytes, int layout);
 // Batched streaming step: one launch over the whole-CTA units, CTA b
 // running units[b] = (grid index into inst, tile + n_tiles * chunk of that
 // grid) with smem_bytes >= every such grid's stream_smem_bytes; then one

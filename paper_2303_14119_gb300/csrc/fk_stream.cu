@@ -565,6 +565,8 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   }
   const T c2 = (T)p.c2;
   const T a2 = c2 < (T)0 ? -c2 : c2;
+  // the source band in registers: the march's stores could alias Params
+  const int band_lo = p.band_lo, band_hi = p.band_hi;
   const T* srcbase = sizeof(T) == 8 ? (const T*)a.tab.src : (const T*)a.tab.src32;
 
   for (int q = 0; q < n_items; q++) {
@@ -575,7 +577,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
     // before waiting for the stage, so their latency overlaps the wait
     const float c1f = a.c1_32[k];
     const T a1 = c1f == 0.f ? (T)0 : (sizeof(T) == 8 ? (T)fabs(a.c1[k]) : (T)fabsf(c1f));
-    const bool band = compute && k >= p.band_lo && k < p.band_hi;
+    const bool band = compute && k >= band_lo && k < band_hi;
     // source term: FP32 grids rebuild it from the separable factors in
     // shared memory, FP64 grids load the 2D table in the update loop
     // collision term (Eq. 3) of FP32 grids: dt nu_k and dt nu_k n_k (FP64
@@ -744,7 +746,7 @@ __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(const __grid_con
 // One grid, half units: CTA b runs units 2b and 2b + 1 on its two halves,
 // each in a region of half_region_bytes.
 template <typename T, bool PADDED, bool BGK>
-__global__ void __launch_bounds__(kBlock, 2)
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 2)
 step_stream_half_kernel(const __grid_constant__ StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nt = a.geom.n_tiles;
@@ -778,7 +780,7 @@ step_stream_batch_kernel(const BatchInst* __restrict__ inst, const int2* __restr
 // pairs[b].z (none if pairs[b].z < 0) on the rest, each half in a region of
 // half_bytes whose slot receives that grid's arguments.
 template <typename T, bool PADDED, bool BGK>
-__global__ void __launch_bounds__(kBlock, 2)
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 2)
 step_stream_batch_half_kernel(const BatchInst* __restrict__ inst, const int4* __restrict__ pairs,
                               int half_bytes) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -845,56 +847,51 @@ size_t stream_cta_smem_bytes(int precision, const Geom& gm, int pitch) {
 namespace {
 // allow the device's largest opt-in shared memory for kernel k and ask how
 // many CTAs of smem_bytes fit on an SM
+// allow the device's largest opt-in shared memory for kernel k and ask how
+// many CTAs of smem_bytes fit on an SM; *best keeps the smallest answer of
+// the kernels that count (count = false: the attribute is only set)
 template <typename K>
-cudaError_t fit_kernel(K k, int optin, size_t smem_bytes, int* best) {
+cudaError_t fit_kernel(K k, int optin, size_t smem_bytes, bool count, int* best) {
   int n = 0;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kBlock, smem_bytes);
-  if (e == cudaSuccess && n < *best) *best = n;
+  if (e == cudaSuccess && count && n < *best) *best = n;
+  return e;
+}
+template <typename T, bool P, bool B>
+cudaError_t fit_four(int optin, size_t smem_bytes, bool whole, bool half, int* best) {
+  cudaError_t e = fit_kernel(step_stream_kernel<T, P, B>, optin, smem_bytes, whole, best);
+  if (e == cudaSuccess) e = fit_kernel(step_stream_batch_kernel<T, P, B>, optin, smem_bytes, whole, best);
+  if (e == cudaSuccess) e = fit_kernel(step_stream_half_kernel<T, P, B>, optin, smem_bytes, half, best);
+  if (e == cudaSuccess)
+    e = fit_kernel(step_stream_batch_half_kernel<T, P, B>, optin, smem_bytes, half, best);
   return e;
 }
 template <typename T>
-int ctas_per_sm(int optin, size_t smem_bytes) {
+int ctas_per_sm(int optin, size_t smem_bytes, int layout) {
+  const bool whole = layout != kLayoutHalf, half = layout != kLayoutWhole;
   int best = 1 << 30;
-  cudaError_t e = fit_kernel(step_stream_kernel<T, false, false>, optin, smem_bytes, &best);
-  if (e == cudaSuccess) e = fit_kernel(step_stream_kernel<T, true, false>, optin, smem_bytes, &best);
-  if (e == cudaSuccess) e = fit_kernel(step_stream_kernel<T, false, true>, optin, smem_bytes, &best);
-  if (e == cudaSuccess) e = fit_kernel(step_stream_kernel<T, true, true>, optin, smem_bytes, &best);
-  if (e == cudaSuccess)
-    e = fit_kernel(step_stream_batch_kernel<T, false, false>, optin, smem_bytes, &best);
-  if (e == cudaSuccess)
-    e = fit_kernel(step_stream_batch_kernel<T, true, false>, optin, smem_bytes, &best);
-  if (e == cudaSuccess)
-    e = fit_kernel(step_stream_batch_kernel<T, false, true>, optin, smem_bytes, &best);
-  if (e == cudaSuccess)
-    e = fit_kernel(step_stream_batch_kernel<T, true, true>, optin, smem_bytes, &best);
-  if (e == cudaSuccess) e = fit_kernel(step_stream_half_kernel<T, false, false>, optin, smem_bytes, &best);
-  if (e == cudaSuccess) e = fit_kernel(step_stream_half_kernel<T, true, false>, optin, smem_bytes, &best);
-  if (e == cudaSuccess) e = fit_kernel(step_stream_half_kernel<T, false, true>, optin, smem_bytes, &best);
-  if (e == cudaSuccess) e = fit_kernel(step_stream_half_kernel<T, true, true>, optin, smem_bytes, &best);
-  if (e == cudaSuccess)
-    e = fit_kernel(step_stream_batch_half_kernel<T, false, false>, optin, smem_bytes, &best);
-  if (e == cudaSuccess)
-    e = fit_kernel(step_stream_batch_half_kernel<T, true, false>, optin, smem_bytes, &best);
-  if (e == cudaSuccess)
-    e = fit_kernel(step_stream_batch_half_kernel<T, false, true>, optin, smem_bytes, &best);
-  if (e == cudaSuccess)
-    e = fit_kernel(step_stream_batch_half_kernel<T, true, true>, optin, smem_bytes, &best);
+  cudaError_t e = fit_four<T, false, false>(optin, smem_bytes, whole, half, &best);
+  if (e == cudaSuccess) e = fit_four<T, true, false>(optin, smem_bytes, whole, half, &best);
+  if (e == cudaSuccess) e = fit_four<T, false, true>(optin, smem_bytes, whole, half, &best);
+  if (e == cudaSuccess) e = fit_four<T, true, true>(optin, smem_bytes, whole, half, &best);
   return e == cudaSuccess ? best : 0;
 }
 }  // namespace
 
-int stream_ctas_per_sm(int precision, size_t smem_bytes) {
+int stream_ctas_per_sm(int precision, size_t smem_bytes, int layout) {
   // the attribute is per kernel, shared by every grid and batch: allow the
-  // device's largest opt-in size once, and ask the occupancy of this size
-  // (the smallest over the single-grid and batched variants)
+  // device's largest opt-in size on every variant, and ask the occupancy of
+  // this size (the smallest over the single-grid and batched variants of
+  // the layout asked for; the half-unit kernels of FP32 grids fit more
+  // CTAs on an SM than the whole-CTA ones)
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return 0;
   if (smem_bytes > (size_t)optin) return 0;
-  return precision == FK_F32 ? ctas_per_sm<float>(optin, smem_bytes)
-                             : ctas_per_sm<double>(optin, smem_bytes);
+  return precision == FK_F32 ? ctas_per_sm<float>(optin, smem_bytes, layout)
+                             : ctas_per_sm<double>(optin, smem_bytes, layout);
 }
 
 namespace {
