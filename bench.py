@@ -100,9 +100,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(precision):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu
-    summary, if its source hash matches the current kernel source."""
+def kernel_traffic(workload, precision):
+    """Per-launch DRAM bytes of the dominant step kernel of `workload` at
+    `precision` from the committed ncu summaries, if there is a record for
+    that pair and its source hash matches the current kernel source."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -114,7 +115,7 @@ def kernel_traffic(precision):
             vals[k.strip()] = v.strip()
     if vals.get("source_hash") != _build.source_hash():
         return None
-    key = "bytes_per_launch_%s" % precision
+    key = "%s_%s" % (workload, precision)
     return float(vals[key]) if key in vals else None
 
 
@@ -396,7 +397,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 * 2 / 1e12
 DFMA_PER_CELL = 4  # the FP64 update is four fused multiply-adds per cell
 
 
-def roofline(res, precision, peak, peak_kind):
+def roofline(res, precision, peak, peak_kind, workload):
     bpc = 4 if precision == "f32" else 8
     if res["launches"] == 0:
         return None
@@ -404,7 +405,7 @@ def roofline(res, precision, peak, peak_kind):
     alg_bytes = 2 * bpc * res["cells_per_launch"]  # one read of f^n, one write of f^{n+1}
     achieved = alg_bytes / avg_s / 1e9
     hbm = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-           "frac": round(achieved / peak, 4), "traffic": kernel_traffic(precision),
+           "frac": round(achieved / peak, 4), "traffic": kernel_traffic(workload, precision),
            "peak_kind": "%s (copy bandwidth)" % peak_kind,
            "kernel": "fused upwind step", "avg_launch_us": round(avg_s * 1e6, 2),
            "alg_bytes_per_launch": alg_bytes}
@@ -453,7 +454,7 @@ def run_ours(args):
                    "cells_per_instance": res["cells"], "precision_storage": args.precision,
                    "accumulators": "f64", "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roofline(res, args.precision, peak, peak_kind),
+        "roofline": roofline(res, args.precision, peak, peak_kind, args.workload),
         "kernel_plan": res["kernel"],
         "gpu_launches": res["gpu_launches"],
         "clocks": res["clocks"],
@@ -469,7 +470,8 @@ def run_ours(args):
         line["side_by_side"] = {other: {
             "value": world * r2["n_inst"] * r2["cells"] * osteps / (r2["ms"] / 1e3),
             "ms_per_step": r2["ms"] / osteps, "steps": osteps,
-            "roofline": roofline(r2, other, peak, peak_kind), "clocks": r2["clocks"]}}
+            "roofline": roofline(r2, other, peak, peak_kind, args.workload),
+            "clocks": r2["clocks"]}}
     if not args.no_e2e:
         e2e_steps = args.e2e_steps or min(int(w.get("steps", 100)), 20000)
         e2e = e2e_arm(fk, torch, w, prec, f0, e2e_steps, batch=not args.no_batch)
@@ -596,7 +598,7 @@ def measure_sweep(fk, torch, workload, precision, steps, warmup, dist, local, wo
     seq = world * len(ins) * 3600.0 / (ms_step_s * per_inst / 1e3)
     peak, peak_kind = measured_peaks()
     res = dict(launches=launches, kernel_ms=kms, cells_per_launch=cells)
-    roof = roofline(res, precision, peak, peak_kind)
+    roof = roofline(res, precision, peak, peak_kind, workload)
     if roof is not None:
         if info["step_launches"] == 1:
             roof["kernel"] = "batched fused upwind step (all %d instances per launch)" % len(ins)
@@ -604,7 +606,7 @@ def measure_sweep(fk, torch, workload, precision, steps, warmup, dist, local, wo
             roof["kernel"] = ("batched fused upwind step (all %d instances per step: one launch "
                               "of whole-CTA units, one of half-CTA units, timed together)"
                               % len(ins))
-        roof["traffic"] = None
+            roof["traffic"] = None  # a record covers one launch
     return {
         "metric": "batched instances/hr (%d steps per instance)" % per_inst, "value": value,
         "unit": "instances/hr", "n_gpus": world, "steps": steps, "warmup": warmup,

@@ -51,7 +51,7 @@ static_assert(kHalfStages <= 32, "a producer lane per stage");
 template <int NT>
 __host__ __device__ constexpr int unit_stages() { return NT == kThreads ? kStages : kHalfStages; }
 constexpr int kVecPerThread = 8;         // 16-byte vectors per consumer thread and plane
-constexpr int kHalfVecPerThread32 = 4;   // the same for half units of FP32 grids
+constexpr int kHalfVecPerThread32 = 3;   // the same for half units of FP32 grids
 // vectors per consumer thread and plane of a unit on NT threads, element size E
 template <int NT, int E>
 __host__ __device__ constexpr int unit_vectors() {
