@@ -382,15 +382,19 @@ fk_status fk_batch_moments(fk_batch *batch, double *sigma, double *gamma_pe, dou
                            double *n_e, double *Ex);
 
 /* Pipelined form of fk_batch_moments, so that a loop can read the moments
- * of step n while step n + 1 runs.  fk_batch_moments_enqueue queues, on the
- * batch's stream after the work enqueued so far, copies of every grid's
- * sigma, Gamma_pe, Gamma_see, n_e and E_x into one of two pinned host slots
- * the batch owns (slot 0 or 1; allocated on its first use) and returns at
- * once.  fk_batch_moments_collect waits for that slot's copies only (not
- * for later work) and unpacks them as fk_batch_moments does.  A slot holds
- * one set: enqueue on a full slot, or collect from an empty one, returns
- * FK_ESTATE.  The values are those of the state the copies were queued
- * after; sticky device errors are reported by fk_batch_sync. */
+ * of step n while step n + 1 runs.  fk_batch_moments_enqueue queues, after
+ * the work enqueued on the batch's stream so far, one small kernel that
+ * packs every grid's sigma, Gamma_pe, Gamma_see, n_e and E_x into one of two
+ * device slots and one copy of that slot into its pinned host twin (slot 0
+ * or 1), both on a copy stream the batch owns (buffers, events and the copy
+ * stream are allocated on first use), and returns at once.  The next batch
+ * step's step kernel runs beside them; its finalize, the first kernel to
+ * overwrite what the packing kernel reads, waits for that kernel (not for
+ * the copy).  fk_batch_moments_collect waits for that slot's copy only (not
+ * for later work) and unpacks it as fk_batch_moments does.  A slot holds one
+ * set: enqueue on a full slot, or collect from an empty one, returns
+ * FK_ESTATE.  The values are those of the state after the work enqueued
+ * before the call; sticky device errors are reported by fk_batch_sync. */
 fk_status fk_batch_moments_enqueue(fk_batch *batch, int32_t slot);
 fk_status fk_batch_moments_collect(fk_batch *batch, int32_t slot, double *sigma,
                                    double *gamma_pe, double *gamma_see, double *n_e, double *Ex);

@@ -26,6 +26,16 @@ constexpr int kBatchMaxTimed = 8192;  // step-kernel launches timed between read
 constexpr int kMinChunk = 4;          // fewest planes per x-chunk the planner picks
 constexpr double kDefaultWaves = 4.0; // default plan: about this many CTA waves
 
+// Where one grid's moments live, and where its n_e / E_x go in a packed slot.
+struct MomentSrc {
+  const DevState* st;
+  const double* ne;
+  const double* ex;
+  long long off;  // planes of the grids before it
+  int nx;
+  int pad;
+};
+
 }  // namespace
 
 struct fk_batch {
@@ -62,11 +72,21 @@ struct fk_batch {
   std::vector<cudaEvent_t> ev; // pairs around the step kernel
   int ev_used = 0;
   // pipelined moment read-back (fk_batch_moments_enqueue / _collect): two
-  // pinned slots, each the grids' DevState then n_e and E_x of every grid
+  // slots, each (sigma, Gamma_pe, Gamma_see) of every grid, then n_e and
+  // E_x of every grid, packed on the device by one gather kernel and
+  // brought to pinned host memory by one copy, both on copy_stream, so that
+  // they run beside the next step kernel; the next finalize (the first
+  // kernel to overwrite what the gather reads) waits for `pending`
   void* h_slot[2] = {nullptr, nullptr};
-  cudaEvent_t slot_ev[2] = {nullptr, nullptr};
+  double* d_slot[2] = {nullptr, nullptr};
+  cudaEvent_t gathered[2] = {nullptr, nullptr};  // the gather kernel has run
+  cudaEvent_t slot_ev[2] = {nullptr, nullptr};   // the slot's copy has landed
   bool slot_full[2] = {false, false};
   size_t sum_nx = 0;
+  MomentSrc* d_msrc = nullptr;  // [n] where each grid's moments live
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t fin_ev = nullptr;   // the batch's work up to an enqueue
+  cudaEvent_t pending = nullptr;  // the last gather, not yet waited for
   std::string err;
 };
 
@@ -90,6 +110,25 @@ fk_status bcuda_fail(fk_batch* b, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                                  \
     if (e_ != cudaSuccess) return bcuda_fail((b), e_, #call); \
   } while (0)
+
+// Pack every grid's sigma, Gamma_pe and Gamma_see (3 doubles per grid), then
+// the n_e of all grids, then their E_x, into out; block i copies grid i.
+__global__ void __launch_bounds__(256)
+gather_moments_kernel(const MomentSrc* __restrict__ src, int n, long long sum_nx,
+                      double* __restrict__ out) {
+  const MomentSrc m = src[blockIdx.x];
+  if (threadIdx.x == 0) {
+    out[3 * (size_t)blockIdx.x] = m.st->sigma;
+    out[3 * (size_t)blockIdx.x + 1] = m.st->g_pe;
+    out[3 * (size_t)blockIdx.x + 2] = m.st->g_see;
+  }
+  double* ne = out + 3 * (size_t)n + m.off;
+  double* ex = ne + sum_nx;
+  for (int k = threadIdx.x; k < m.nx; k += blockDim.x) {
+    ne[k] = m.ne[k];
+    ex[k] = m.ex[k];
+  }
+}
 
 int chunks_of(int nx, int len) { return (nx + len - 1) / len; }
 
@@ -264,6 +303,13 @@ cudaError_t enqueue_batch_step(fk_batch* b, int p, cudaStream_t s, cudaEvent_t e
     e = launch_step_stream_batch(inst, b->d_units, b->n_units, b->d_pairs, b->n_pairs, b->prec,
                                  b->padded, b->bgk, b->smem, b->half_bytes, s);
   if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, s);
+  // a moment gather queued before this step may still read the moments and
+  // scalars the finalize overwrites (never inside a capture: the graph's
+  // launch waits instead)
+  if (e == cudaSuccess && b->pending && s == b->stream) {
+    e = cudaStreamWaitEvent(s, b->pending, 0);
+    b->pending = nullptr;
+  }
   if (e == cudaSuccess) e = launch_finalize_batch(inst, b->d_fblk, b->n_fblk, s);
   return e;
 }
@@ -308,6 +354,10 @@ fk_status enqueue_steps(fk_batch* b, long long n) {
         const fk_status s = build_batch_graph(b, p);
         if (s != FK_OK) return s;
       }
+      if (b->pending) {
+        BK_CUDA(b, cudaStreamWaitEvent(b->stream, b->pending, 0));
+        b->pending = nullptr;
+      }
       BK_CUDA(b, cudaGraphLaunch(b->graph[p], b->stream));
       b->steps += kBatchGraphSteps;  // even: the parity is unchanged
       n -= kBatchGraphSteps;
@@ -326,6 +376,7 @@ void free_batch(fk_batch* b) {
   if (!b) return;
   cudaSetDevice(b->dev);
   if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->copy_stream) cudaStreamSynchronize(b->copy_stream);  // a gather or copy in flight
   drop_graphs(b);
   for (fk_grid* g : b->grids) {
     if (!g || g->batch != b) continue;
@@ -341,8 +392,13 @@ void free_batch(fk_batch* b) {
   if (b->done) cudaEventDestroy(b->done);
   for (int q = 0; q < 2; q++) {
     if (b->h_slot[q]) cudaFreeHost(b->h_slot[q]);
+    if (b->d_slot[q]) cudaFree(b->d_slot[q]);
+    if (b->gathered[q]) cudaEventDestroy(b->gathered[q]);
     if (b->slot_ev[q]) cudaEventDestroy(b->slot_ev[q]);
   }
+  if (b->d_msrc) cudaFree(b->d_msrc);
+  if (b->fin_ev) cudaEventDestroy(b->fin_ev);
+  if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -558,28 +614,42 @@ fk_status fk_batch_moments_enqueue(fk_batch* b, int32_t slot) {
   if (!b) return FK_EINVAL;
   if (slot != 0 && slot != 1) return bfail(b, FK_EINVAL, "slot must be 0 or 1");
   BK_CUDA(b, cudaSetDevice(b->dev));
-  if (!b->h_slot[slot]) {  // first use of the slot: its pinned buffer and event
+  if (!b->d_msrc) {  // first use: the grids' source pointers and the side stream
+    std::vector<MomentSrc> src(b->n);
     size_t nx = 0;
-    for (const fk_grid* g : b->grids) nx += g->nx;
+    for (int i = 0; i < b->n; i++) {
+      const fk_grid* g = b->grids[i];
+      src[i] = MomentSrc{g->d_st, g->d_ne, g->d_Ex, (long long)nx, g->nx, 0};
+      nx += g->nx;
+    }
     b->sum_nx = nx;
-    BK_CUDA(b, cudaMallocHost(&b->h_slot[slot], b->n * sizeof(DevState) + 2 * nx * sizeof(double)));
+    BK_CUDA(b, cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking));
+    BK_CUDA(b, cudaEventCreateWithFlags(&b->fin_ev, cudaEventDisableTiming));
+    BK_CUDA(b, cudaMalloc(&b->d_msrc, src.size() * sizeof(MomentSrc)));
+    BK_CUDA(b, cudaMemcpy(b->d_msrc, src.data(), src.size() * sizeof(MomentSrc),
+                          cudaMemcpyHostToDevice));
+  }
+  const size_t bytes = (3 * (size_t)b->n + 2 * b->sum_nx) * sizeof(double);
+  if (!b->h_slot[slot]) {  // first use of the slot: its buffers and events
+    BK_CUDA(b, cudaMallocHost(&b->h_slot[slot], bytes));
+    BK_CUDA(b, cudaMalloc(&b->d_slot[slot], bytes));
+    BK_CUDA(b, cudaEventCreateWithFlags(&b->gathered[slot], cudaEventDisableTiming));
     BK_CUDA(b, cudaEventCreateWithFlags(&b->slot_ev[slot], cudaEventDisableTiming));
   }
   if (b->slot_full[slot]) return bfail(b, FK_ESTATE, "slot holds uncollected moments");
-  DevState* hst = static_cast<DevState*>(b->h_slot[slot]);
-  double* hne = reinterpret_cast<double*>(hst + b->n);
-  double* hex = hne + b->sum_nx;
-  size_t off = 0;
-  for (int i = 0; i < b->n; i++) {
-    const fk_grid* g = b->grids[i];
-    const size_t vb = (size_t)g->nx * sizeof(double);
-    BK_CUDA(b, cudaMemcpyAsync(hst + i, g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost,
-                               b->stream));
-    BK_CUDA(b, cudaMemcpyAsync(hne + off, g->d_ne, vb, cudaMemcpyDeviceToHost, b->stream));
-    BK_CUDA(b, cudaMemcpyAsync(hex + off, g->d_Ex, vb, cudaMemcpyDeviceToHost, b->stream));
-    off += g->nx;
-  }
-  BK_CUDA(b, cudaEventRecord(b->slot_ev[slot], b->stream));
+  // the slot's previous copy has landed (it was collected), so its device
+  // buffer is free; the gather reads the state of the work enqueued so far
+  // (and only reads it: the next step kernel may run beside it)
+  BK_CUDA(b, cudaEventRecord(b->fin_ev, b->stream));
+  BK_CUDA(b, cudaStreamWaitEvent(b->copy_stream, b->fin_ev, 0));
+  gather_moments_kernel<<<b->n, 256, 0, b->copy_stream>>>(b->d_msrc, b->n,
+                                                          (long long)b->sum_nx, b->d_slot[slot]);
+  BK_CUDA(b, cudaGetLastError());
+  BK_CUDA(b, cudaEventRecord(b->gathered[slot], b->copy_stream));
+  b->pending = b->gathered[slot];  // gathers run in order: the last covers the earlier ones
+  BK_CUDA(b, cudaMemcpyAsync(b->h_slot[slot], b->d_slot[slot], bytes, cudaMemcpyDeviceToHost,
+                             b->copy_stream));
+  BK_CUDA(b, cudaEventRecord(b->slot_ev[slot], b->copy_stream));
   b->slot_full[slot] = true;
   return FK_OK;
 }
@@ -592,13 +662,13 @@ fk_status fk_batch_moments_collect(fk_batch* b, int32_t slot, double* sigma, dou
   BK_CUDA(b, cudaSetDevice(b->dev));
   BK_CUDA(b, cudaEventSynchronize(b->slot_ev[slot]));
   b->slot_full[slot] = false;
-  const DevState* hst = static_cast<const DevState*>(b->h_slot[slot]);
-  const double* hne = reinterpret_cast<const double*>(hst + b->n);
+  const double* hs = static_cast<const double*>(b->h_slot[slot]);
+  const double* hne = hs + 3 * (size_t)b->n;
   const double* hex = hne + b->sum_nx;
   for (int i = 0; i < b->n; i++) {
-    if (sigma) sigma[i] = hst[i].sigma;
-    if (gamma_pe) gamma_pe[i] = hst[i].g_pe;
-    if (gamma_see) gamma_see[i] = hst[i].g_see;
+    if (sigma) sigma[i] = hs[3 * (size_t)i];
+    if (gamma_pe) gamma_pe[i] = hs[3 * (size_t)i + 1];
+    if (gamma_see) gamma_see[i] = hs[3 * (size_t)i + 2];
   }
   if (n_e) memcpy(n_e, hne, b->sum_nx * sizeof(double));
   if (Ex) memcpy(Ex, hex, b->sum_nx * sizeof(double));

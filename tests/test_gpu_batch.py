@@ -300,3 +300,26 @@ def test_pipelined_moments_equal_the_blocking_getter_step_by_step():
             assert np.array_equal(x, y)
     for g in a + b:
         g.close()
+
+
+def test_pipelined_moments_are_those_of_the_step_they_followed():
+    """The packing kernel runs in order with the batch's steps and the copy
+    on the batch's own copy stream: moments enqueued after step 3 and
+    collected after 33 more steps (a graph replay among them) are step 3's."""
+    a, b = twins(fk.FK_F64, SHAPES[:3])
+    nx = sum(g.shape[0] for g in a)
+    with fk.Batch(a) as ba, fk.Batch(b) as bb:
+        ba.step(3)
+        ba.moments_enqueue(1)
+        ba.step(33)
+        ne, ex = np.empty(nx), np.empty(nx)
+        got = ba.moments_collect(1, ne, ex)[:3] + (ne, ex)
+        bb.step(3)
+        ne, ex = np.empty(nx), np.empty(nx)
+        ref = bb.moments(ne, ex)[:3] + (ne, ex)
+        for x, y in zip(got, ref):
+            assert np.array_equal(x, y)
+        bb.step(33)
+        assert np.array_equal(ba.moments()[0], bb.moments()[0])
+    for g in a + b:
+        g.close()

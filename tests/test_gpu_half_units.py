@@ -109,6 +109,40 @@ def test_per_step_parity_all_terms(half, prec, tol, monkeypatch):
     g.close()
 
 
+@pytest.mark.parametrize("half", [True, False])
+@pytest.mark.parametrize("prec,tol", [(fk.FK_F64, 1e-12), (fk.FK_F32, 3e-7)])
+def test_halo_zero_row_then_bulk_copy_in_one_stage(half, prec, tol, monkeypatch):
+    """Gauss's law makes E_x fall with x, so c_1 < 0 on the planes next to
+    the wall and c_1 > 0 past the zero of E_x.  On a plane with c_1 < 0 the
+    producer zero-fills the halo row after the last v1 tile (i1 = nv1); the
+    same stage comes back 4 planes later, where c_1 > 0 and the bulk copy of
+    the tile lands on that row.  With one chunk per tile (a one-grid batch,
+    chunk length nx) the zero of E_x lies inside every unit's ring, in both
+    layouts, and each step must still match the oracle."""
+    layout(monkeypatch, half)
+    shape = (48, 40, 30)
+    g, o = setup(shape, prec, 41)
+    assert g.info()["units_per_cta"] == (2 if half else 1)
+    ex = g.moments()[1]
+    k0 = int(np.argmax(ex < 0))  # first plane with c_1 > 0
+    assert ex[0] > 0 and 8 <= k0 <= shape[0] - 8, (k0, ex[0])
+    with fk.Batch([g]) as b:
+        b.set_chunks([shape[0]])
+        assert list(b.chunks()) == [shape[0]]
+        for _ in range(3):
+            o.set_state(g.get_f(), g.surface_charge())
+            b.step(1)
+            assert b.sync() == [fk.FK_OK]
+            o.step(1)
+            fg, fo = g.get_f(), o.get_f()
+            assert rel_l1(fg, fo) <= tol
+            # the edge row the zero-fill and the copy share, plane by plane
+            edge = np.abs(fg[:, -1, :] - fo[:, -1, :]).max(axis=1)
+            assert np.all(edge <= 10 * tol * np.abs(fo).max()), edge.max()
+            assert abs(g.surface_charge() - o.surface_charge()) <= tol * abs(o.surface_charge())
+    g.close()
+
+
 @pytest.mark.parametrize("prec,tol", [(fk.FK_F64, 1e-10), (fk.FK_F32, 1e-5)])
 def test_multi_step_parity_and_ledger(prec, tol):
     shape = (30, 28, 26)
