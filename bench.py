@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--chunk-len", type=int, default=0,
                     help="planes per x-chunk of every instance instead of the autotuner's choice "
                          "(for profiling runs, where the tuner's timing trials are distorted)")
+    ap.add_argument("--tile-rows", type=int, default=-1,
+                    help="v1-row cap of every instance's whole-CTA tiles (0: the default "
+                         "tiles) instead of the autotuner's tile search (-1)")
     return ap.parse_args()
 
 
@@ -184,11 +187,13 @@ def make_grids(fk, w, precision, stream):
 
 
 def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=True,
-             kernel_steps=50, chunk_len=0):
+             kernel_steps=50, chunk_len=0, tile_rows=-1):
     """Time `steps` steps of the workload's instances after `warmup` steps,
     as users run them: each step a CUDA-graph replay (batch: one step-kernel
     launch per unit layout and one finalize launch for all instances, x-chunks
-    autotuned before the warm-up; else each instance's own graph).  The
+    and v1 tiles autotuned before the warm-up; else each instance's own
+    graph).  chunk_len > 0 pins the x-chunks, tile_rows >= 0 the tile-row cap
+    (0: the default tiles), each instead of the autotuner's choice.  The
     step kernel's own launch durations (CUDA events around each launch,
     direct launches) are taken in a separate pass of `kernel_steps` steps
     after the timed region, for the roofline."""
@@ -198,6 +203,8 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
     assert stream, "time_arm needs a non-default current stream"
     grids = make_grids(fk, w, precision, stream)
     for g in grids:
+        if tile_rows >= 0:
+            g.set_tile_rows(tile_rows)
         g.set_f(f0)
     b = fk.Batch(grids, stream) if batch else None
     tuned = 0
@@ -205,7 +212,7 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
         if chunk_len > 0:
             b.set_chunks([chunk_len] * len(grids))
         else:
-            tuned = b.autotune(2)
+            tuned = b.autotune(2, tiles=tile_rows < 0)
 
     def advance(n):
         if b is not None:
@@ -253,9 +260,11 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
         b.set_kernel_timing(False)
         assert b.sync() == [fk.FK_OK] * len(grids)
         info = b.info()
+        ginfo = grids[0].info()
         plan = dict(mode="batch", units=info["units"], smem_bytes=info["smem_bytes"],
                     ctas_per_sm=info["ctas_per_sm"], chunk_len=b.chunks(),
-                    n_tiles=grids[0].info()["n_tiles"], autotune_steps=tuned,
+                    n_tiles=ginfo["n_tiles"], tile_rows=ginfo["tile_rows"],
+                    tile_cap=[g.info()["tile_cap"] for g in grids], autotune_steps=tuned,
                     timed="CUDA-graph replay (32 steps per graph)",
                     kernel_times="CUDA events around each step-kernel launch, separate "
                                  "pass of %d direct-launched steps" % kernel_steps)
@@ -280,15 +289,20 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
                 grids=grids, kernel=plan)
 
 
-def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True):
+def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True, plan=None):
     """The user's loop through the C ABI with host buffers: upload f0 from
     pinned host memory, then per step advance (the instances as one batch,
     or each alone) and read n_e, E_x, sigma and the wall fluxes back (the
     batch: queued into pinned slots, step n's read while step n + 1 runs),
-    finally read f back; all inside the timed region."""
+    finally read f back; all inside the timed region.  plan: the batch's
+    x-chunks and tile caps (as time_arm's autotuner left them), set up
+    before the timed region."""
     stream = torch.cuda.current_stream().cuda_stream
     assert stream, "e2e_arm needs a non-default current stream"
     grids = make_grids(fk, w, precision, stream)
+    if batch and plan is not None:
+        for g, cap in zip(grids, plan["tile_cap"]):
+            g.set_tile_rows(cap)
     nx = w["nx"]
     # an FP32 grid exchanges f with the host in its own storage type
     f32 = precision == fk.FK_F32
@@ -309,6 +323,8 @@ def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True):
         else:
             g.set_f(f_host)
     b = fk.Batch(grids, stream) if batch else None
+    if b is not None and plan is not None:
+        b.set_chunks(plan["chunk_len"])
     ne_all = np.empty(nx * len(grids))
     ex_all = np.empty(nx * len(grids))
     slot = 0
@@ -440,7 +456,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     prec = fk.FK_F32 if args.precision == "f32" else fk.FK_F64
     res = time_arm(fk, torch, w, prec, f0, args.steps, args.warmup, dist, local,
-                   batch=not args.no_batch, chunk_len=args.chunk_len)
+                   batch=not args.no_batch, chunk_len=args.chunk_len, tile_rows=args.tile_rows)
     for g in res.pop("grids"):
         g.close()
     ms = reduce_over_ranks(res["ms"], dist, "max")
@@ -474,7 +490,8 @@ def run_ours(args):
             "clocks": r2["clocks"]}}
     if not args.no_e2e:
         e2e_steps = args.e2e_steps or min(int(w.get("steps", 100)), 20000)
-        e2e = e2e_arm(fk, torch, w, prec, f0, e2e_steps, batch=not args.no_batch)
+        e2e = e2e_arm(fk, torch, w, prec, f0, e2e_steps, batch=not args.no_batch,
+                      plan=res["kernel"] if not args.no_batch else None)
         e2e["value"] = reduce_over_ranks(e2e["value"], dist, "sum")
         line["e2e"] = e2e
     if not args.no_sweep:

@@ -35,6 +35,14 @@
  *    streaming step is not checked per cell: with f >= 0 and the Courant sum
  *    (checked every step) at most 1, its update is a sum of non-negative
  *    terms.
+ *  - Range of f.  FP64 grids: the streaming step sums f^{n+1} for n_e through
+ *    an exact split of each value into two FP32 parts, which covers
+ *    2^-126 <= |f| < 2^128 (about 1.2e-38 to 3.4e38); smaller magnitudes
+ *    count as 0 in n_e, and larger ones, infinities and NaN make the sum
+ *    non-finite, so the step reports FK_ENUMERIC.  FP32 grids store f in
+ *    FP32; their half-CTA units sum the wall fluxes v1 f in FP32 pairs, so
+ *    |f| max|v1| must stay below 3.4e38 (above it the flux is non-finite and
+ *    the step reports FK_ENUMERIC).
  *  - Failure-detection test knobs (off by default, read at fk_create_grid):
  *    FK_TEST_WAIT_CYCLES=<n> sets the limit of the streaming kernel's bounded
  *    waits to n cycles (default about 2 s); FK_TEST_WITHHOLD_COPY=<q> makes
@@ -82,8 +90,8 @@ typedef enum {
  * 2 <= nx <= 8192 and 2 <= nv1, nv2 <= 65536 cells; h_max > 0 (m); v1_min < v1_max, v2_min < v2_max
  * (m/s); dt > 0 (s), or dt <= 0 to take dt = cfl * dx / max(|v1_min|,
  * |v1_max|) with cfl > 0; history_capacity = rows kept in the device history
- * ring (0 selects 65536).  Sec. 2, paragraph on default parameters: "grid
- * and time resolutions are prescribed by the CFL conditions". */
+ * ring (0 selects 65536).  Sec. 2, paragraph on default parameters: the
+ * paper sets the grid and the time step by the CFL conditions. */
 typedef struct {
   int32_t nx, nv1, nv2;
   int32_t precision; /* fk_precision */
@@ -270,10 +278,23 @@ fk_status fk_set_state(fk_grid *grid, const void *buf, size_t len);
  * 0 direct-load), v1-row tiles per plane, x-chunks, planes per chunk,
  * work units per CTA of the streaming kernel (2 where each sign half of the
  * v1 rows fits the tile of a half-CTA unit, else 1; the environment
- * variable FK_STREAM_HALF=0 at grid creation keeps 1).
+ * variable FK_STREAM_HALF=0 at grid creation keeps 1), v1 rows of the
+ * largest tile, the tile-row cap of fk_set_tile_rows (0: none).
  * Host-side, no synchronisation. */
-#define FK_INFO_LEN 11
+#define FK_INFO_LEN 13
 fk_status fk_grid_info(const fk_grid *grid, double *out);
+
+/* Work decomposition of the streaming step kernel's whole-CTA units: cap
+ * the v1 rows of a tile at max_rows (>= 1), or 0 for the default plan (the
+ * most rows for which two CTAs fit on an SM).  Grids whose sign halves run
+ * as half-CTA units keep their tiles.  Waits for the grid's pending work,
+ * keeps its state and re-plans its tiles (and x-chunks); the next fk_step
+ * recaptures its graphs.  The per-cell update does not depend on the
+ * tiles, but n_e(x) (Eq. 14) is summed per (plane, tile) before the planes'
+ * FP64 fold, so the tile plan sets the rounding of n_e, E_x and everything
+ * after them: two grids step bit for bit alike only with the same plan.
+ * FK_EINVAL for max_rows < 0, FK_ESTATE while a batch steps the grid. */
+fk_status fk_set_tile_rows(fk_grid *grid, int32_t max_rows);
 
 /* Kernel timing (tracing).  enabled != 0: later fk_step calls launch each
  * step directly (no graph replay) and record a CUDA event pair around every
@@ -411,6 +432,17 @@ fk_status fk_batch_moments_collect(fk_batch *batch, int32_t slot, double *sigma,
  * memory plan: the most rows for which two CTAs fit on an SM, or, where each
  * sign half of the v1 rows fits a half-CTA unit, one such half per tile. */
 fk_status fk_batch_autotune(fk_batch *batch, int32_t steps_per_trial, int64_t *steps_taken);
+
+/* The same search, and for every bucket whose grids run whole-CTA units
+ * also the v1 tile: besides each grid's current tiles, caps of about 5120
+ * and 4096 cells per tile plane (rows = cells / pitch, at least 4; only
+ * where they cut the grid's tiles), each timed at the chunk candidates.
+ * The grids keep the tile caps found, as after fk_set_tile_rows (their
+ * fk_grid_info reports them); the trials' steps advance the grids with the
+ * plans tried.  Afterwards a grid in the batch steps bit for bit as the same
+ * state stepped alone with the same tile cap. */
+fk_status fk_batch_autotune_tiles(fk_batch *batch, int32_t steps_per_trial,
+                                  int64_t *steps_taken);
 
 /* Read (chunk_len[n]) or set the planes per x-chunk of every grid.  Set:
  * each value is clamped to [1, nx]; the next fk_batch_step uses it. */

@@ -126,6 +126,44 @@ fk_status fk::sync_state_with(fk_grid* g, DevState* out, double* n_e, double* Ex
 }
 
 namespace {
+fk_status plan_geometry(fk_grid* g);
+}  // namespace
+
+fk_status fk::replan_tiles(fk_grid* g, int cap) {
+  g->tile_cap = cap;
+  const fk_status s = plan_geometry(g);
+  if (s != FK_OK) return s;
+  const int nu = g->geom.n_tiles;
+  if (nu > g->part_cap) {  // more tiles: larger partial-sum buffers (the grid is idle)
+    double** bufs[] = {&g->part.n, &g->part.lv, &g->part.pe, &g->part.see, &g->part.vac};
+    for (double** b : bufs) {
+      if (*b) FK_CUDA(g, cudaFree(*b));
+      *b = nullptr;
+    }
+    g->part_cap = 0;
+    const size_t nparts = (size_t)g->nx * nu;
+    FK_CUDA(g, cudaMalloc(&g->part.n, nparts * sizeof(double)));
+    FK_CUDA(g, cudaMalloc(&g->part.lv, nparts * sizeof(double)));
+    FK_CUDA(g, cudaMalloc(&g->part.pe, nu * sizeof(double)));
+    FK_CUDA(g, cudaMalloc(&g->part.see, nu * sizeof(double)));
+    FK_CUDA(g, cudaMalloc(&g->part.vac, nu * sizeof(double)));
+    FK_CUDA(g, cudaMemsetAsync(g->part.lv, 0, nparts * sizeof(double), g->stream));
+    FK_CUDA(g, cudaMemsetAsync(g->part.pe, 0, nu * sizeof(double), g->stream));
+    FK_CUDA(g, cudaMemsetAsync(g->part.see, 0, nu * sizeof(double), g->stream));
+    FK_CUDA(g, cudaMemsetAsync(g->part.vac, 0, nu * sizeof(double), g->stream));
+    FK_CUDA(g, cudaStreamSynchronize(g->stream));
+    g->part_cap = nu;
+  }
+  g->part.nu = nu;
+  for (int p = 0; p < 2; p++)  // captured with the old decomposition
+    if (g->graph[p]) {
+      cudaGraphExecDestroy(g->graph[p]);
+      g->graph[p] = nullptr;
+    }
+  return FK_OK;
+}
+
+namespace {
 
 // Evaluate the current state: moments of f, then finalize in `mode`.
 fk_status evaluate(fk_grid* g, int mode) {
@@ -237,7 +275,8 @@ void free_grid(fk_grid* g) {
   void* ptrs[] = {g->d_prm, g->d_st, g->d_f[0], g->d_f[1], g->tab.v1, g->tab.cx,
                   g->tab.cx32, g->tab.delta, g->tab.gse, g->tab.src, g->tab.src32,
                   g->tab.gfe_raw, g->tab.srow32, g->tab.scol32, g->tab.tsum, g->tab.m1, g->tab.m2,
-                  g->tab.m1_32, g->tab.m2_32, g->d_bgk, g->d_bgk32, g->part.n, g->part.lv,
+                  g->tab.m1_32, g->tab.m2_32, g->tab.v1p, g->tab.deltap,
+                  g->d_bgk, g->d_bgk32, g->part.n, g->part.lv,
                   g->part.pe, g->part.see,
                   g->part.vac, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist,
                   g->d_stage, g->d_f3, g->d_st_mid, g->fin.pre, g->fin.bsum, g->fin.blv,
@@ -295,14 +334,19 @@ fk_status build_graph(fk_grid* g, int parity) {
 // Where each sign half of the v1 rows fits the tile of a half-CTA unit,
 // units run two to a CTA (FK_STREAM_HALF=0 keeps one unit per CTA).
 fk_status plan_geometry(fk_grid* g) {
-  const char* env = getenv("FK_STEP_KERNEL");
+  if (g->env_direct < 0) {  // the environment's choices hold for the grid's life
+    const char* env = getenv("FK_STEP_KERNEL");
+    const char* env_half = getenv("FK_STREAM_HALF");
+    g->env_direct = env && strcmp(env, "direct") == 0;
+    g->env_no_half = env_half && strcmp(env_half, "0") == 0;
+  }
   FK_CUDA(g, cudaSetDevice(g->dev));
   int sms = 0, smem_sm = 0, reserved = 0;
   FK_CUDA(g, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->dev));
   FK_CUDA(g, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, g->dev));
   FK_CUDA(g, cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, g->dev));
   int ti_max = stream_tile_rows(g->prec, g->pitch, smem_sm, reserved, false);
-  g->use_stream = ti_max > 0 && !(env && strcmp(env, "direct") == 0);
+  g->use_stream = ti_max > 0 && !g->env_direct;
   if (!g->use_stream) ti_max = std::max(1, 4096 / g->pitch);
   int i_neg = 0;
   for (int i = 0; i < g->nv1; i++)
@@ -310,14 +354,14 @@ fk_status plan_geometry(fk_grid* g) {
   Geom& m = g->geom;
   m.i_neg = i_neg;
   m.half = 0;
-  const char* env_half = getenv("FK_STREAM_HALF");
-  if (g->use_stream && !(env_half && strcmp(env_half, "0") == 0)) {
+  if (g->use_stream && !g->env_no_half) {
     const int ti_half = stream_tile_rows(g->prec, g->pitch, smem_sm, reserved, true);
     if (ti_half > 0 && std::max(i_neg, g->nv1 - i_neg) <= ti_half) {
       m.half = 1;
       ti_max = ti_half;
     }
   }
+  if (g->use_stream && !m.half && g->tile_cap > 0) ti_max = std::min(ti_max, g->tile_cap);
   auto split = [&](int rows, int* nt, int* ti) {
     if (rows <= 0) {
       *nt = 0;
@@ -457,6 +501,7 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
     }
   }
   g->part.nu = g->geom.n_tiles;
+  g->part_cap = g->part.nu;
   const size_t nparts = (size_t)d.nx * g->part.nu;
   CREATE_CUDA(dalloc(&g->d_prm, sizeof(Params)));
   CREATE_CUDA(dalloc(&g->d_st, sizeof(DevState)));
@@ -478,6 +523,8 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   CREATE_CUDA(dalloc(&g->tab.m2, g->pitch * sizeof(double)));
   CREATE_CUDA(dalloc(&g->tab.m1_32, d.nv1 * sizeof(float)));
   CREATE_CUDA(dalloc(&g->tab.m2_32, g->pitch * sizeof(float)));
+  CREATE_CUDA(dalloc(&g->tab.v1p, d.nv1 * sizeof(float2)));
+  CREATE_CUDA(dalloc(&g->tab.deltap, nv * sizeof(float2)));
   CREATE_CUDA(dalloc(&g->d_bgk, 2 * (size_t)d.nx * sizeof(double)));
   CREATE_CUDA(dalloc(&g->d_bgk32, 2 * (size_t)d.nx * sizeof(float)));
   CREATE_CUDA(cudaMemsetAsync(g->d_bgk, 0, 2 * (size_t)d.nx * sizeof(double), g->stream));
@@ -1081,7 +1128,19 @@ fk_status fk_grid_info(const fk_grid* g, double* out) {
   out[8] = g->geom.n_chunks;
   out[9] = g->geom.chunk_len;
   out[10] = g->geom.half ? 2.0 : 1.0;
+  out[11] = std::max(g->geom.ti_neg, g->geom.ti_pos);
+  out[12] = g->tile_cap;
   return FK_OK;
+}
+
+fk_status fk_set_tile_rows(fk_grid* g, int32_t max_rows) {
+  if (!g) return FK_EINVAL;
+  FK_NOT_IN_BATCH(g);
+  if (max_rows < 0) return fail(g, FK_EINVAL, "max_rows must be >= 0");
+  DevState st;
+  const fk_status s = sync_state(g, &st);  // the grid's work is done
+  if (s != FK_OK) return s;
+  return replan_tiles(g, max_rows);
 }
 
 fk_status fk_set_kernel_timing(fk_grid* g, int enabled) {

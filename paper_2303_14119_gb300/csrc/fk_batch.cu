@@ -246,6 +246,27 @@ void drop_graphs(fk_batch* b) {
     }
 }
 
+// Shared memory per CTA and CTAs per SM of the batch's two launches, from
+// its grids' current tile plans; false if a plan does not fit an SM.
+bool batch_resources(fk_batch* b) {
+  b->smem = 0;
+  b->half_bytes = 0;
+  bool any_whole = false, any_half = false;
+  for (const fk_grid* g : b->grids) {
+    if (g->geom.half)
+      b->half_bytes = std::max(
+          b->half_bytes, (int)stream_half_bytes(g->prec, g->geom.stage_elems, g->pitch));
+    else
+      b->smem = std::max(b->smem, stream_smem_bytes(g->prec, g->geom.stage_elems, g->pitch));
+    (g->geom.half ? any_half : any_whole) = true;
+  }
+  b->per_sm_whole = any_whole ? stream_ctas_per_sm(b->prec, b->smem, kLayoutWhole) : 1 << 30;
+  b->per_sm_half =
+      any_half ? stream_ctas_per_sm(b->prec, 2 * (size_t)b->half_bytes, kLayoutHalf) : 1 << 30;
+  b->per_sm = std::min(b->per_sm_whole, b->per_sm_half);
+  return b->per_sm > 0;
+}
+
 // Upload both parities' grid arguments and the unit list of the current
 // chunking (after the batch's earlier work: the buffers may be in use).
 fk_status upload_plan(fk_batch* b) {
@@ -479,11 +500,6 @@ fk_status fk_batch_create(fk_grid* const* grids, int32_t n, void* cuda_stream, f
   std::vector<int2> fblk;
   for (int i = 0; i < n; i++) {
     fk_grid* g = gs[i];
-    if (g->geom.half)
-      b->half_bytes = std::max(
-          b->half_bytes, (int)stream_half_bytes(g->prec, g->geom.stage_elems, g->pitch));
-    else
-      b->smem = std::max(b->smem, stream_smem_bytes(g->prec, g->geom.stage_elems, g->pitch));
     if (g->pitch != g->nv2) b->padded = true;
     if (g->prm.collisions) b->bgk = true;
     b->cells += (double)g->nx * g->nv1 * g->nv2;
@@ -497,15 +513,7 @@ fk_status fk_batch_create(fk_grid* const* grids, int32_t n, void* cuda_stream, f
     }
     b->cur0[i] = g->enq_cur;
   }
-  {
-    bool any_whole = false, any_half = false;
-    for (const fk_grid* g : b->grids) (g->geom.half ? any_half : any_whole) = true;
-    b->per_sm_whole = any_whole ? stream_ctas_per_sm(b->prec, b->smem, kLayoutWhole) : 1 << 30;
-    b->per_sm_half =
-        any_half ? stream_ctas_per_sm(b->prec, 2 * (size_t)b->half_bytes, kLayoutHalf) : 1 << 30;
-    b->per_sm = std::min(b->per_sm_whole, b->per_sm_half);
-  }
-  if (b->per_sm <= 0) {
+  if (!batch_resources(b)) {
     free_batch(b);
     return bfail(nullptr, FK_EINVAL, "the grids' shared-memory plans do not fit an SM");
   }
@@ -710,7 +718,14 @@ fk_status fk_batch_info(const fk_batch* b, double* out) {
   return FK_OK;
 }
 
-fk_status fk_batch_autotune(fk_batch* b, int32_t steps_per_trial, int64_t* steps_taken) {
+namespace {
+
+// Cells per tile plane that the tile search of fk_batch_autotune_tiles tries
+// beside each grid's current tiles (rows = cells / pitch, at least 4).
+constexpr int kTileCellTargets[] = {5120, 4096};
+
+// The autotuner (fk_batch_autotune; tiles: fk_batch_autotune_tiles).
+fk_status autotune(fk_batch* b, int32_t steps_per_trial, int64_t* steps_taken, bool tiles) {
   if (!b) return FK_EINVAL;
   if (steps_per_trial < 1) return bfail(b, FK_EINVAL, "steps_per_trial must be >= 1");
   BK_CUDA(b, cudaSetDevice(b->dev));
@@ -741,6 +756,25 @@ fk_status fk_batch_autotune(fk_batch* b, int32_t steps_per_trial, int64_t* steps
     taken += steps_per_trial;
     return FK_OK;
   };
+  // every grid of bucket q with the tile-row cap caps[i] (the batch is idle
+  // after a trial); false if the shared-memory plans no longer fit an SM
+  auto set_caps = [&](int q, const std::vector<int>& caps) -> fk_status {
+    bool changed = false;
+    for (int i = 0; i < b->n; i++)
+      if (b->bucket[i] == q && b->grids[i]->tile_cap != caps[i]) {
+        const fk_status s = replan_tiles(b->grids[i], caps[i]);
+        if (s != FK_OK) {
+          b->err = b->grids[i]->err;
+          return s;
+        }
+        changed = true;
+      }
+    if (changed) {
+      if (!batch_resources(b)) return bfail(b, FK_EINVAL, "a tile plan does not fit an SM");
+      b->dirty = true;
+    }
+    return FK_OK;
+  };
   fk_status s = FK_OK;
   float best = 0.f, ms = 0.f;
   // buckets by their cells, largest first
@@ -758,59 +792,98 @@ fk_status fk_batch_autotune(fk_batch* b, int32_t steps_per_trial, int64_t* steps
   s = trial(&ms);  // warm-up (first touch of the plan)
   if (s == FK_OK) s = trial(&best);
   std::vector<int> keep = b->chunk_len;
+  std::vector<int> keep_caps(b->n);
+  for (int i = 0; i < b->n; i++) keep_caps[i] = b->grids[i]->tile_cap;
   for (size_t oi = 0; oi < order.size() && s == FK_OK; oi++) {
     const int q = order[oi];
-    // candidate chunk lengths: powers of two from kMinChunk up to the
-    // bucket's largest x range, and the lengths whose chunk count gives the
-    // bucket about a whole number k of waves of unit slots (equal units
-    // otherwise leave the last wave part-empty)
-    std::vector<int> cand;
-    for (int L = kMinChunk;; L *= 2) {
-      cand.push_back(std::min(L, bmax_nx[q]));
-      if (L >= bmax_nx[q]) break;
-    }
-    double row_units = 0.0;  // units of one chunk of every grid in the bucket
     bool half_bucket = true;
     for (int i = 0; i < b->n; i++)
-      if (b->bucket[i] == q) {
-        row_units += b->grids[i]->geom.n_tiles;
-        half_bucket = half_bucket && b->grids[i]->geom.half;
+      if (b->bucket[i] == q) half_bucket = half_bucket && b->grids[i]->geom.half;
+    // tile plans: the grids' current ones, then (tile search, whole-CTA
+    // buckets) caps of about kTileCellTargets cells per tile plane where
+    // they cut a grid's tiles
+    std::vector<std::vector<int>> plans(1, keep_caps);
+    if (tiles && !half_bucket)
+      for (const int cells : kTileCellTargets) {
+        std::vector<int> caps = keep_caps;
+        bool cuts = false;
+        for (int i = 0; i < b->n; i++)
+          if (b->bucket[i] == q) {
+            const fk_grid* g = b->grids[i];
+            caps[i] = std::max(4, cells / g->pitch);
+            cuts |= caps[i] < std::max(g->geom.ti_neg, g->geom.ti_pos);
+          }
+        if (cuts) plans.push_back(caps);
       }
-    // unit slots of the launch the bucket's units run in
-    const double slots =
-        (double)b->sms * (half_bucket ? 2.0 * b->per_sm_half : (double)b->per_sm_whole);
-    for (int k = 1; k <= 12 && row_units > 0.0; k++) {
-      const int c = std::max(1, (int)std::lround(k * slots / row_units));
-      const int L = (bmax_nx[q] + c - 1) / c;
-      if (L >= kMinChunk && L <= bmax_nx[q]) cand.push_back(L);
-    }
-    std::sort(cand.begin(), cand.end());
-    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-    for (size_t ci = 0; ci < cand.size() && s == FK_OK; ci++) {
-      const int Lc = cand[ci];
-      bool changed = false;
-      for (int i = 0; i < b->n; i++)
-        if (b->bucket[i] == q) {
-          const int len = even_chunk_len(b->grids[i]->nx, Lc);
-          changed |= len != b->chunk_len[i];
-          b->chunk_len[i] = len;
-        }
-      if (changed) {
-        b->dirty = true;
-        s = trial(&ms);
+    for (size_t pi = 0; pi < plans.size() && s == FK_OK; pi++) {
+      if (pi > 0) {  // a new tile plan: time it at the best chunking so far first
+        s = set_caps(q, plans[pi]);
+        if (s == FK_OK) s = trial(&ms);
         if (s == FK_OK && ms < best) {
           best = ms;
-          keep = b->chunk_len;
+          keep_caps = plans[pi];
         }
       }
-      b->chunk_len = keep;
-      b->dirty = true;
+      // candidate chunk lengths: powers of two from kMinChunk up to the
+      // bucket's largest x range, and the lengths whose chunk count gives the
+      // bucket about a whole number k of waves of unit slots (equal units
+      // otherwise leave the last wave part-empty)
+      std::vector<int> cand;
+      for (int L = kMinChunk;; L *= 2) {
+        cand.push_back(std::min(L, bmax_nx[q]));
+        if (L >= bmax_nx[q]) break;
+      }
+      double row_units = 0.0;  // units of one chunk of every grid in the bucket
+      for (int i = 0; i < b->n; i++)
+        if (b->bucket[i] == q) row_units += b->grids[i]->geom.n_tiles;
+      // unit slots of the launch the bucket's units run in
+      const double slots =
+          (double)b->sms * (half_bucket ? 2.0 * b->per_sm_half : (double)b->per_sm_whole);
+      for (int k = 1; k <= 12 && row_units > 0.0; k++) {
+        const int c = std::max(1, (int)std::lround(k * slots / row_units));
+        const int L = (bmax_nx[q] + c - 1) / c;
+        if (L >= kMinChunk && L <= bmax_nx[q]) cand.push_back(L);
+      }
+      std::sort(cand.begin(), cand.end());
+      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+      for (size_t ci = 0; ci < cand.size() && s == FK_OK; ci++) {
+        const int Lc = cand[ci];
+        bool changed = false;
+        for (int i = 0; i < b->n; i++)
+          if (b->bucket[i] == q) {
+            const int len = even_chunk_len(b->grids[i]->nx, Lc);
+            changed |= len != b->chunk_len[i];
+            b->chunk_len[i] = len;
+          }
+        if (changed) {
+          b->dirty = true;
+          s = trial(&ms);
+          if (s == FK_OK && ms < best) {
+            best = ms;
+            keep = b->chunk_len;
+            keep_caps = plans[pi];
+          }
+        }
+        b->chunk_len = keep;
+        b->dirty = true;
+      }
     }
+    if (s == FK_OK) s = set_caps(q, keep_caps);  // the bucket's best tile plan
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (steps_taken) *steps_taken = taken;
   return s;
+}
+
+}  // namespace
+
+fk_status fk_batch_autotune(fk_batch* b, int32_t steps_per_trial, int64_t* steps_taken) {
+  return autotune(b, steps_per_trial, steps_taken, false);
+}
+
+fk_status fk_batch_autotune_tiles(fk_batch* b, int32_t steps_per_trial, int64_t* steps_taken) {
+  return autotune(b, steps_per_trial, steps_taken, true);
 }
 
 fk_status fk_batch_set_kernel_timing(fk_batch* b, int enabled) {

@@ -27,6 +27,9 @@ struct fk_grid {
   fk::Tables tab{};
   fk::Partials part{};
   fk::Geom geom{};
+  int tile_cap = 0;   // whole-CTA v1 tiles of at most this many rows (0: the plan's most)
+  int env_direct = -1, env_no_half = -1;  // FK_STEP_KERNEL / FK_STREAM_HALF at creation
+  int part_cap = 0;   // tiles the partial-sum buffers hold
   bool use_stream = true;  // streaming kernel (else the direct-load kernel)
   double *d_ne = nullptr, *d_Ex = nullptr, *d_c1 = nullptr, *d_hist = nullptr;
   float* d_c1_32 = nullptr;
@@ -98,6 +101,11 @@ fk_status sync_state(fk_grid* g, DevState* out);
 // The same, also reading n_e and E_x [nx] into the host arrays given
 // (either may be NULL): one wait for all the copies.
 fk_status sync_state_with(fk_grid* g, DevState* out, double* n_e, double* Ex);
+// Cap the v1 rows of the grid's whole-CTA tiles (0: the shared-memory plan's
+// most) and re-plan its work decomposition; the grid must be idle.  The
+// partial-sum buffers grow if the new plan has more tiles; captured graphs
+// are dropped.
+fk_status replan_tiles(fk_grid* g, int cap);
 // Status for sticky device flags (FK_OK if none); sets the grid's message.
 fk_status flags_status(fk_grid* g, unsigned flags);
 

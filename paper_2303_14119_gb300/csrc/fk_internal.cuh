@@ -105,6 +105,10 @@ struct Tables {
   double* m2;     // [pitch] (zero on padding)
   float* m1_32;
   float* m2_32;
+  // for the wall sums of FP32 grids' half units, as FP32 pairs x = x.x +
+  // x.y: x.x = x rounded to FP32, x.y = the rest rounded to FP32
+  float2* v1p;     // [nv1] v1
+  float2* deltap;  // [nv1][pitch] delta
 };
 
 // Work decomposition shared by the step kernels and the finalize kernel.

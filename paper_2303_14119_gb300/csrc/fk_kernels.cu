@@ -56,6 +56,12 @@ constexpr int kTabBlocks = 256;
 constexpr int kTabThreads = 256;
 constexpr int kTabFoldThreads = 1024;
 
+// x as an FP32 pair (hi, lo): hi = x rounded to FP32, lo = x - hi rounded.
+__device__ __forceinline__ float2 split_pair(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+
 // Cell centre lo + (i + 1/2) h with separate roundings (no fused multiply-
 // add), so the velocity grid is bit-identical to a host computation.
 __device__ __forceinline__ double cell_centre(double lo, int i, double h) {
@@ -118,6 +124,7 @@ tables_fold_kernel(Tables t, int nv1, int nv2, int pitch, double v1_min, double 
   for (int i = threadIdx.x; i < nv1; i += blockDim.x) {
     const double v1 = cell_centre(v1_min, i, dv1);
     t.v1[i] = v1;
+    t.v1p[i] = split_pair(v1);
     t.cx[i] = __ddiv_rn(__dmul_rn(v1, dt), dx);
     t.cx32[i] = (float)t.cx[i];
   }
@@ -201,6 +208,7 @@ tables_scale_kernel(Tables t, int ncell, double dt, double j_over_ew) {
   const double nse = t.tsum[2 * kTabBlocks], nfe = t.tsum[2 * kTabBlocks + 1];
   for (int c = blockIdx.x * kTabThreads + threadIdx.x; c < ncell; c += kTabBlocks * kTabThreads) {
     t.gse[c] = nse > 0.0 ? t.gse[c] / nse : 0.0;
+    t.deltap[c] = split_pair(t.delta[c]);
     const double s = nfe > 0.0 ? dt * j_over_ew * (t.gfe_raw[c] / nfe) : 0.0;
     t.src[c] = s;
     t.src32[c] = (float)s;

@@ -207,6 +207,39 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
   s = t;
 }
 
+// FP32 pairs x.x + x.y, for the wall sums of FP32 grids' half units:
+// the leading product of a pair by a float or a pair is exact (TwoProd
+// with a fused multiply-add), sums take TwoSum of the leading parts and add
+// the trailing parts (Dekker 1971; Knuth, TAOCP Vol. 2, 4.2.2), about 44
+// bits in all, on the FP32 pipe instead of GB300's narrow FP64 one.
+__device__ __forceinline__ float2 pair_mul(float2 a, float b) {
+  const float p = a.x * b;
+  float e = fmaf(a.x, b, -p);
+  e = fmaf(a.y, b, e);
+  return make_float2(p, e);
+}
+__device__ __forceinline__ float2 pair_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return make_float2(p, e);
+}
+__device__ __forceinline__ void pair_acc(float2& s, float2 x) {
+  two_sum_acc(s.x, s.y, x.x);
+  s.y += x.y;
+}
+// sum over the warp, valid in lane 0
+__device__ __forceinline__ float2 pair_warp_sum(float2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_down_sync(0xffffffffu, v.x, o);
+    const float ol = __shfl_down_sync(0xffffffffu, v.y, o);
+    two_sum_acc(v.x, v.y, oh);
+    v.y += ol;
+  }
+  return v;
+}
+
 // Wall (x = 0, v1 < 0: Eqs. 12-14) or vacuum (x = h_max, v1 > 0) sums of
 // f^{n+1} over this consumer thread's cells of one plane, read back from
 // its own stores; returns whether one of those cells is negative.  Called
@@ -243,6 +276,46 @@ __device__ __noinline__ bool wall_terms(const T* oplane, const double* v1tab,
   out3[1] = see;
   out3[2] = vac;
   return neg;  // a value of the plane is negative
+}
+
+// The same sums for the half-CTA units of FP32 grids, in FP32 pairs (v1
+// and delta as pairs, exact leading products) and folded over the warp
+// (out3 valid in lane 0): thin tiles run three CTAs to an SM, and there the
+// FP64 instructions of the two boundary planes held up whole units.
+__device__ __noinline__ bool wall_terms_pairs(const float* oplane, const float2* v1p,
+                                              const float2* deltap, int tid, int nthreads,
+                                              int i0, int rows, int nv2, int pitch, bool wall,
+                                              double* out3) {
+  const int QV = pitch / 4;
+  float2 pe = make_float2(0.f, 0.f), see = pe, vac = pe;
+  bool neg = false;
+  for (int m = 0; m < kVecPerThread; m++) {
+    const int v = tid + nthreads * m;
+    if (v >= rows * QV) break;
+    const int r = v / QV, q = v - (v / QV) * QV;
+    const int i = i0 + r;
+    const float2 v1 = v1p[i];
+    for (int e = 0; e < 4 && q * 4 + e < nv2; e++) {
+      const size_t c = (size_t)i * pitch + q * 4 + e;
+      const float fn = oplane[c];
+      neg = neg || fn < 0.f;
+      const float2 g = pair_mul(v1, fn);
+      if (wall) {
+        const float2 mg = make_float2(-g.x, -g.y);  // Eq. 13 without dv1 dv2
+        pair_acc(pe, mg);
+        pair_acc(see, pair_mul(deltap[c], mg));  // Eq. 12
+      } else {
+        pair_acc(vac, g);
+      }
+    }
+  }
+  pe = pair_warp_sum(pe);
+  see = pair_warp_sum(see);
+  vac = pair_warp_sum(vac);
+  out3[0] = (double)pe.x + (double)pe.y;
+  out3[1] = (double)see.x + (double)see.y;
+  out3[2] = (double)vac.x + (double)vac.y;
+  return neg;  // a value of the thread's cells is negative
 }
 
 // Barrier over the threads of one unit: the whole CTA (barrier 0), or one
@@ -705,14 +778,25 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       const bool wall = k == 0 && dir < 0, vout = k == nx - 1 && dir > 0;
       if (wall || vout) {  // uniform over the block
         double b3[3];
-        const bool neg =
-            wall_terms<T>(oplane, a.tab.v1, a.tab.delta, tid, NT, i0, rows, nv2, pitch, wall, b3);
-        if (__any_sync(0xffffffffu, neg) && lane == 0) atomicOr(&a.st->flags, kFlagNegative);
-        const double w1 = warp_sum(b3[0]), w2 = warp_sum(b3[1]), w3 = warp_sum(b3[2]);
-        if (lane == 0) {
-          wsl[1] = w1;
-          wsl[2] = w2;
-          wsl[3] = w3;
+        if constexpr (sizeof(T) == 4 && NT == kHalfThreads) {
+          const bool neg = wall_terms_pairs(oplane, a.tab.v1p, a.tab.deltap, tid, NT, i0, rows,
+                                            nv2, pitch, wall, b3);
+          if (__any_sync(0xffffffffu, neg) && lane == 0) atomicOr(&a.st->flags, kFlagNegative);
+          if (lane == 0) {
+            wsl[1] = b3[0];
+            wsl[2] = b3[1];
+            wsl[3] = b3[2];
+          }
+        } else {
+          const bool neg =
+              wall_terms<T>(oplane, a.tab.v1, a.tab.delta, tid, NT, i0, rows, nv2, pitch, wall, b3);
+          if (__any_sync(0xffffffffu, neg) && lane == 0) atomicOr(&a.st->flags, kFlagNegative);
+          const double w1 = warp_sum(b3[0]), w2 = warp_sum(b3[1]), w3 = warp_sum(b3[2]);
+          if (lane == 0) {
+            wsl[1] = w1;
+            wsl[2] = w2;
+            wsl[3] = w3;
+          }
         }
       } else if (k == 0 || k == nx - 1) {
         if (lane == 0) wsl[1] = wsl[2] = wsl[3] = 0.0;

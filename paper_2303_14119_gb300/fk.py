@@ -98,12 +98,14 @@ def load(build_if_missing: bool = True):
         "fk_set_surface_charge": [P, D],
         "fk_grid_info": [P, dp],
         "fk_set_kernel_timing": [P, I],
+        "fk_set_tile_rows": [P, C.c_int32],
         "fk_kernel_timing": [P, i64p, dp],
         "fk_batch_create": [C.POINTER(P), C.c_int32, P, C.POINTER(P)],
         "fk_batch_destroy": [P],
         "fk_batch_step": [P, I64],
         "fk_batch_sync": [P, C.POINTER(C.c_int32)],
         "fk_batch_autotune": [P, C.c_int32, i64p],
+        "fk_batch_autotune_tiles": [P, C.c_int32, i64p],
         "fk_batch_get_chunks": [P, C.POINTER(C.c_int32)],
         "fk_batch_set_chunks": [P, C.POINTER(C.c_int32)],
         "fk_batch_info": [P, dp],
@@ -313,7 +315,7 @@ def fk_set_surface_charge(g, sigma):
     _check(load().fk_set_surface_charge(g, float(sigma)), "fk_set_surface_charge", g)
 
 
-FK_INFO_LEN = 11
+FK_INFO_LEN = 13
 
 
 def fk_grid_info(g):
@@ -321,7 +323,12 @@ def fk_grid_info(g):
     _check(load().fk_grid_info(g, _dp(out)), "fk_grid_info", g)
     return dict(dx=out[0], dv1=out[1], dv2=out[2], dt=out[3], c2=out[4], cx_max=out[5],
                 kernel="stream" if out[6] else "direct", n_tiles=int(out[7]),
-                n_chunks=int(out[8]), chunk_len=int(out[9]), units_per_cta=int(out[10]))
+                n_chunks=int(out[8]), chunk_len=int(out[9]), units_per_cta=int(out[10]),
+                tile_rows=int(out[11]), tile_cap=int(out[12]))
+
+
+def fk_set_tile_rows(g, max_rows):
+    _check(load().fk_set_tile_rows(g, int(max_rows)), "fk_set_tile_rows", g)
 
 
 def fk_set_kernel_timing(g, enabled):
@@ -438,6 +445,9 @@ class Grid:
 
     def set_kernel_timing(self, enabled):
         fk_set_kernel_timing(self.h, enabled)
+
+    def set_tile_rows(self, max_rows):
+        fk_set_tile_rows(self.h, max_rows)
 
     def kernel_timing(self):
         return fk_kernel_timing(self.h)
@@ -663,6 +673,13 @@ def fk_batch_autotune(b, steps_per_trial=2):
     return taken.value
 
 
+def fk_batch_autotune_tiles(b, steps_per_trial=2):
+    taken = C.c_int64()
+    _bcheck(load().fk_batch_autotune_tiles(b, int(steps_per_trial), C.byref(taken)),
+            "fk_batch_autotune_tiles", b)
+    return taken.value
+
+
 def fk_batch_get_chunks(b, n):
     out = (C.c_int32 * n)()
     _bcheck(load().fk_batch_get_chunks(b, out), "fk_batch_get_chunks", b)
@@ -727,7 +744,11 @@ class Batch:
     def sync(self):
         return fk_batch_sync(self.h, len(self.grids))
 
-    def autotune(self, steps_per_trial=2):
+    def autotune(self, steps_per_trial=2, tiles=False):
+        """Chunk lengths per size bucket (tiles: and the v1 tile rows of the
+        whole-CTA buckets); returns the steps the trials took."""
+        if tiles:
+            return fk_batch_autotune_tiles(self.h, steps_per_trial)
         return fk_batch_autotune(self.h, steps_per_trial)
 
     def scalars(self):

@@ -35,6 +35,16 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
+def test_binding_constants_match_the_header():
+    """Every integer #define of include/fk.h has the binding's value."""
+    text = open(os.path.join(ROOT, "include", "fk.h")).read()
+    defs = dict(re.findall(r"^#define\s+(FK_[A-Z0-9_]+)\s+(\d+)\s*$", text, flags=re.M))
+    assert "FK_INFO_LEN" in defs and "FK_HISTORY_COLS" in defs
+    for name, value in defs.items():
+        if hasattr(fk, name):
+            assert getattr(fk, name) == int(value), name
+
+
 def _desc(**kw):
     d = dict(nx=8, nv1=6, nv2=6, precision=0, h_max=20e-6, v1_min=-6e7, v1_max=6e7,
              v2_min=-3e7, v2_max=3e7, dt=0.0, cfl=0.4, history_capacity=0, device=0, reserved=0)
@@ -68,6 +78,7 @@ def test_null_arguments():
     assert lib.fk_destroy_grid(None) == fk.FK_OK
     assert lib.fk_step(None, 1) == fk.FK_EINVAL
     assert lib.fk_sync(None) == fk.FK_EINVAL
+    assert lib.fk_set_tile_rows(None, 16) == fk.FK_EINVAL
 
 
 def test_batch_create_rejects_bad_arguments_on_host():
@@ -89,6 +100,7 @@ def test_batch_calls_reject_null_handles():
     assert lib.fk_batch_step(None, 1) == fk.FK_EINVAL
     assert lib.fk_batch_sync(None, None) == fk.FK_EINVAL
     assert lib.fk_batch_autotune(None, 1, C.byref(n)) == fk.FK_EINVAL
+    assert lib.fk_batch_autotune_tiles(None, 1, C.byref(n)) == fk.FK_EINVAL
     assert lib.fk_batch_get_chunks(None, None) == fk.FK_EINVAL
     assert lib.fk_batch_set_chunks(None, None) == fk.FK_EINVAL
     assert lib.fk_batch_info(None, C.byref(d)) == fk.FK_EINVAL

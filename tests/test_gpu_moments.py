@@ -9,9 +9,13 @@ converted to FP64 once.  All terms are >= 0, so the relative error per plane
 is at most (31 + 5 + 6) * 2^-24 (about 2.5e-6); the direct-load kernel
 keeps a compensated FP32 sum per thread.  Here n_e(x) of
 fk_moments and the ledger's N are compared with FP64 numpy sums of the same
-FP32 state read back with fk_get_f32.  The FP32 ledger (every cumulative
-term, and its closure) is compared with the FP64 oracle over 300 strongly
-coupled steps.
+FP32 state read back with fk_get_f32.  The wall sums (Gamma_pe and
+Gamma_see at x = 0, the outflow at x = h_max) are FP64 sums of the FP32
+values in whole-CTA units and FP32 pairs with exact leading products (about
+44 bits) in half-CTA units: both are compared with the oracle's FP64 sums
+over the same FP32 state.  The FP32 ledger (every cumulative term, and
+its closure) is compared with the FP64 oracle over 300 strongly coupled
+steps.
 """
 import numpy as np
 import pytest
@@ -65,6 +69,33 @@ def test_fp32_density_moment_against_fp64_sum(shape, layout):
         N_ref = ref.sum() * o.info()["dx"]
         assert abs(N / N_ref - 1.0) <= BOUND
     print("max per-plane relative error of n_e: %.3e (bound %.3e)" % (worst, BOUND))
+    g.close()
+
+
+@pytest.mark.parametrize("shape,layout", [((64, 48, 48), 2), ((96, 128, 200), 1),
+                                           ((40, 256, 256), 1)])
+def test_fp32_wall_fluxes_against_the_oracle_on_the_same_state(shape, layout):
+    """Gamma_pe, Gamma_see and the vacuum outflow that the step kernel sums
+    for the new state agree with the oracle's FP64 sums over the same FP32
+    values to 1e-11 relative (plain FP32 sums would sit near 1e-7)."""
+    g, o = make_pair(shape, prec=fk.FK_F32)
+    assert g.info()["kernel"] == "stream" and g.info()["units_per_cta"] == layout
+    f0, sigma = strong_physics(g, o, shape, seed=25)
+    g.set_state(f0, sigma)
+    worst = 0.0
+    for n in (1, 6):
+        g.step(n)
+        _, _, pe, see = g.moments()
+        vac = g.history(1)[-1][5]
+        o.set_state(g.get_f(), g.surface_charge())
+        _, _, pe_o, see_o = o.moments()
+        vac_o = o.boundary_fluxes()["vac"]
+        for name, got, ref in (("pe", pe, pe_o), ("see", see, see_o), ("vac", vac, vac_o)):
+            assert ref != 0.0, name
+            err = abs(got - ref) / abs(ref)
+            worst = max(worst, err)
+            assert err <= 1e-11, (name, n, got, ref)
+    print("max relative error of the FP32 grid's wall sums: %.3e" % worst)
     g.close()
 
 
