@@ -130,28 +130,44 @@ fk_status plan_geometry(fk_grid* g);
 }  // namespace
 
 fk_status fk::replan_tiles(fk_grid* g, int cap) {
+  // on any failure the grid keeps its previous plan and buffers
+  const Geom old_geom = g->geom;
+  const int old_cap = g->tile_cap;
+  const bool old_stream = g->use_stream;
+  auto restore = [&](fk_status s) {
+    g->geom = old_geom;
+    g->tile_cap = old_cap;
+    g->use_stream = old_stream;
+    return s;
+  };
   g->tile_cap = cap;
   const fk_status s = plan_geometry(g);
-  if (s != FK_OK) return s;
+  if (s != FK_OK) return restore(s);
+  if (g->use_stream != old_stream) return restore(fail(g, FK_EINVAL, "the tile plan does not fit"));
   const int nu = g->geom.n_tiles;
   if (nu > g->part_cap) {  // more tiles: larger partial-sum buffers (the grid is idle)
-    double** bufs[] = {&g->part.n, &g->part.lv, &g->part.pe, &g->part.see, &g->part.vac};
-    for (double** b : bufs) {
-      if (*b) FK_CUDA(g, cudaFree(*b));
-      *b = nullptr;
-    }
-    g->part_cap = 0;
     const size_t nparts = (size_t)g->nx * nu;
-    FK_CUDA(g, cudaMalloc(&g->part.n, nparts * sizeof(double)));
-    FK_CUDA(g, cudaMalloc(&g->part.lv, nparts * sizeof(double)));
-    FK_CUDA(g, cudaMalloc(&g->part.pe, nu * sizeof(double)));
-    FK_CUDA(g, cudaMalloc(&g->part.see, nu * sizeof(double)));
-    FK_CUDA(g, cudaMalloc(&g->part.vac, nu * sizeof(double)));
-    FK_CUDA(g, cudaMemsetAsync(g->part.lv, 0, nparts * sizeof(double), g->stream));
-    FK_CUDA(g, cudaMemsetAsync(g->part.pe, 0, nu * sizeof(double), g->stream));
-    FK_CUDA(g, cudaMemsetAsync(g->part.see, 0, nu * sizeof(double), g->stream));
-    FK_CUDA(g, cudaMemsetAsync(g->part.vac, 0, nu * sizeof(double), g->stream));
-    FK_CUDA(g, cudaStreamSynchronize(g->stream));
+    const size_t sizes[5] = {nparts, nparts, (size_t)nu, (size_t)nu, (size_t)nu};
+    double* nb[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (int q = 0; q < 5; q++) {
+      cudaError_t e = cudaMalloc(&nb[q], sizes[q] * sizeof(double));
+      if (e == cudaSuccess) e = cudaMemsetAsync(nb[q], 0, sizes[q] * sizeof(double), g->stream);
+      if (e != cudaSuccess) {
+        for (double* p : nb)
+          if (p) cudaFree(p);
+        return restore(cuda_fail(g, e, "allocating the partial sums of the tile plan"));
+      }
+    }
+    const cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+      for (double* p : nb) cudaFree(p);
+      return restore(cuda_fail(g, e, "cudaStreamSynchronize"));
+    }
+    double** bufs[5] = {&g->part.n, &g->part.lv, &g->part.pe, &g->part.see, &g->part.vac};
+    for (int q = 0; q < 5; q++) {
+      if (*bufs[q]) cudaFree(*bufs[q]);
+      *bufs[q] = nb[q];
+    }
     g->part_cap = nu;
   }
   g->part.nu = nu;

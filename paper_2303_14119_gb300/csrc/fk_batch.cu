@@ -757,23 +757,27 @@ fk_status autotune(fk_batch* b, int32_t steps_per_trial, int64_t* steps_taken, b
     return FK_OK;
   };
   // every grid of bucket q with the tile-row cap caps[i] (the batch is idle
-  // after a trial); false if the shared-memory plans no longer fit an SM
+  // after a trial).  A grid whose re-plan fails keeps its plan; the batch's
+  // shared memory and slots follow whatever plans the grids hold.
   auto set_caps = [&](int q, const std::vector<int>& caps) -> fk_status {
+    fk_status first = FK_OK;
     bool changed = false;
     for (int i = 0; i < b->n; i++)
       if (b->bucket[i] == q && b->grids[i]->tile_cap != caps[i]) {
         const fk_status s = replan_tiles(b->grids[i], caps[i]);
-        if (s != FK_OK) {
+        if (s == FK_OK) {
+          changed = true;
+        } else if (first == FK_OK) {
+          first = s;
           b->err = b->grids[i]->err;
-          return s;
         }
-        changed = true;
       }
     if (changed) {
-      if (!batch_resources(b)) return bfail(b, FK_EINVAL, "a tile plan does not fit an SM");
       b->dirty = true;
+      if (!batch_resources(b) && first == FK_OK)
+        first = bfail(b, FK_EINVAL, "a tile plan does not fit an SM");
     }
-    return FK_OK;
+    return first;
   };
   fk_status s = FK_OK;
   float best = 0.f, ms = 0.f;
