@@ -64,6 +64,12 @@ def parse():
     ap.add_argument("--chunk-len", type=int, default=0,
                     help="planes per x-chunk of every instance instead of the autotuner's choice "
                          "(for profiling runs, where the tuner's timing trials are distorted)")
+    ap.add_argument("--collisions", action="store_true",
+                    help="switch on the BGK collision term (Eqs. 3-5; T_e 2 eV, ln Lambda 10)")
+    ap.add_argument("--reflection", type=float, default=0.0,
+                    help="electron reflection coefficient R_f at the wall")
+    ap.add_argument("--scheme", default="unsplit", choices=["unsplit", "lie", "strang"],
+                    help="time scheme (the split schemes step each instance alone)")
     ap.add_argument("--tile-rows", type=int, default=-1,
                     help="v1-row cap of every instance's whole-CTA tiles (0: the default "
                          "tiles) instead of the autotuner's tile search (-1)")
@@ -173,7 +179,13 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- our arm
-def make_grids(fk, w, precision, stream):
+SCHEMES = {"unsplit": 0, "lie": 1, "strang": 2}
+PASSES = {"unsplit": 1, "lie": 2, "strang": 3}  # passes over f per step
+
+
+def make_grids(fk, w, precision, stream, phys=None):
+    """The workload's instances; phys: optional terms of Eq. 2 and the wall
+    (collisions, reflection) and the time scheme."""
     grids = []
     for Ey in w.get("Ey_sweep", (w["Ey"],)):
         g = fk.Grid(w["nx"], w["nv1"], w["nv2"], w["h_max"], -w["v1_span"], w["v1_span"],
@@ -182,12 +194,19 @@ def make_grids(fk, w, precision, stream):
         g.set_fields(Ey)
         g.set_see(w["delta_max"], w["A_max"], w["k_s"], w["T_se"])
         g.set_source(w["J"], w["x_lo"], w["x_hi"], w["T_fe"])
+        if phys:
+            if phys["collisions"]:
+                g.set_collisions(2.0, 10.0, True)
+            if phys["reflection"] > 0.0:
+                g.set_reflection(phys["reflection"])
+            if phys["scheme"] != "unsplit":
+                g.set_scheme(SCHEMES[phys["scheme"]])
         grids.append(g)
     return grids
 
 
 def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=True,
-             kernel_steps=50, chunk_len=0, tile_rows=-1):
+             kernel_steps=50, chunk_len=0, tile_rows=-1, phys=None):
     """Time `steps` steps of the workload's instances after `warmup` steps,
     as users run them: each step a CUDA-graph replay (batch: one step-kernel
     launch per unit layout and one finalize launch for all instances, x-chunks
@@ -201,7 +220,7 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
     # legacy default), so the events below bracket exactly the grids' work
     stream = torch.cuda.current_stream().cuda_stream
     assert stream, "time_arm needs a non-default current stream"
-    grids = make_grids(fk, w, precision, stream)
+    grids = make_grids(fk, w, precision, stream, phys)
     for g in grids:
         if tile_rows >= 0:
             g.set_tile_rows(tile_rows)
@@ -283,13 +302,16 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
         plan = dict(mode="per-instance", timed="CUDA-graph replay per instance",
                     **{k: info[k] for k in ("kernel", "n_tiles", "n_chunks", "chunk_len")})
         cells_per_launch = cells
-        gpu_launches = 2 * steps * len(grids)
+        # per step: the pass(es), the Strang mid-step fold, the finalize
+        scheme = phys["scheme"] if phys else "unsplit"
+        per_step = {"unsplit": 2, "lie": 3, "strang": 5}[scheme]
+        gpu_launches = per_step * steps * len(grids)
     return dict(ms=ms, launches=launches, kernel_ms=kms, cells=cells, n_inst=len(grids),
                 cells_per_launch=cells_per_launch, gpu_launches=gpu_launches, clocks=ck,
                 grids=grids, kernel=plan)
 
 
-def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True, plan=None):
+def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True, plan=None, phys=None):
     """The user's loop through the C ABI with host buffers: upload f0 from
     pinned host memory, then per step advance (the instances as one batch,
     or each alone) and read n_e, E_x, sigma and the wall fluxes back (the
@@ -299,7 +321,7 @@ def e2e_arm(fk, torch, w, precision, f0_pinned, steps, batch=True, plan=None):
     before the timed region."""
     stream = torch.cuda.current_stream().cuda_stream
     assert stream, "e2e_arm needs a non-default current stream"
-    grids = make_grids(fk, w, precision, stream)
+    grids = make_grids(fk, w, precision, stream, phys)
     if batch and plan is not None:
         for g, cap in zip(grids, plan["tile_cap"]):
             g.set_tile_rows(cap)
@@ -413,15 +435,19 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 * 2 / 1e12
 DFMA_PER_CELL = 4  # the FP64 update is four fused multiply-adds per cell
 
 
-def roofline(res, precision, peak, peak_kind, workload):
+def roofline(res, precision, peak, peak_kind, workload, passes=1, plain=True):
+    """passes: passes over f per timed launch (one read of f and one write
+    each; the split schemes' passes are timed together); plain: the
+    workload's default physics, the only case the traffic record covers."""
     bpc = 4 if precision == "f32" else 8
     if res["launches"] == 0:
         return None
     avg_s = res["kernel_ms"] / res["launches"] / 1e3
-    alg_bytes = 2 * bpc * res["cells_per_launch"]  # one read of f^n, one write of f^{n+1}
+    alg_bytes = passes * 2 * bpc * res["cells_per_launch"]  # one read of f^n, one write of f^{n+1}
     achieved = alg_bytes / avg_s / 1e9
     hbm = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-           "frac": round(achieved / peak, 4), "traffic": kernel_traffic(workload, precision),
+           "frac": round(achieved / peak, 4),
+           "traffic": kernel_traffic(workload, precision) if plain else None,
            "peak_kind": "%s (copy bandwidth)" % peak_kind,
            "kernel": "fused upwind step", "avg_launch_us": round(avg_s * 1e6, 2),
            "alg_bytes_per_launch": alg_bytes}
@@ -455,8 +481,13 @@ def run_ours(args):
     f0[...] = synth.initial_f(shape, w["seed"], w["noise_rel"], w["J"], w["T_fe"])
     peak, peak_kind = measured_peaks()
     prec = fk.FK_F32 if args.precision == "f32" else fk.FK_F64
+    phys = dict(collisions=args.collisions, reflection=args.reflection, scheme=args.scheme)
+    plain = not args.collisions and args.reflection == 0.0 and args.scheme == "unsplit"
+    # batches step the unsplit scheme only: a split scheme steps each instance alone
+    batch = not args.no_batch and args.scheme == "unsplit"
+    passes = PASSES[args.scheme]
     res = time_arm(fk, torch, w, prec, f0, args.steps, args.warmup, dist, local,
-                   batch=not args.no_batch, chunk_len=args.chunk_len, tile_rows=args.tile_rows)
+                   batch=batch, chunk_len=args.chunk_len, tile_rows=args.tile_rows, phys=phys)
     for g in res.pop("grids"):
         g.close()
     ms = reduce_over_ranks(res["ms"], dist, "max")
@@ -470,28 +501,34 @@ def run_ours(args):
                    "cells_per_instance": res["cells"], "precision_storage": args.precision,
                    "accumulators": "f64", "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roofline(res, args.precision, peak, peak_kind, args.workload),
+        "roofline": roofline(res, args.precision, peak, peak_kind, args.workload, passes, plain),
         "kernel_plan": res["kernel"],
         "gpu_launches": res["gpu_launches"],
         "clocks": res["clocks"],
     }
+    if not plain:
+        line["config"]["physics"] = dict(
+            collisions="BGK, T_e 2 eV, ln Lambda 10" if args.collisions else "off",
+            reflection=args.reflection, scheme=args.scheme,
+            passes_per_step=passes, timed_launches=("the step kernel" if passes == 1 else
+                                                    "the %d passes of a step together" % passes))
     if not args.no_side:
         other = "f64" if args.precision == "f32" else "f32"
         oprec = fk.FK_F64 if other == "f64" else fk.FK_F32
         osteps = max(1, args.steps // (2 if other == "f64" else 1))
         r2 = time_arm(fk, torch, w, oprec, f0, osteps, args.warmup, dist, local,
-                      batch=not args.no_batch)
+                      batch=batch, phys=phys)
         for g in r2.pop("grids"):
             g.close()
         line["side_by_side"] = {other: {
             "value": world * r2["n_inst"] * r2["cells"] * osteps / (r2["ms"] / 1e3),
             "ms_per_step": r2["ms"] / osteps, "steps": osteps,
-            "roofline": roofline(r2, other, peak, peak_kind, args.workload),
+            "roofline": roofline(r2, other, peak, peak_kind, args.workload, passes, plain),
             "clocks": r2["clocks"]}}
     if not args.no_e2e:
         e2e_steps = args.e2e_steps or min(int(w.get("steps", 100)), 20000)
-        e2e = e2e_arm(fk, torch, w, prec, f0, e2e_steps, batch=not args.no_batch,
-                      plan=res["kernel"] if not args.no_batch else None)
+        e2e = e2e_arm(fk, torch, w, prec, f0, e2e_steps, batch=batch,
+                      plan=res["kernel"] if batch else None, phys=phys)
         e2e["value"] = reduce_over_ranks(e2e["value"], dist, "sum")
         line["e2e"] = e2e
     if not args.no_sweep:
