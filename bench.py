@@ -453,13 +453,15 @@ def roofline(res, precision, peak, peak_kind, workload, passes=1, plain=True):
            "alg_bytes_per_launch": alg_bytes}
     if precision == "f32":
         return hbm
-    # FP64 on GB300 is bound by the FP64 pipe, not by HBM
-    tflops = 2 * DFMA_PER_CELL * res["cells_per_launch"] / avg_s / 1e12
+    # FP64 on GB300 is bound by the FP64 pipe, not by HBM (every pass of a
+    # split step runs the fused update, four DFMA per cell)
+    flops = passes * 2 * DFMA_PER_CELL * res["cells_per_launch"]
+    tflops = flops / avg_s / 1e12
     return {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
             "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
             "traffic": hbm["traffic"], "peak_kind": "derived (FP64 FMA units x clock)",
             "kernel": "fused upwind step", "avg_launch_us": hbm["avg_launch_us"],
-            "alg_flops_per_launch": 2 * DFMA_PER_CELL * res["cells_per_launch"],
+            "alg_flops_per_launch": flops,
             "hbm": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")}}
 
 

@@ -30,11 +30,11 @@
  *    state, later steps do nothing, and the next getter or fk_sync returns
  *    the status.  Where f is checked for negative values: every cell of a
  *    state set with fk_set_f / fk_set_f32 (the call returns FK_ENEGATIVE),
- *    every cell a direct-load or split-scheme pass writes, and the wall and
- *    vacuum planes of every streaming step.  The interior of a
- *    streaming step is not checked per cell: with f >= 0 and the Courant sum
- *    (checked every step) at most 1, its update is a sum of non-negative
- *    terms.
+ *    every cell a direct-load pass writes, and the wall and vacuum planes of
+ *    every streaming step or split-scheme pass on the streaming kernel.  The
+ *    interior of a streaming pass is not checked per cell: with f >= 0 and
+ *    the Courant sum (checked every step) at most 1, its update is a sum of
+ *    non-negative terms.
  *  - Range of f.  FP64 grids: the streaming step sums f^{n+1} for n_e through
  *    an exact split of each value into two FP32 parts, which covers
  *    2^-126 <= |f| < 2^128 (about 1.2e-38 to 3.4e38); smaller magnitudes

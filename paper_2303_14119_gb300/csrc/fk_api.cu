@@ -92,6 +92,14 @@ namespace {
 
 fk_status upload_params(fk_grid* g) {
   FK_CUDA(g, cudaMemcpyAsync(g->d_prm, &g->prm, sizeof(Params), cudaMemcpyHostToDevice, g->stream));
+  if (g->d_prm_x) {  // an x pass of a split step: advection in x and the wall only
+    g->prm_x = g->prm;
+    g->prm_x.c2 = 0.0;
+    g->prm_x.band_lo = g->prm_x.band_hi = 0;
+    g->prm_x.collisions = 0;
+    FK_CUDA(g, cudaMemcpyAsync(g->d_prm_x, &g->prm_x, sizeof(Params), cudaMemcpyHostToDevice,
+                               g->stream));
+  }
   return FK_OK;
 }
 
@@ -196,7 +204,41 @@ cudaError_t enqueue_step(fk_grid* g, int cur, cudaStream_t s, cudaEvent_t ev0, c
   cudaError_t e = cudaSuccess;
   if (ev0) e = cudaEventRecord(ev0, s);
   if (e == cudaSuccess) {
-    if (g->scheme == kSchemeLie) {
+    if (g->scheme != kSchemeUnsplit && g->use_stream) {
+      // the split steps' passes on the streaming kernel: an x pass is the
+      // fused step with c_1 = c_2 = 0, no source and no collisions (c_x / 2
+      // for a Strang half pass); the velocity pass is the fused step with
+      // c_x = 0.  Partial sums a pass writes that a later pass writes again
+      // are overwritten; the last Strang pass sets its velocity-edge loss
+      // (zero) aside, the step's is the velocity pass's.
+      const bool bgk = g->prm.collisions != 0;
+      float* const zero32 = reinterpret_cast<float*>(g->d_zero);
+      StepArgs xp = a, vp = a;
+      xp.prm = g->d_prm_x;
+      xp.c1 = g->d_zero;
+      xp.c1_32 = zero32;
+      vp.tab.cx = g->d_zero;
+      vp.tab.cx32 = zero32;
+      if (g->scheme == kSchemeLie) {
+        xp.f_out = g->d_f3;
+        vp.f_in = g->d_f3;
+        e = launch_step_stream(xp, g->prec, false, s);
+        if (e == cudaSuccess) e = launch_step_stream(vp, g->prec, bgk, s);
+      } else {
+        xp.tab.cx = g->d_cx_half;
+        xp.tab.cx32 = g->d_cx32_half;
+        StepArgs x2 = xp;
+        vp.f_in = a.f_out;
+        vp.f_out = g->d_f3;
+        x2.f_in = g->d_f3;
+        x2.st = g->d_st_mid;
+        x2.part.lv = g->d_lv_aside;
+        e = launch_step_stream(xp, g->prec, false, s);
+        if (e == cudaSuccess) e = launch_step_stream(vp, g->prec, bgk, s);
+        if (e == cudaSuccess) e = launch_strang_mid(vp, g->d_st_mid, s);
+        if (e == cudaSuccess) e = launch_step_stream(x2, g->prec, false, s);
+      }
+    } else if (g->scheme == kSchemeLie) {
       // x-advection of f^n into the intermediate buffer, then the velocity
       // step of that state into f^{n+1} (both direct-load passes)
       StepArgs ax = a, av = a;
@@ -295,7 +337,8 @@ void free_grid(fk_grid* g) {
                   g->d_bgk, g->d_bgk32, g->part.n, g->part.lv,
                   g->part.pe, g->part.see,
                   g->part.vac, g->d_ne, g->d_Ex, g->d_c1, g->d_c1_32, g->d_hist,
-                  g->d_stage, g->d_f3, g->d_st_mid, g->fin.pre, g->fin.bsum, g->fin.blv,
+                  g->d_stage, g->d_f3, g->d_st_mid, g->d_prm_x, g->d_zero, g->d_cx_half,
+                  g->d_cx32_half, g->d_lv_aside, g->fin.pre, g->fin.bsum, g->fin.blv,
                   g->fin.counter};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -319,6 +362,22 @@ fk_status split_buffers(fk_grid* g, int scheme) {
   if (scheme == kSchemeStrang && !g->d_st_mid) {
     FK_CUDA(g, dalloc(&g->d_st_mid, sizeof(DevState)));
     FK_CUDA(g, cudaMemsetAsync(g->d_st_mid, 0, sizeof(DevState), g->stream));
+  }
+  if (scheme != kSchemeUnsplit && g->use_stream && !g->d_prm_x) {
+    // the passes run on the streaming kernel (the tables of c_x are final
+    // since creation, the parameters are re-uploaded with every setter)
+    const size_t nz = (size_t)std::max(g->nx, g->nv1);
+    FK_CUDA(g, dalloc(&g->d_zero, nz * sizeof(double)));
+    FK_CUDA(g, cudaMemsetAsync(g->d_zero, 0, nz * sizeof(double), g->stream));
+    FK_CUDA(g, dalloc(&g->d_cx_half, g->nv1 * sizeof(double)));
+    FK_CUDA(g, dalloc(&g->d_cx32_half, g->nv1 * sizeof(float)));
+    FK_CUDA(g, launch_scale_tables(g->tab.cx, g->tab.cx32, 0.5, g->nv1, g->d_cx_half,
+                                   g->d_cx32_half, g->stream));
+    // at most one tile per v1 row
+    FK_CUDA(g, dalloc(&g->d_lv_aside, (size_t)g->nx * g->nv1 * sizeof(double)));
+    FK_CUDA(g, dalloc(&g->d_prm_x, sizeof(Params)));
+    const fk_status s = upload_params(g);
+    if (s != FK_OK) return s;
   }
   return FK_OK;
 }

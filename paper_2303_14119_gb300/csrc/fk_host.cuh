@@ -56,6 +56,18 @@ struct fk_grid {
   // refused and the getters wait for the batch's last enqueued step
   int scheme = 0;             // kSchemeUnsplit or kSchemeLie
   void* d_f3 = nullptr;       // intermediate state of the split steps
+  // the split steps' passes on the streaming kernel: the parameters of an
+  // x pass (c_2 = 0, no source band, no collisions), zeros for the c_1 of
+  // an x pass and the c_x of the velocity pass (one array of
+  // max(nx, nv1) doubles, which read as floats are zeros too), c_x / 2 of
+  // a Strang half pass, and the velocity-edge partials the last Strang
+  // pass writes aside (the velocity pass's are the step's)
+  fk::Params prm_x{};
+  fk::Params* d_prm_x = nullptr;
+  double* d_zero = nullptr;
+  double* d_cx_half = nullptr;
+  float* d_cx32_half = nullptr;
+  double* d_lv_aside = nullptr;
   fk::DevState* d_st_mid = nullptr;  // Strang step: wall fluxes after the velocity pass
   fk_batch* batch = nullptr;
   cudaEvent_t batch_done = nullptr;
@@ -106,6 +118,9 @@ fk_status sync_state_with(fk_grid* g, DevState* out, double* n_e, double* Ex);
 // partial-sum buffers grow if the new plan has more tiles; captured graphs
 // are dropped.
 fk_status replan_tiles(fk_grid* g, int cap);
+// dst[i] = s * src[i] and dst32[i] = s * src32[i] for i < n.
+cudaError_t launch_scale_tables(const double* src, const float* src32, double s, int n,
+                                double* dst, float* dst32, cudaStream_t st);
 // Status for sticky device flags (FK_OK if none); sets the grid's message.
 fk_status flags_status(fk_grid* g, unsigned flags);
 

@@ -217,6 +217,21 @@ tables_scale_kernel(Tables t, int ncell, double dt, double j_over_ew) {
 
 int tables_scratch_doubles() { return 2 * kTabBlocks + 2; }
 
+__global__ void scale_tables_kernel(const double* src, const float* src32, double s, int n,
+                                    double* dst, float* dst32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    dst[i] = s * src[i];
+    dst32[i] = (float)s * src32[i];
+  }
+}
+
+cudaError_t launch_scale_tables(const double* src, const float* src32, double s, int n,
+                                double* dst, float* dst32, cudaStream_t st) {
+  scale_tables_kernel<<<(n + 255) / 256, 256, 0, st>>>(src, src32, s, n, dst, dst32);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tables(const Tables& t, int nv1, int nv2, int pitch, double v1_min,
                           double v2_min, double dv1, double dv2, double dt, double dx,
                           double delta_max, double A_max, double k_s, double T_se,
