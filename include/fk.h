@@ -49,7 +49,13 @@
  *    the work unit of tile 0, chunk 0 skip the plane copy of its pipeline
  *    item q, so that the waits on it run out and the step reports
  *    FK_ETIMEOUT (every copy that was issued still lands before the kernel
- *    leaves).
+ *    leaves).  FK_TEST_FAIL_ALLOC=<n> (read at each allocation) makes the
+ *    n-th device or pinned allocation since the start of the last
+ *    fk_create_grid or fk_batch_create fail, so that the call returns
+ *    FK_ENOMEM after freeing what it allocated.
+ *  - Builds: the release library, and a debug-bounds build (compiled with
+ *    FK_DEBUG_BOUNDS) whose streaming step kernel checks every index before
+ *    the access and reports a failed check as FK_EBOUNDS instead.
  *  - Calls on one grid must not run concurrently from several threads.
  *    Distinct grids are independent.
  */
@@ -76,8 +82,11 @@ typedef enum {
   FK_ENUMERIC = 5, /* a moment or flux became NaN or infinite */
   FK_ETIMEOUT = 6, /* a bounded wait inside a kernel ran out */
   FK_ESTATE = 7,   /* call not valid in the grid's current state */
-  FK_ENEGATIVE = 8 /* f has a negative value: a state set with one, or a
+  FK_ENEGATIVE = 8, /* f has a negative value: a state set with one, or a
                       step that produced one beyond rounding */
+  FK_EBOUNDS = 9   /* debug-bounds build (FK_DEBUG_BOUNDS) only: an index of
+                      the streaming step kernel fell outside its buffer; the
+                      access was skipped */
 } fk_status;
 
 typedef enum {

@@ -2,7 +2,10 @@
 
 Each ``csrc/*.cu`` file compiles to an object in ``_build/`` in parallel;
 the objects link into one shared library with the CUDA runtime linked
-statically.  Sources newer than the library trigger a rebuild.
+statically.  Sources newer than the library trigger a rebuild.  The variant
+"bounds" builds ``libflashkin_bounds.so`` with FK_DEBUG_BOUNDS (the step
+kernel checks every index first; the library is loaded instead of the
+release one when FK_LIBRARY=bounds is set).
 """
 from __future__ import annotations
 
@@ -16,6 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libflashkin.so")
+LIBS = {"release": LIB, "bounds": os.path.join(HERE, "libflashkin_bounds.so")}
+VARIANT_FLAGS = {"release": [], "bounds": ["-DFK_DEBUG_BOUNDS"]}
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
@@ -34,22 +39,27 @@ def _deps():
             glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(variant: str = "release") -> bool:
+    lib = LIBS[variant]
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(),
+          variant: str = "release") -> str:
+    lib = LIBS[variant]
+    out = OUT if variant == "release" else os.path.join(OUT, variant)
     with _lock:
-        if not force and not stale():
-            return LIB
-        os.makedirs(OUT, exist_ok=True)
+        if not force and not stale(variant):
+            return lib
+        os.makedirs(out, exist_ok=True)
         procs, objs = [], []
         for src in _sources():
-            obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
-            cmd = [NVCC, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj]
+            obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
+            cmd = [NVCC, *ARCH, *FLAGS, *VARIANT_FLAGS[variant], *extra_flags, "-c", src, "-o",
+                   obj]
             if verbose:
                 print(" ".join(cmd))
             procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -63,10 +73,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
                 errors.append(src)
         if errors:
             raise RuntimeError("nvcc failed for: " + ", ".join(errors))
-        tmp = LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call([NVCC, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp])
-        os.replace(tmp, LIB)
-    return LIB
+        tmp = lib + ".tmp%d" % os.getpid()
+        subprocess.check_call([NVCC, *ARCH, "-shared", "-cudart", "static", *objs, "-ldl",
+                               "-o", tmp])
+        os.replace(tmp, lib)
+    return lib
 
 
 

@@ -55,6 +55,8 @@ fk_status cuda_fail(fk_grid* g, cudaError_t e, const char* what) {
 }  // namespace
 
 fk_status fk::flags_status(fk_grid* g, unsigned flags) {
+  if (flags & kFlagBounds)
+    return fail(g, FK_EBOUNDS, "an index of the step kernel fell outside its buffer (debug-bounds build)");
   if (flags & kFlagTimeout) return fail(g, FK_ETIMEOUT, "a bounded wait inside the step kernel ran out");
   if (flags & kFlagNegative)
     return fail(g, FK_ENEGATIVE, "f has a negative value (the state set, or a step beyond rounding)");
@@ -137,6 +139,24 @@ namespace {
 fk_status plan_geometry(fk_grid* g);
 }  // namespace
 
+namespace {
+thread_local long long g_alloc_calls = 0;
+}  // namespace
+
+void fk::alloc_hook_reset() { g_alloc_calls = 0; }
+
+cudaError_t fk::hooked_alloc(void** p, size_t bytes, bool host) {
+  const char* e = getenv("FK_TEST_FAIL_ALLOC");
+  if (e && *e) {
+    const long long n = atoll(e);
+    if (n > 0 && ++g_alloc_calls == n) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return host ? cudaMallocHost(p, bytes) : cudaMalloc(p, bytes);
+}
+
 fk_status fk::replan_tiles(fk_grid* g, int cap) {
   // on any failure the grid keeps its previous plan and buffers
   const Geom old_geom = g->geom;
@@ -158,7 +178,7 @@ fk_status fk::replan_tiles(fk_grid* g, int cap) {
     const size_t sizes[5] = {nparts, nparts, (size_t)nu, (size_t)nu, (size_t)nu};
     double* nb[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     for (int q = 0; q < 5; q++) {
-      cudaError_t e = cudaMalloc(&nb[q], sizes[q] * sizeof(double));
+      cudaError_t e = hooked_alloc(reinterpret_cast<void**>(&nb[q]), sizes[q] * sizeof(double));
       if (e == cudaSuccess) e = cudaMemsetAsync(nb[q], 0, sizes[q] * sizeof(double), g->stream);
       if (e != cudaSuccess) {
         for (double* p : nb)
@@ -351,7 +371,7 @@ void free_grid(fk_grid* g) {
 
 template <typename P>
 cudaError_t dalloc(P** p, size_t bytes) {
-  return cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16);
+  return hooked_alloc(reinterpret_cast<void**>(p), bytes ? bytes : 16);
 }
 
 // The buffers a time scheme needs beyond the two state buffers: a third
@@ -477,6 +497,7 @@ extern "C" {
 
 fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** out) {
   g_create_error.clear();
+  alloc_hook_reset();
   if (!desc || !out) return fail(nullptr, FK_EINVAL, "desc and out must not be NULL");
   *out = nullptr;
   const fk_grid_desc& d = *desc;
@@ -580,7 +601,8 @@ fk_status fk_create_grid(const fk_grid_desc* desc, void* cuda_stream, fk_grid** 
   const size_t nparts = (size_t)d.nx * g->part.nu;
   CREATE_CUDA(dalloc(&g->d_prm, sizeof(Params)));
   CREATE_CUDA(dalloc(&g->d_st, sizeof(DevState)));
-  CREATE_CUDA(cudaMallocHost(&g->h_stage, sizeof(DevState) + 2 * (size_t)d.nx * sizeof(double)));
+  CREATE_CUDA(hooked_alloc(&g->h_stage, sizeof(DevState) + 2 * (size_t)d.nx * sizeof(double),
+                           true));
   CREATE_CUDA(dalloc(&g->d_f[0], fbytes));
   CREATE_CUDA(dalloc(&g->d_f[1], fbytes));
   CREATE_CUDA(dalloc(&g->tab.v1, d.nv1 * sizeof(double)));
@@ -809,6 +831,7 @@ fk_status fk_set_convergence(fk_grid* g, int64_t window, double rel_tol) {
 
 fk_status fk_step(fk_grid* g, int64_t n) {
   if (!g) return FK_EINVAL;
+  const NvtxRange range("fk_step");
   FK_NOT_IN_BATCH(g);
   if (n < 0) return fail(g, FK_EINVAL, "n must be >= 0");
   if (g->known_flags) return flags_status(g, g->known_flags);
@@ -924,7 +947,7 @@ fk_status fk_get_f(fk_grid* g, double* host_f) {
     FK_CUDA(g, cudaMemcpy2D(host_f, g->nv2 * sizeof(double), src, g->pitch * sizeof(double),
                             g->nv2 * sizeof(double), rows, cudaMemcpyDeviceToHost));
   } else {
-    if (!g->d_stage) FK_CUDA(g, cudaMalloc(&g->d_stage, kStageElems * sizeof(double)));
+    if (!g->d_stage) FK_CUDA(g, dalloc(&g->d_stage, kStageElems * sizeof(double)));
     const size_t rows_per = std::max<size_t>(1, kStageElems / g->nv2);
     for (size_t r0 = 0; r0 < rows; r0 += rows_per) {
       const size_t nr = std::min(rows_per, rows - r0);
@@ -950,7 +973,7 @@ fk_status fk_set_f(fk_grid* g, const double* host_f) {
     FK_CUDA(g, cudaMemcpy2DAsync(dst, g->pitch * sizeof(double), host_f, g->nv2 * sizeof(double),
                                  g->nv2 * sizeof(double), rows, cudaMemcpyHostToDevice, g->stream));
   } else {
-    if (!g->d_stage) FK_CUDA(g, cudaMalloc(&g->d_stage, kStageElems * sizeof(double)));
+    if (!g->d_stage) FK_CUDA(g, dalloc(&g->d_stage, kStageElems * sizeof(double)));
     const size_t rows_per = std::max<size_t>(1, kStageElems / g->nv2);
     for (size_t r0 = 0; r0 < rows; r0 += rows_per) {
       const size_t nr = std::min(rows_per, rows - r0);

@@ -288,14 +288,14 @@ fk_status upload_plan(fk_batch* b) {
     if (b->d_units) BK_CUDA(b, cudaFree(b->d_units));
     b->d_units = nullptr;
     b->max_units = 0;
-    BK_CUDA(b, cudaMalloc(&b->d_units, units.size() * sizeof(int2)));
+    BK_CUDA(b, hooked_alloc(reinterpret_cast<void**>(&b->d_units), units.size() * sizeof(int2)));
     b->max_units = (int)units.size();
   }
   if ((int)pairs.size() > b->max_pairs) {
     if (b->d_pairs) BK_CUDA(b, cudaFree(b->d_pairs));
     b->d_pairs = nullptr;
     b->max_pairs = 0;
-    BK_CUDA(b, cudaMalloc(&b->d_pairs, pairs.size() * sizeof(int4)));
+    BK_CUDA(b, hooked_alloc(reinterpret_cast<void**>(&b->d_pairs), pairs.size() * sizeof(int4)));
     b->max_pairs = (int)pairs.size();
   }
   b->n_units = (int)units.size();
@@ -445,6 +445,7 @@ extern "C" {
 
 fk_status fk_batch_create(fk_grid* const* grids, int32_t n, void* cuda_stream, fk_batch** out) {
   g_batch_create_error.clear();
+  alloc_hook_reset();
   if (!grids || !out || n < 1)
     return bfail(nullptr, FK_EINVAL, "grids and out must not be NULL and n must be >= 1");
   *out = nullptr;
@@ -518,8 +519,8 @@ fk_status fk_batch_create(fk_grid* const* grids, int32_t n, void* cuda_stream, f
     return bfail(nullptr, FK_EINVAL, "the grids' shared-memory plans do not fit an SM");
   }
   b->n_fblk = (int)fblk.size();
-  CREATE_B(cudaMalloc(&b->d_inst, 2 * (size_t)n * sizeof(BatchInst)));
-  CREATE_B(cudaMalloc(&b->d_fblk, fblk.size() * sizeof(int2)));
+  CREATE_B(hooked_alloc(reinterpret_cast<void**>(&b->d_inst), 2 * (size_t)n * sizeof(BatchInst)));
+  CREATE_B(hooked_alloc(reinterpret_cast<void**>(&b->d_fblk), fblk.size() * sizeof(int2)));
   CREATE_B(cudaMemcpy(b->d_fblk, fblk.data(), fblk.size() * sizeof(int2),
                       cudaMemcpyHostToDevice));
 #undef CREATE_B
@@ -546,6 +547,7 @@ fk_status fk_batch_destroy(fk_batch* b) {
 
 fk_status fk_batch_step(fk_batch* b, int64_t n) {
   if (!b) return FK_EINVAL;
+  const NvtxRange range("fk_batch_step");
   if (n < 0) return bfail(b, FK_EINVAL, "n must be >= 0");
   BK_CUDA(b, cudaSetDevice(b->dev));
   return enqueue_steps(b, n);
@@ -633,14 +635,14 @@ fk_status fk_batch_moments_enqueue(fk_batch* b, int32_t slot) {
     b->sum_nx = nx;
     BK_CUDA(b, cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking));
     BK_CUDA(b, cudaEventCreateWithFlags(&b->fin_ev, cudaEventDisableTiming));
-    BK_CUDA(b, cudaMalloc(&b->d_msrc, src.size() * sizeof(MomentSrc)));
+    BK_CUDA(b, hooked_alloc(reinterpret_cast<void**>(&b->d_msrc), src.size() * sizeof(MomentSrc)));
     BK_CUDA(b, cudaMemcpy(b->d_msrc, src.data(), src.size() * sizeof(MomentSrc),
                           cudaMemcpyHostToDevice));
   }
   const size_t bytes = (3 * (size_t)b->n + 2 * b->sum_nx) * sizeof(double);
   if (!b->h_slot[slot]) {  // first use of the slot: its buffers and events
-    BK_CUDA(b, cudaMallocHost(&b->h_slot[slot], bytes));
-    BK_CUDA(b, cudaMalloc(&b->d_slot[slot], bytes));
+    BK_CUDA(b, hooked_alloc(&b->h_slot[slot], bytes, true));
+    BK_CUDA(b, hooked_alloc(reinterpret_cast<void**>(&b->d_slot[slot]), bytes));
     BK_CUDA(b, cudaEventCreateWithFlags(&b->gathered[slot], cudaEventDisableTiming));
     BK_CUDA(b, cudaEventCreateWithFlags(&b->slot_ev[slot], cudaEventDisableTiming));
   }
@@ -727,6 +729,7 @@ constexpr int kTileCellTargets[] = {5120, 4096};
 // The autotuner (fk_batch_autotune; tiles: fk_batch_autotune_tiles).
 fk_status autotune(fk_batch* b, int32_t steps_per_trial, int64_t* steps_taken, bool tiles) {
   if (!b) return FK_EINVAL;
+  const NvtxRange range(tiles ? "fk_batch_autotune_tiles" : "fk_batch_autotune");
   if (steps_per_trial < 1) return bfail(b, FK_EINVAL, "steps_per_trial must be >= 1");
   BK_CUDA(b, cudaSetDevice(b->dev));
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -2,6 +2,8 @@
 // batch API (internal; the public ABI is include/fk.h).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 #include <vector>
 
@@ -76,6 +78,15 @@ struct fk_grid {
 
 namespace fk {
 
+// An NVTX range over a host call (tracing: profilers and timeline tools
+// show each fk_step / batch step as a named range; free without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Passes of the direct-load step kernel: a whole step, the moments of f_in
 // only, and the passes of the split steps: x-advection with the wall and
 // vacuum boundaries (over dt; over dt/2 without partial sums; over dt/2
@@ -118,6 +129,12 @@ fk_status sync_state_with(fk_grid* g, DevState* out, double* n_e, double* Ex);
 // partial-sum buffers grow if the new plan has more tiles; captured graphs
 // are dropped.
 fk_status replan_tiles(fk_grid* g, int cap);
+// Device (host: pinned host) allocation through the failure-injection test
+// hook: with FK_TEST_FAIL_ALLOC=<n> in the environment, the n-th allocation
+// since the last alloc_hook_reset() (called at the start of fk_create_grid
+// and fk_batch_create) fails with cudaErrorMemoryAllocation.
+cudaError_t hooked_alloc(void** p, size_t bytes, bool host = false);
+void alloc_hook_reset();
 // dst[i] = s * src[i] and dst32[i] = s * src32[i] for i < n.
 cudaError_t launch_scale_tables(const double* src, const float* src32, double s, int n,
                                 double* dst, float* dst32, cudaStream_t st);

@@ -23,6 +23,7 @@ enum : unsigned {
   kFlagNumeric = 2u,
   kFlagTimeout = 4u,
   kFlagNegative = 8u,
+  kFlagBounds = 16u,  // FK_DEBUG_BOUNDS builds: an index check failed
 };
 
 // Default limit of a bounded wait inside a kernel: cycles (about 2 s).

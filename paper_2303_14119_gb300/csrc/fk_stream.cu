@@ -199,6 +199,20 @@ __device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
   const float l = __uint2float_rn(r29) * scale;
   lo = ok ? (sign ? -l : l) : 0.f;
 }
+// Debug-bounds build (-DFK_DEBUG_BOUNDS): the step kernel checks the index
+// of each shared- and global-memory access and of each bulk copy against its
+// buffer first; a failed check sets kFlagBounds in the grid's state and the
+// access is skipped (a skipped copy still completes its stage's phase).  In
+// the release build every check is the constant true.
+#ifdef FK_DEBUG_BOUNDS
+__device__ __forceinline__ bool in_bounds(bool ok, DevState* st) {
+  if (!ok) atomicOr(&st->flags, kFlagBounds);
+  return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(bool, DevState*) { return true; }
+#endif
+
 // s + c += x, exactly in s (TwoSum), the rounding error collected in c
 __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
   const float t = s + x;
@@ -365,6 +379,11 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   const int s0 = chunk * gm.chunk_len;
   const int s1 = min(nx, s0 + gm.chunk_len);
   if (s0 >= s1 || i0 >= i1) return;  // uniform over the block
+  // the tile fits its row tables and a stage holds it with its halo row
+  if (!in_bounds(i0 >= 0 && i1 <= nv1 && i1 - i0 <= kMaxTileRows &&
+                     (i1 - i0 + 1) * pitch <= gm.stage_elems,
+                 a.st))
+    return;  // uniform over the block
 
   // march: step s visits plane k(s); the upwind plane of the first one is
   // loaded first ("prime" item) unless it lies outside the domain
@@ -410,6 +429,8 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   T* __restrict__ fout = static_cast<T*>(a.f_out);
   const size_t plane = (size_t)nv1 * pitch;
   const int QV = pitch / VEC;  // vectors per row
+  const int stage_n = gm.stage_elems;     // elements of a stage
+  const size_t f_n = (size_t)nx * plane;  // elements of f
   const int rows = i1 - i0;
 
   if (warp == NW) {
@@ -451,7 +472,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       int zrow = -1;
       if (c1 > 0.f && i0 == 0) zrow = 0;
       if (c1 < 0.f && i1 == nv1) zrow = rows;
-      if (zrow >= 0) {
+      if (zrow >= 0 && in_bounds((zrow + 1) * pitch <= stage_n, a.st)) {
         float4* z = reinterpret_cast<float4*>(stage + (size_t)zrow * pitch);
         const int n16 = pitch * (int)sizeof(T) / 16;
         for (int c = lane; c < n16; c += 32) z[c] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -477,11 +498,20 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         int lo = i0, hi = i1;
         if (c1 > 0.f && i0 > 0) lo = i0 - 1;  // v1 halo row on the upwind side
         if (c1 < 0.f && i1 < nv1) hi = i1 + 1;
-        T* dst = stage + (size_t)(lo - i0 + (c1 > 0.f ? 1 : 0)) * pitch;
-        const T* src = fin + (size_t)k * plane + (size_t)lo * pitch;
+        const int dofs = (lo - i0 + (c1 > 0.f ? 1 : 0)) * pitch;  // in the stage
+        const size_t sofs = (size_t)k * plane + (size_t)lo * pitch;  // in f
+        T* dst = stage + dofs;
+        const T* src = fin + sofs;
         const uint32_t bytes = (uint32_t)((hi - lo) * pitch * sizeof(T));
-        mbar_expect_tx(&full[st], bytes);  // release: the zero row is visible too
-        bulk_g2s(dst, src, bytes, &full[st]);
+        if (in_bounds(k >= 0 && k < nx && lo >= 0 && hi <= nv1 && dofs >= 0 &&
+                          dofs + (hi - lo) * pitch <= stage_n &&
+                          sofs + (size_t)(hi - lo) * pitch <= f_n,
+                      a.st)) {
+          mbar_expect_tx(&full[st], bytes);  // release: the zero row is visible too
+          bulk_g2s(dst, src, bytes, &full[st]);
+        } else {
+          mbar_expect_tx(&full[st], 0);  // no data: the stage's phase completes
+        }
       }
     };
     // What the partial sums of a consumed compute item need from its stage
@@ -512,11 +542,12 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       const T a1t = sizeof(T) == 4 ? (T)fabsf(c1f) : (T)a1d;
       const int erow = (c1f > 0.f && i1 == nv1) ? nv1 - 1 : ((c1f < 0.f && i0 == 0) ? 0 : -1);
       const int rb = c1f > 0.f ? 1 : 0;  // stage row of the tile's first row
-      if (erow >= 0) {
+      if (erow >= 0 && in_bounds(erow - i0 + rb >= 0 && (erow - i0 + rb + 1) * pitch <= stage_n,
+                                 a.st)) {
         const T* r = sb + (size_t)(erow - i0 + rb) * pitch;
         for (int j = lane; j < nv2; j += 32) g.lvt += a1t * r[j];
       }
-      if (has_a2)
+      if (has_a2 && in_bounds((rows - 1 + rb) * pitch + nv2 <= stage_n, a.st))
         for (int r = lane; r < rows; r += 32) g.lvt += a2t * sb[(size_t)(r + rb) * pitch + nv2 - 1];
       if (lane < NW) {
         const double* ws = wsum + (st * kWarps + lane) * kWs;
@@ -550,7 +581,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         }
       }
       if constexpr (sizeof(T) == 4) sum[0] = (double)sumf;  // one conversion per plane
-      if (lane == 0) {
+      if (lane == 0 && in_bounds(k >= 0 && k < nx && t >= 0 && t < nt, a.st)) {
         a.part.n[(size_t)k * nt + t] = sum[0];
         a.part.lv[(size_t)k * nt + t] = lv;
         if (k == 0) {
@@ -667,11 +698,13 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
     }
     // the tile's first row sits at stage row 1 when this plane's halo lies
     // above (c_1 > 0), at row 0 otherwise
-    const T* sb = reinterpret_cast<const T*>(stage_base + st * sbytes) + (c1f > 0.f ? pitch : 0);
+    const int sbo = c1f > 0.f ? pitch : 0;  // sb's offset in the stage
+    const T* sb = reinterpret_cast<const T*>(stage_base + st * sbytes) + sbo;
     if (!compute) {
 #pragma unroll
       for (int m = 0; m < M; m++) {
         if (!(valid >> m & 1)) continue;
+        if (!in_bounds(sbo + (int)(soff[m] & 0xFFFFFF) + VEC <= stage_n, a.st)) continue;
         const Vec<T> own = *reinterpret_cast<const Vec<T>*>(sb + (soff[m] & 0xFFFFFF));
 #pragma unroll
         for (int e = 0; e < VEC; e++) xr[m][e] = own.e[e];
@@ -690,7 +723,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         if (NT * m >= rows * QV) break;  // no thread of the unit has vector m (uniform)
         const int so = soff[m] & 0xFFFFFF;
         Vec<T> own;
-        if (valid >> m & 1)
+        if ((valid >> m & 1) && in_bounds(sbo + so + VEC <= stage_n, a.st))
           own = *reinterpret_cast<const Vec<T>*>(sb + so);
         else
 #pragma unroll
@@ -701,8 +734,13 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
         if (zleft >> m & 1)
           left = (T)0;
         else if (lane == 0)
-          left = sb[so - 1];
-        const Vec<T> nb = *reinterpret_cast<const Vec<T>*>(sb + so + nboff);
+          left = in_bounds(sbo + so - 1 >= 0, a.st) ? sb[so - 1] : (T)0;
+        Vec<T> nb;
+        if (in_bounds(sbo + so + nboff >= 0 && sbo + so + nboff + VEC <= stage_n, a.st))
+          nb = *reinterpret_cast<const Vec<T>*>(sb + so + nboff);
+        else
+#pragma unroll
+          for (int e = 0; e < VEC; e++) nb.e[e] = (T)0;
         const T d = sizeof(T) == 8 ? (T)dg[soff[m] >> 24] : (T)0;  // unused on FP32 grids
         Vec<T> src;
 #pragma unroll
@@ -754,8 +792,9 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
             sl_ += l;
           }
         }
-        __stcs(reinterpret_cast<float4*>(oplane + so + gbase),
-               *reinterpret_cast<const float4*>(&out));
+        if (in_bounds((size_t)k * plane + gbase + so + VEC <= f_n, a.st))
+          __stcs(reinterpret_cast<float4*>(oplane + so + gbase),
+                 *reinterpret_cast<const float4*>(&out));
       }
       // warp sum of this plane's f^{n+1} (an FP32 grid sums its 32 lanes in
       // FP32; everything above a warp is FP64)

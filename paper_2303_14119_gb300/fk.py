@@ -20,13 +20,14 @@ import numpy as np
 from . import _build
 
 (FK_OK, FK_EINVAL, FK_ENOMEM, FK_ECUDA, FK_ECFL, FK_ENUMERIC, FK_ETIMEOUT, FK_ESTATE,
- FK_ENEGATIVE) = range(9)
+ FK_ENEGATIVE, FK_EBOUNDS) = range(10)
 FK_F64, FK_F32 = 0, 1
 FK_SCHEME_UNSPLIT, FK_SCHEME_LIE, FK_SCHEME_STRANG = 0, 1, 2
 FK_HISTORY_COLS = 8
 FK_LEDGER_LEN = 9
 STATUS_NAMES = {0: "FK_OK", 1: "FK_EINVAL", 2: "FK_ENOMEM", 3: "FK_ECUDA", 4: "FK_ECFL",
-                5: "FK_ENUMERIC", 6: "FK_ETIMEOUT", 7: "FK_ESTATE", 8: "FK_ENEGATIVE"}
+                5: "FK_ENUMERIC", 6: "FK_ETIMEOUT", 7: "FK_ESTATE", 8: "FK_ENEGATIVE",
+                9: "FK_EBOUNDS"}
 
 
 class fk_grid_desc(C.Structure):
@@ -52,20 +53,28 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """Path of the library load() takes (the FK_LIBRARY variant)."""
+    return _build.LIBS.get(os.environ.get("FK_LIBRARY", "release") or "release", _build.LIB)
 
 
 def load(build_if_missing: bool = True):
     """Load ``libflashkin.so`` (building it first if it is missing or stale
-    and nvcc is available).  Raises if it cannot be loaded."""
+    and nvcc is available); with FK_LIBRARY=bounds in the environment, the
+    debug-bounds build ``libflashkin_bounds.so`` instead.  Raises if it
+    cannot be loaded."""
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_missing and (not os.path.exists(_build.LIB) or _build.stale()):
-        _build.build()
-    if not os.path.exists(_build.LIB):
-        raise ImportError("libflashkin.so is not built; run paper_2303_14119_gb300._build.build()")
-    lib = C.CDLL(_build.LIB)
+    variant = os.environ.get("FK_LIBRARY", "release") or "release"
+    if variant not in _build.LIBS:
+        raise ImportError("FK_LIBRARY must be one of %s" % sorted(_build.LIBS))
+    path = _build.LIBS[variant]
+    if build_if_missing and (not os.path.exists(path) or _build.stale(variant)):
+        _build.build(variant=variant)
+    if not os.path.exists(path):
+        raise ImportError("%s is not built; run paper_2303_14119_gb300._build.build()"
+                          % os.path.basename(path))
+    lib = C.CDLL(path)
     P, D, I, I64 = C.c_void_p, C.c_double, C.c_int, C.c_int64
     dp = C.POINTER(C.c_double)
     fp = C.POINTER(C.c_float)

@@ -123,3 +123,13 @@ def test_fowler_nordheim_host_function_matches_the_oracle():
     d = Ct.c_double()
     assert lib.fk_fowler_nordheim(0.0, 4.0, Ct.byref(d), None) == fk.FK_EINVAL
     assert lib.fk_fowler_nordheim(1e9, -1.0, None, None) == fk.FK_EINVAL
+
+
+def test_debug_bounds_build_compiles_and_exports_every_symbol():
+    """The FK_DEBUG_BOUNDS variant builds (nvcc cross-compiles without a GPU)
+    and exports the same entry points; loading it makes no device call."""
+    from paper_2303_14119_gb300 import _build
+    path = _build.build(variant="bounds")
+    lib = C.CDLL(path)
+    missing = [n for n in declared_entry_points() if not hasattr(lib, n)]
+    assert not missing, missing

@@ -11,6 +11,11 @@
 - Negative f: a state with a negative value injected from the host is
   reported as FK_ENEGATIVE by fk_set_f, and the grid refuses to step until a
   valid state is set.
+- Allocation failure: with FK_TEST_FAIL_ALLOC=n the n-th device or pinned
+  allocation of a grid's or a batch's creation fails on the host (nothing
+  reaches the GPU).  Creation must return FK_ENOMEM for every n up to the
+  number of allocations, free what it allocated, and leave the device
+  usable.
 """
 import os
 
@@ -92,3 +97,55 @@ def test_negative_input_state_is_reported(prec):
     g.step(3)
     assert g.step_count()[0] == 3
     g.close()
+
+
+def _grid(shape, prec=fk.FK_F64):
+    return fk.Grid(*shape, 20e-6, -6e7, 6e7, -3e7, 3e7, cfl=0.4, precision=prec)
+
+
+@pytest.mark.parametrize("prec", [fk.FK_F64, fk.FK_F32])
+def test_every_allocation_failure_of_a_creation_is_reported(prec, monkeypatch):
+    shape = (16, 24, 20)
+    failed = 0
+    for n in range(1, 200):
+        monkeypatch.setenv("FK_TEST_FAIL_ALLOC", str(n))
+        try:
+            g = _grid(shape, prec)
+        except fk.FkError as e:
+            assert e.status == fk.FK_ENOMEM, (n, e)
+            failed += 1
+            continue
+        finally:
+            monkeypatch.delenv("FK_TEST_FAIL_ALLOC")
+        g.close()
+        break
+    assert failed >= 20  # every allocation point of the grid was made to fail
+    # batches: a grid pair, each allocation of the batch's creation in turn
+    grids = [_grid(shape, prec), _grid((9, 8, 8), prec)]
+    bfailed = 0
+    for n in range(1, 50):
+        monkeypatch.setenv("FK_TEST_FAIL_ALLOC", str(n))
+        try:
+            b = fk.Batch(grids)
+        except fk.FkError as e:
+            assert e.status == fk.FK_ENOMEM, (n, e)
+            bfailed += 1
+            continue
+        finally:
+            monkeypatch.delenv("FK_TEST_FAIL_ALLOC")
+        b.step(3)
+        assert b.sync() == [fk.FK_OK, fk.FK_OK]
+        b.close()
+        break
+    assert bfailed >= 2
+    # the grids (released by every failed batch) and the device still work
+    g, o = make_pair(shape, prec=prec)
+    f0, sigma = strong_physics(g, o, shape, seed=41, c1f=0.05)
+    g.set_state(f0, sigma)
+    o.set_state(f0, sigma)
+    g.step(5)
+    o.step(5)
+    assert rel_l1(g.get_f(), o.get_f()) <= (1e-12 if prec == fk.FK_F64 else 1e-6)
+    for x in grids + [g]:
+        x.step(2)
+        x.close()
