@@ -19,19 +19,21 @@ namespace fk {
 namespace {
 
 constexpr int kMTile = 128;   // rows per CTA (one MMA M)
-constexpr int kKChunk = 64;   // K staged per round (4 MMAs of K = 16)
-constexpr int kNMax = 256;    // columns per CTA (one MMA N)
+constexpr int kNTile = 64;    // columns per CTA (one MMA N at most)
+constexpr int kNMax = 256;    // the largest N the entry points accept
+constexpr int kKChunk = 64;   // K per stage (4 MMAs of K = 16)
+constexpr int kGemmStages = 4;     // stages of the ring: K chunks in flight
 constexpr int kGemmThreads = 128;  // 4 warps: one per 32-lane slice of tensor memory
 constexpr int kCoreBytes = 128;    // one 8 x 16-byte core matrix
-// A tile: [kMTile/8 row groups][kKChunk/8 K groups] core matrices
+// a tile: [rows/8 row groups][kKChunk/8 K groups] core matrices
 constexpr int kLboBytes = kCoreBytes;                        // next core matrix along K
 constexpr int kSboBytes = (kKChunk / 8) * kCoreBytes;        // next 8-row group
 constexpr int kATileBytes = kMTile * kKChunk * 2;            // 16 KB
-constexpr int kBTileBytes = kNMax * kKChunk * 2;             // 32 KB
-// dynamic shared memory per CTA: the two tiles, padded so that at most two
-// CTAs share an SM (2 x 256 tensor-memory columns = all 512)
-constexpr int kGemmSmem = 100 * 1024;
-static_assert(kATileBytes + kBTileBytes <= kGemmSmem, "GEMM tiles exceed the shared memory");
+constexpr int kBTileBytes = kNTile * kKChunk * 2;            // 8 KB
+constexpr int kGemmStageBytes = kATileBytes + kBTileBytes;   // 24 KB
+// dynamic shared memory per CTA: the ring (two CTAs fit on an SM, with 2 x
+// 64 of its 512 tensor-memory columns)
+constexpr int kGemmSmem = kGemmStages * kGemmStageBytes;
 
 __device__ __forceinline__ uint16_t f32_to_bf16(float x) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));
@@ -43,83 +45,123 @@ __device__ __forceinline__ float gelu_grad(float z) {
          z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-// Copy rows [r0, r0 + rows) x K columns [k0, k0 + kKChunk) of a K-major bf16
-// matrix into the core-matrix layout; zeros outside [0, nrows) x [0, K).
+// 16-byte asynchronous copy global -> shared (cp.async); zeros when !full
+// (no byte of src is read then; src stays a valid address)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool full) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(dst)), "l"(src),
+               "r"(full ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// wait until at most n of this thread's copy groups are still pending
+__device__ __forceinline__ void cp_async_wait(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+  }
+}
+
+// Queue the copy of rows [r0, r0 + rows) x K columns [k0, k0 + kKChunk) of a
+// K-major bf16 matrix into the core-matrix layout; zeros outside
+// [0, nrows) x [0, K).
 __device__ __forceinline__ void stage_tile(unsigned char* dst, const uint16_t* src, long long ld,
                                            int r0, int rows, int nrows, int k0, int K) {
   const int vecs = rows * (kKChunk / 8);
   for (int v = threadIdx.x; v < vecs; v += kGemmThreads) {
     const int r = v / (kKChunk / 8), kc = v - (v / (kKChunk / 8)) * (kKChunk / 8);
     const int gr = r0 + r, gk = k0 + kc * 8;
-    uint4 val = make_uint4(0u, 0u, 0u, 0u);
-    if (gr < nrows && gk < K) val = *reinterpret_cast<const uint4*>(src + (long long)gr * ld + gk);
-    *reinterpret_cast<uint4*>(dst + ((r >> 3) * (kKChunk / 8) + kc) * kCoreBytes + (r & 7) * 16) = val;
+    const bool in = gr < nrows && gk < K;
+    cp_async16(dst + ((r >> 3) * (kKChunk / 8) + kc) * kCoreBytes + (r & 7) * 16,
+               in ? src + (long long)gr * ld + gk : src, in);
   }
 }
 
+// One CTA: rows [m0, m0 + 128) x columns [n0, n0 + Nc) of C.  The K chunks
+// stream through a ring of kGemmStages shared-memory stages: every thread
+// queues its part of a chunk's copies (cp.async) up to kGemmStages chunks
+// ahead; once a chunk has landed, one thread issues its four MMAs and
+// commits them to the stage's mbarrier, whose phase frees the stage for
+// the chunk kGemmStages later.  Each output element sums its K terms in
+// the same order whatever the grid, so results are deterministic.
 template <int EPI>
 __global__ void __launch_bounds__(kGemmThreads) gemm_tn_kernel(const __grid_constant__ GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sA = smem;
-  unsigned char* sB = smem + kATileBytes;
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar[kGemmStages];
   __shared__ uint32_t s_taddr;
-  __shared__ int s_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kMTile;
-  const int N = g.N, Nt = (g.N + 15) / 16 * 16;
-  const uint32_t ncols = Nt <= 32 ? 32u : (Nt <= 64 ? 64u : (Nt <= 128 ? 128u : 256u));
+  const int n0 = blockIdx.y * kNTile;
+  const int N = g.N;
+  const int Nc = min(kNTile, (N + 15) / 16 * 16 - n0);  // this CTA's columns, a multiple of 16
+  const uint32_t ncols = Nc <= 32 ? 32u : 64u;
   if (warp == 0) {
     tc::tmem_alloc(&s_taddr, ncols);
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(&bar, 1);
+    for (int q = 0; q < kGemmStages; q++) tc::mbar_init(&bar[q], 1);
     tc::fence_mbar_init();
-    s_ok = 1;
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = s_taddr;
-  const uint32_t idesc = tc::idesc_bf16_f32(kMTile, Nt);
-  uint32_t phase = 0;
+  const uint32_t idesc = tc::idesc_bf16_f32(kMTile, Nc);
+  const int nch = (g.K + kKChunk - 1) / kKChunk;
+  auto stage = [&](int c) {
+    unsigned char* sA = smem + (c % kGemmStages) * kGemmStageBytes;
+    stage_tile(sA, g.A, g.lda, m0, kMTile, g.M, c * kKChunk, g.K);
+    stage_tile(sA + kATileBytes, g.B, g.ldb, n0, Nc, N, c * kKChunk, g.K);
+    cp_async_commit();
+  };
+  for (int c = 0; c < min(kGemmStages, nch); c++) stage(c);
+  uint32_t parity = 0;  // bit q: the phase of stage q's mbarrier to wait for
   bool ok = true;
-  for (int k0 = 0; k0 < g.K && ok; k0 += kKChunk) {
-    stage_tile(sA, g.A, g.lda, m0, kMTile, g.M, k0, g.K);
-    stage_tile(sB, g.B, g.ldb, 0, Nt, N, k0, g.K);
+  for (int c = 0; c < nch && ok; c++) {
+    const int q = c % kGemmStages;
+    // chunk c's copies (later chunks' groups may still be in flight)
+    cp_async_wait(min(nch, c + kGemmStages) - 1 - c);
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     if (tid == 0) {
-      const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+      const uint32_t a0 = tc::smem_u32(smem + q * kGemmStageBytes), b0 = a0 + kATileBytes;
       for (int kk = 0; kk < kKChunk / 16; kk++) {
         // K step of 16 = two core matrices along K
         const uint64_t ad = tc::smem_desc(a0 + kk * 2 * kLboBytes, kLboBytes, kSboBytes);
         const uint64_t bd = tc::smem_desc(b0 + kk * 2 * kLboBytes, kLboBytes, kSboBytes);
-        tc::mma_bf16(taddr, ad, bd, idesc, (k0 > 0 || kk > 0) ? 1u : 0u);
+        tc::mma_bf16(taddr, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
       }
-      tc::mma_commit(&bar);
+      tc::mma_commit(&bar[q]);
     }
-    // the MMAs have read the tiles (and written D) once the phase completes
-    ok = tc::mbar_wait(&bar, phase);
-    phase ^= 1;
-    tc::fence_after_sync();
-    if (!__syncthreads_and(ok)) ok = false;
+    if (c + kGemmStages < nch || c == nch - 1) {
+      // the stage is free (or, after the last chunk, D is complete) once
+      // its MMAs have run
+      ok = tc::mbar_wait(&bar[q], (parity >> q) & 1u);
+      parity ^= 1u << q;
+      tc::fence_after_sync();
+      if (!__syncthreads_and(ok)) ok = false;
+      if (ok && c + kGemmStages < nch) stage(c + kGemmStages);
+    }
   }
+  cp_async_wait(0);  // nothing left in flight into shared memory
   if (ok) {
     // epilogue: warp w holds rows m0 + 32 w + lane (tensor-memory lanes)
     const int row = m0 + warp * 32 + lane;
     const bool live = row < g.M;
-    for (int c0 = 0; c0 < Nt; c0 += 16) {
+    for (int c0 = 0; c0 < Nc; c0 += 16) {
       uint32_t r[16];
       tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
       tc::tmem_wait_ld();
       if (!live) continue;
 #pragma unroll
       for (int e = 0; e < 16; e++) {
-        const int col = c0 + e;
+        const int col = n0 + c0 + e;
         if (col >= N) break;
         float v = __uint_as_float(r[e]);
         if (EPI == kEpiF32) {
@@ -141,8 +183,10 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tn_kernel(const __grid_cons
     }
   } else if (tid == 0) {
     atomicOr(g.err, 1);
-    // a second bounded wait for MMAs still in flight before the memory is freed
-    tc::mbar_wait(&bar, phase ^ 1);
+    // a second bounded wait for MMAs still in flight before the memory is
+    // freed: the last chunk's commit completes after every earlier one
+    const int q = (nch - 1) % kGemmStages;
+    tc::mbar_wait(&bar[q], (parity >> q) & 1u);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -157,7 +201,7 @@ cudaError_t launch_gemm_epi(const GemmArgs& g, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(gemm_tn_kernel<EPI>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
   if (e != cudaSuccess) return e;
-  const int grid = (g.M + kMTile - 1) / kMTile;
+  const dim3 grid((g.M + kMTile - 1) / kMTile, ((g.N + 15) / 16 * 16 + kNTile - 1) / kNTile);
   gemm_tn_kernel<EPI><<<grid, kGemmThreads, kGemmSmem, s>>>(g);
   return cudaGetLastError();
 }
