@@ -199,10 +199,11 @@ fk_status fk_set_reflection(fk_grid *grid, double R_f);
  * from its own input state, so the surface charge and the wall ledger terms
  * take dt/2 of the fluxes of f^n and dt/2 of those of the state after the
  * velocity step.  Sec. 2 states only an explicit upwind update; the split
- * forms run as two (Lie) or three (Strang) passes over f (the direct-load
- * kernel and one more buffer of f), and grids using them cannot join a
- * batch.  FK_EINVAL for another value; FK_ESTATE while the grid is in a
- * batch. */
+ * forms run as two (Lie) or three (Strang) passes over f through one more
+ * buffer of f: each pass is the streaming step kernel with the other terms'
+ * coefficients zeroed (the direct-load kernel on grids too wide for it),
+ * and grids using them cannot join a batch.  FK_EINVAL for another value;
+ * FK_ESTATE while the grid is in a batch. */
 #define FK_SCHEME_UNSPLIT 0
 #define FK_SCHEME_LIE 1
 #define FK_SCHEME_STRANG 2
