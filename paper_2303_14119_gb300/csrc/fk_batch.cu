@@ -815,7 +815,7 @@ fk_status autotune(fk_batch* b, int32_t steps_per_trial, int64_t* steps_taken, b
         std::vector<int> caps = keep_caps;
         bool cuts = false;
         for (int i = 0; i < b->n; i++)
-          if (b->bucket[i] == q) {
+          if (b->bucket[i] == q && !b->grids[i]->geom.half) {  // half units keep their tiles
             const fk_grid* g = b->grids[i];
             caps[i] = std::max(4, cells / g->pitch);
             cuts |= caps[i] < std::max(g->geom.ti_neg, g->geom.ti_pos);
