@@ -627,7 +627,10 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   // the whole march; per vector its offset in a stage and in a plane
   int soff[M];  // offset from the tile's first cell (low 24 bits) and row (top byte)
   const int gbase = i0 * pitch;  // the tile's first cell in a plane
-  unsigned valid = 0, zleft = 0;  // bit m: vector m exists / starts a row
+  // bit m: vector m exists / starts a row; zleft bit 16 + m: vector m is
+  // the last of a padded row (pitch > nv2: only a row's last vector holds
+  // padding, its elements from nv2 - (pitch - VEC) on)
+  unsigned valid = 0, zleft = 0;
   T ax[M];
   T xr[M][VEC];
 #pragma unroll
@@ -639,6 +642,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       const int r = v / QV, qv = v - r * QV;
       valid |= 1u << m;
       if (qv == 0) zleft |= 1u << m;
+      if (PADDED && qv == QV - 1 && pitch != nv2) zleft |= 1u << (16 + m);
       soff[m] = (r * pitch + qv * VEC) | (r << 24);
       const T cx = sizeof(T) == 8 ? (T)a.tab.cx[i0 + r] : (T)a.tab.cx32[i0 + r];
       ax[m] = cx < (T)0 ? -cx : cx;
@@ -780,7 +784,8 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
           T se = src.e[e];
           if (BGK && sizeof(T) == 4) se = fmaf(-(float)bgk_a, (float)f, (float)se);  // loss dt nu f
           T fn = upd<T>(f, xr[m][e], nb.e[e], fw, ax[m], a1, a2, se, d);
-          if (PADDED && (so % pitch) + e >= nv2) fn = (T)0;  // row padding stays zero
+          if (PADDED && (zleft >> (16 + m) & 1) && e >= nv2 - (pitch - VEC))
+            fn = (T)0;  // row padding stays zero
           out.e[e] = fn;
           xr[m][e] = f;  // x-upwind value for the next plane is f^n here
           if (sizeof(T) == 4) {
