@@ -231,7 +231,8 @@ def time_arm(fk, torch, w, precision, f0, steps, warmup, dist, device, batch=Tru
         if chunk_len > 0:
             b.set_chunks([chunk_len] * len(grids))
         else:
-            tuned = b.autotune(2, tiles=tile_rows < 0)
+            # four steps per trial: the tile plans differ by about 1 %
+            tuned = b.autotune(4, tiles=tile_rows < 0)
 
     def advance(n):
         if b is not None:
