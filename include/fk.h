@@ -337,8 +337,8 @@ fk_status fk_kernel_timing(fk_grid *grid, int64_t *launches, double *total_ms);
  * overwrites the slots it uses before reading them, so nothing needs
  * clearing; calls that overlap on the GPU (different streams or devices
  * sharing one context) race on it and must be ordered by the caller.
- * The first call on each device looks up the array's device address with
- * that device current; make that first call before any stream capture.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current.
  * The address is kept for the life of the process: after a reset of the
  * device's primary context (cudaDeviceReset) the entry point must not be
  * called again in that process.
