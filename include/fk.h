@@ -460,11 +460,12 @@ fk_status fk_batch_get_chunks(const fk_batch *batch, int32_t *chunk_len);
 fk_status fk_batch_set_chunks(fk_batch *batch, const int32_t *chunk_len);
 
 /* Batch facts, FK_BATCH_INFO_LEN doubles: grids, work units of one batch
- * step, finalize blocks, dynamic shared memory per CTA (bytes), CTAs per
- * SM, phase-space cells of all grids, size buckets, batch steps enqueued,
- * CTAs of whole-CTA units, CTAs of half units (two to a CTA).  A batch step
- * launches the step kernel once per nonzero CTA count, then the finalize
- * kernel.  Host-side, no synchronisation. */
+ * step, CTAs of the finalize launch (one per 128 planes of a grid with more
+ * than 128, one per four grids of at most 128), dynamic shared memory per
+ * CTA (bytes), CTAs per SM, phase-space cells of all grids, size buckets,
+ * batch steps enqueued, CTAs of whole-CTA units, CTAs of half units (two to
+ * a CTA).  A batch step launches the step kernel once per nonzero CTA
+ * count, then the finalize kernel.  Host-side, no synchronisation. */
 #define FK_BATCH_INFO_LEN 10
 fk_status fk_batch_info(const fk_batch *batch, double *out);
 

@@ -59,8 +59,9 @@ struct fk_batch {
   int n_units = 0, max_units = 0;
   int4* d_pairs = nullptr;     // [max_pairs] CTAs of two half units, largest first
   int n_pairs = 0, max_pairs = 0;
-  int2* d_fblk = nullptr;      // [n_fblk] finalize blocks
-  int n_fblk = 0;
+  int2* d_fblk = nullptr;      // [n_fblk] finalize entries: n_fmulti (grid, block)
+  int n_fblk = 0;               // pairs of the grids of several finalize blocks,
+  int n_fmulti = 0;             // then (grid, -1) for those of one
   size_t smem = 0;             // dynamic shared memory per CTA (whole-CTA units)
   int half_bytes = 0;          // shared memory of one half unit's region
   int per_sm = 0, sms = 0;      // CTAs per SM (the smaller of the two layouts), SMs
@@ -331,7 +332,7 @@ cudaError_t enqueue_batch_step(fk_batch* b, int p, cudaStream_t s, cudaEvent_t e
     e = cudaStreamWaitEvent(s, b->pending, 0);
     b->pending = nullptr;
   }
-  if (e == cudaSuccess) e = launch_finalize_batch(inst, b->d_fblk, b->n_fblk, s);
+  if (e == cudaSuccess) e = launch_finalize_batch(inst, b->d_fblk, b->n_fmulti, b->n_fblk, s);
   return e;
 }
 
@@ -498,13 +499,16 @@ fk_status fk_batch_create(fk_grid* const* grids, int32_t n, void* cuda_stream, f
   CREATE_B(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
   CREATE_B(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
   CREATE_B(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev));
-  std::vector<int2> fblk;
+  std::vector<int2> fblk, fone;
   for (int i = 0; i < n; i++) {
     fk_grid* g = gs[i];
     if (g->pitch != g->nv2) b->padded = true;
     if (g->prm.collisions) b->bgk = true;
     b->cells += (double)g->nx * g->nv1 * g->nv2;
-    for (int q = 0; q < finalize_blocks(g->nx); q++) fblk.push_back(make_int2(i, q));
+    if (finalize_blocks(g->nx) == 1)
+      fone.push_back(make_int2(i, -1));
+    else
+      for (int q = 0; q < finalize_blocks(g->nx); q++) fblk.push_back(make_int2(i, q));
     DevState st;
     const fk_status s = sync_state(g, &st);  // the grid's own work is done
     if (s != FK_OK) {
@@ -518,6 +522,8 @@ fk_status fk_batch_create(fk_grid* const* grids, int32_t n, void* cuda_stream, f
     free_batch(b);
     return bfail(nullptr, FK_EINVAL, "the grids' shared-memory plans do not fit an SM");
   }
+  b->n_fmulti = (int)fblk.size();
+  fblk.insert(fblk.end(), fone.begin(), fone.end());
   b->n_fblk = (int)fblk.size();
   CREATE_B(hooked_alloc(reinterpret_cast<void**>(&b->d_inst), 2 * (size_t)n * sizeof(BatchInst)));
   CREATE_B(hooked_alloc(reinterpret_cast<void**>(&b->d_fblk), fblk.size() * sizeof(int2)));
@@ -709,7 +715,7 @@ fk_status fk_batch_info(const fk_batch* b, double* out) {
   if (!pairs.empty() && pairs.back().z < 0) halves -= 1;
   out[0] = b->n;
   out[1] = (double)whole.size() + halves;
-  out[2] = b->n_fblk;
+  out[2] = finalize_batch_ctas(b->n_fmulti, b->n_fblk);
   out[3] = (double)std::max(b->smem, 2 * (size_t)b->half_bytes);
   out[4] = b->per_sm;
   out[5] = b->cells;

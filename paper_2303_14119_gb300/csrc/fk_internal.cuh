@@ -218,10 +218,13 @@ cudaError_t launch_step_stream_batch(const BatchInst* inst, const int2* units, i
                                      const int4* pairs, int n_pairs, int precision, bool padded,
                                      bool bgk, size_t smem_bytes, int half_bytes,
                                      cudaStream_t s);
-// Batched finalize (step mode): block b finalizes block blocks[b].y of grid
-// blocks[b].x; every grid's blocks 0 .. finalize_blocks(nx) - 1 appear once.
-cudaError_t launch_finalize_batch(const BatchInst* inst, const int2* blocks, int n_blocks,
-                                  cudaStream_t s);
+// Batched finalize (step mode) over n_entries entries: the first n_multi
+// are (grid, block) pairs, one CTA each, listing blocks 0 ..
+// finalize_blocks(nx) - 1 of every grid with more than one; the rest are
+// (grid, -1), one warp each, four to a CTA, for the grids of one block.
+cudaError_t launch_finalize_batch(const BatchInst* inst, const int2* blocks, int n_multi,
+                                  int n_entries, cudaStream_t s);
+int finalize_batch_ctas(int n_multi, int n_entries);
 int finalize_blocks(int nx);
 cudaError_t launch_finalize(const StepArgs& a, double* ne, double* Ex, double* c1,
                             float* c1_32, double* hist, const FinScratch& fs, int mode,

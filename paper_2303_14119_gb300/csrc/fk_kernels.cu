@@ -654,17 +654,208 @@ finalize_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ FinO
   finalize_body(a, o, blockIdx.x, gridDim.x, mode);
 }
 
-// Many grids in one launch (step mode): block b is block blocks[b].y of grid
-// blocks[b].x; each grid elects its own last block with its own counter.
+// One grid of at most kFinThreads planes (one finalize block) in step mode,
+// on one warp: the arithmetic of finalize_body run with a single block, in
+// the same fixed order -- each plane's partials in order, per 32-plane group
+// the warp scan and shuffle trees of that group's warp, the group totals
+// folded as block_sum's warp 0 folds them, phase B's scans over one block
+// total -- so the new state is bit for bit the one finalize_body gives.
+// A single block needs no last-block election, so the atomic counter, the
+// fences and the round trip of the prefix sums through FinScratch go, and
+// the group values stay in registers.
+__device__ __forceinline__ void finalize_warp_body(const StepArgs& a, const FinOut& o,
+                                                   const int lane) {
+  constexpr int G = kFinThreads / 32;  // 32-plane groups
+  const Params& p = *a.prm;
+  DevState* st = a.st;
+  if (st->flags) return;
+  const int nx = a.nx, nu = a.part.nu;
+  // ---- phase A
+  double nk[G], lk[G];
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    const int k = 32 * g + lane;
+    nk[g] = 0.0;
+    lk[g] = 0.0;
+    if (k < nx) {
+      const double* pn = a.part.n + (size_t)k * nu;
+      const double* pl = a.part.lv + (size_t)k * nu;
+      double sn = 0.0, sl = 0.0;
+      int u = 0;
+      for (; u + 8 <= nu; u += 8) {
+        double xn[8], xl[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          xn[q] = pn[u + q];
+          xl[q] = pl[u + q];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          sn += xn[q];
+          sl += xl[q];
+        }
+      }
+      for (; u < nu; u++) {
+        sn += pn[u];
+        sl += pl[u];
+      }
+      nk[g] = sn * p.dvv;
+      lk[g] = sl;
+      o.ne[k] = nk[g];
+    }
+  }
+  double pre[G];
+  double woff = 0.0, btot = 0.0, blv = 0.0;
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    double incl = nk[g];
+    for (int d = 1; d < 32; d <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.0;
+    pre[g] = woff + excl;
+    woff += __shfl_sync(0xffffffffu, incl, 31);
+    double vn = nk[g], vl = lk[g];
+    for (int d = 16; d > 0; d >>= 1) {
+      vn += __shfl_down_sync(0xffffffffu, vn, d);
+      vl += __shfl_down_sync(0xffffffffu, vl, d);
+    }
+    vn = __shfl_sync(0xffffffffu, vn, 0);
+    vl = __shfl_sync(0xffffffffu, vl, 0);
+    if (lane == g) {
+      btot = vn;
+      blv = vl;
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    btot += __shfl_down_sync(0xffffffffu, btot, d);
+    blv += __shfl_down_sync(0xffffffffu, blv, d);
+  }
+  // ---- phase B: finalize_body's last-block work with one block total
+  // (valid in lane 0), the other lanes' entries zero
+  const double b0 = lane == 0 ? btot : 0.0;
+  double l = (lane == 0 ? blv : 0.0) + 0.0;
+  double i0s = b0;
+  for (int d = 1; d < 32; d <<= 1) {
+    const double y0 = __shfl_up_sync(0xffffffffu, i0s, d);
+    if (lane >= d) i0s += y0;
+  }
+  const double half = __shfl_sync(0xffffffffu, i0s, 31);
+  const double boff0 = __shfl_sync(0xffffffffu, i0s - b0, 0);
+  const double ntot_raw = half + 0.0;  // the empty second half of the scan
+  double pe = 0.0, see = 0.0, vac = 0.0;
+  for (int u = lane; u < nu; u += 32) {
+    pe += a.part.pe[u];
+    see += a.part.see[u];
+    vac += a.part.vac[u];
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    l += __shfl_down_sync(0xffffffffu, l, d);
+    pe += __shfl_down_sync(0xffffffffu, pe, d);
+    see += __shfl_down_sync(0xffffffffu, see, d);
+    vac += __shfl_down_sync(0xffffffffu, vac, d);
+  }
+  DevState d = *st;
+  if (lane == 0) {
+    const double ntot = ntot_raw * p.dx;
+    pe *= p.dvv;
+    see = p.see_enabled ? see * p.dvv * (1.0 - p.refl) : 0.0;
+    vac *= p.dvv;
+    const double lv = l * p.lv_scale;
+    d.cum_emit += p.dt * (d.g_see + p.refl * d.g_pe);
+    d.cum_see += p.dt * d.g_see;
+    d.cum_pe += p.dt * d.g_pe;
+    d.cum_vac += p.dt * d.g_vac;
+    d.cum_lv += p.dt * lv;
+    d.cum_inj += p.dt * p.inj;
+    d.sigma += kQe * p.dt * (d.g_see - (1.0 - p.refl) * d.g_pe);
+    d.step += 1;
+    d.g_pe = pe;
+    d.g_see = see;
+    d.g_vac = vac;
+    d.n_tot = ntot;
+    if (!isfinite(pe) || !isfinite(see) || !isfinite(vac) || !isfinite(ntot) ||
+        !isfinite(d.sigma))
+      d.flags |= kFlagNumeric;
+    *st = d;
+  }
+  const double e_wall = __shfl_sync(0xffffffffu, d.sigma, 0) * p.ex_sigma;
+  double cmax = 0.0, ex0 = 0.0;
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    const int kk = 32 * g + lane;
+    if (kk >= nx) continue;
+    const double below = boff0 + pre[g];
+    const double n_k = nk[g];
+    const double e = p.self_consistent ? e_wall - p.ex_n * (below + 0.5 * n_k) : p.Ex_ext;
+    if (g == 0) ex0 = e;
+    o.Ex[kk] = e;
+    const double c = p.c1_per_ex * e;
+    o.c1[kk] = c;
+    o.c1_32[kk] = (float)c;
+    double cfl = fabs(c);
+    if (p.collisions) {
+      const double ak = n_k > 0.0 ? p.bgk_c * n_k : 0.0;
+      a.bgk[kk] = ak;
+      a.bgk[nx + kk] = ak * n_k;
+      a.bgk32[kk] = (float)ak;
+      a.bgk32[nx + kk] = (float)(ak * n_k);
+      cfl += ak;
+    }
+    cmax = fmax(cmax, cfl);
+  }
+  for (int q = 16; q > 0; q >>= 1) cmax = fmax(cmax, __shfl_down_sync(0xffffffffu, cmax, q));
+  if (lane == 0) {
+    if (cmax + p.cx_max + fabs(p.c2) > 1.0 + 1e-12) d.flags |= kFlagCfl;
+    const long long row = d.step;
+    const long long cap = p.hist_cap;
+    double rr[FK_HISTORY_COLS] = {(double)row, (double)row * p.dt, d.sigma, d.g_pe,
+                                  d.g_see, d.g_vac, d.n_tot, ex0};
+    double* r = o.hist + (size_t)(row % cap) * FK_HISTORY_COLS;
+    for (int q = 0; q < FK_HISTORY_COLS; q++) r[q] = rr[q];
+    if (row + 1 > d.hist_count) d.hist_count = row + 1;
+    if (d.sat_step < 0 && row >= p.sat_window && p.sat_window < cap) {
+      const double* h = o.hist + (size_t)((row - p.sat_window) % cap) * FK_HISTORY_COLS;
+      bool ok = true;
+      for (int q = 2; q <= 4; q++)
+        if (!(fabs(rr[q] - h[q]) <= p.sat_tol * fabs(rr[q]))) ok = false;
+      if (ok) d.sat_step = row;
+    }
+    st->flags = d.flags;
+    st->hist_count = d.hist_count;
+    st->sat_step = d.sat_step;
+  }
+}
+
+// Many grids in one launch (step mode).  Blocks below n_multi run
+// finalize_body: block b is block blocks[b].y of grid blocks[b].x, and each
+// grid elects its own last block with its own counter.  The grids of one
+// finalize block (entries blocks[n_multi ..], y = -1) go four to a block,
+// one warp each.
 __global__ void __launch_bounds__(kFinThreads)
-finalize_batch_kernel(const BatchInst* __restrict__ inst, const int2* __restrict__ blocks) {
-  __shared__ BatchInst bi;
-  const int2 m = blocks[blockIdx.x];
-  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(inst + m.x);
-  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&bi);
-  for (int w = threadIdx.x; w < (int)(sizeof(BatchInst) / 8); w += blockDim.x) dst[w] = src[w];
-  __syncthreads();
-  finalize_body(bi.a, bi.o, m.y, (bi.a.nx + kFinThreads - 1) / kFinThreads, kModeStep);
+finalize_batch_kernel(const BatchInst* __restrict__ inst, const int2* __restrict__ blocks,
+                      int n_multi, int n_entries) {
+  constexpr int G = kFinThreads / 32;
+  __shared__ BatchInst bi[G];
+  if ((int)blockIdx.x < n_multi) {
+    const int2 m = blocks[blockIdx.x];
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(inst + m.x);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&bi[0]);
+    for (int w = threadIdx.x; w < (int)(sizeof(BatchInst) / 8); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    finalize_body(bi[0].a, bi[0].o, m.y, (bi[0].a.nx + kFinThreads - 1) / kFinThreads, kModeStep);
+    return;
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = n_multi + ((int)blockIdx.x - n_multi) * G + w;
+  if (q >= n_entries) return;
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(inst + blocks[q].x);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&bi[w]);
+  for (int i = lane; i < (int)(sizeof(BatchInst) / 8); i += 32) dst[i] = src[i];
+  __syncwarp();
+  finalize_warp_body(bi[w].a, bi[w].o, lane);
 }
 
 // Strang step, after the velocity pass (one warp): fold the wall and vacuum
@@ -717,10 +908,15 @@ cudaError_t launch_finalize(const StepArgs& a, double* ne, double* Ex, double* c
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_batch(const BatchInst* inst, const int2* blocks, int n_blocks,
-                                  cudaStream_t s) {
-  if (n_blocks <= 0) return cudaSuccess;
-  finalize_batch_kernel<<<n_blocks, kFinThreads, 0, s>>>(inst, blocks);
+int finalize_batch_ctas(int n_multi, int n_entries) {
+  return n_multi + (n_entries - n_multi + kFinThreads / 32 - 1) / (kFinThreads / 32);
+}
+
+cudaError_t launch_finalize_batch(const BatchInst* inst, const int2* blocks, int n_multi,
+                                  int n_entries, cudaStream_t s) {
+  const int n_ctas = finalize_batch_ctas(n_multi, n_entries);
+  if (n_ctas <= 0) return cudaSuccess;
+  finalize_batch_kernel<<<n_ctas, kFinThreads, 0, s>>>(inst, blocks, n_multi, n_entries);
   return cudaGetLastError();
 }
 

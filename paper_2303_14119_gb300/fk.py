@@ -703,7 +703,7 @@ def fk_batch_set_chunks(b, chunk_len):
 def fk_batch_info(b):
     out = np.empty(FK_BATCH_INFO_LEN)
     _bcheck(load().fk_batch_info(b, _dp(out)), "fk_batch_info", b)
-    return dict(grids=int(out[0]), units=int(out[1]), finalize_blocks=int(out[2]),
+    return dict(grids=int(out[0]), units=int(out[1]), finalize_ctas=int(out[2]),
                 smem_bytes=int(out[3]), ctas_per_sm=int(out[4]), cells=float(out[5]),
                 buckets=int(out[6]), steps=int(out[7]), whole_ctas=int(out[8]),
                 half_ctas=int(out[9]),

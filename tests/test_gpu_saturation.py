@@ -89,3 +89,42 @@ def test_fp32_saturated_charge_within_1e4_of_fp64(which):
     assert abs(h32[n, 2] / h64[n, 2] - 1.0) <= 1e-4
     # saturation detected within a few hundred steps of the FP64 path's
     assert abs(sat32 - sat64) <= 0.05 * w["sat_window"]
+
+
+def test_batched_runs_saturate_at_the_oracle_steps_bitwise_as_alone():
+    """Both saturating runs in one batch, beside a grid of several finalize
+    blocks (nx = 300) and a grid of five planes: the batch's finalize (one
+    warp for each grid of at most 128 planes, four to a CTA; whole blocks
+    for the others) fires the convergence test at the oracle's saturated
+    steps, and the saturating grids' histories are those of the grids
+    stepped alone, bit for bit."""
+    runs = golden()["runs"]
+    w = synth.WORKLOADS[NAME]
+    n = max(r["sat_step"] for r in runs) + 1
+    alone = [run(r["Ey"], fk.FK_F64, n) for r in runs]
+
+    def grid(nx, Ey):
+        g = fk.Grid(nx, w["nv1"], w["nv2"], w["h_max"], -w["v1_span"], w["v1_span"],
+                    -w["v2_span"], w["v2_span"], cfl=w["cfl"], precision=fk.FK_F64,
+                    history_capacity=1 << 18)
+        g.set_fields(Ey)
+        g.set_see(w["delta_max"], w["A_max"], w["k_s"], w["T_se"])
+        g.set_source(w["J"], w["x_lo"], w["x_hi"], w["T_fe"])
+        g.set_convergence(w["sat_window"], w["sat_tol"])
+        return g
+
+    sat_grids = [grid(w["nx"], r["Ey"]) for r in runs]
+    grids = [grid(300, runs[0]["Ey"]), sat_grids[0], grid(5, runs[1]["Ey"]), sat_grids[1]]
+    with fk.Batch(grids) as b:
+        # one finalize CTA per 128 planes of the 300-plane grid, one for the
+        # three grids of at most 128
+        assert b.info()["finalize_ctas"] == 3 + 1
+        b.step(n)
+        status = b.sync()
+    assert status[1] == fk.FK_OK and status[3] == fk.FK_OK
+    for g, r, (sat, hist) in zip(sat_grids, runs, alone):
+        step, sat_b = g.step_count()
+        assert step == n and sat_b == sat == r["sat_step"]
+        assert np.array_equal(g.history(n + 1), hist)
+    for g in grids:
+        g.close()
