@@ -708,6 +708,9 @@ __device__ __forceinline__ void finalize_warp_body(const StepArgs& a, const FinO
   double woff = 0.0, btot = 0.0, blv = 0.0;
 #pragma unroll
   for (int g = 0; g < G; g++) {
+    // a group past the last plane: its sums are +0 (lane g keeps 0.0) and
+    // its scan feeds no plane
+    if (32 * g >= nx) break;
     double incl = nk[g];
     for (int d = 1; d < 32; d <<= 1) {
       const double y = __shfl_up_sync(0xffffffffu, incl, d);

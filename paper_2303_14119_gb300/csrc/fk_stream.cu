@@ -28,6 +28,7 @@
 //
 // Per cell: f' = f + |c_x|(f_ux - f) + |c_1|(f_u1 - f) + |c_2|(f_u2 - f) + dt S
 // (FP32: increment form) or the convex form of the same sum (FP64).
+#include <type_traits>
 #include <stdint.h>
 
 #include "fk_internal.cuh"
@@ -343,20 +344,49 @@ __device__ __forceinline__ void unit_sync(int bar) {
   }
 }
 
+// A pointer field of the step arguments read where it is used.  SA: the
+// arguments sit in the CTA's shared memory (batched kernels), and a read
+// there at each use (an LDS) keeps the pointer out of the registers of the
+// march; otherwise they are kernel parameters, which instructions take
+// directly.
+template <bool SA, typename X>
+__device__ __forceinline__ X arg_at_use(const X& field) {
+  static_assert(sizeof(X) == 8, "pointer fields");
+  if constexpr (SA) {
+    unsigned long long v;
+    asm volatile("ld.shared.b64 %0, [%1];"
+                 : "=l"(v)
+                 : "r"((unsigned)__cvta_generic_to_shared(&field)));
+    return reinterpret_cast<X>(v);
+  } else {
+    return field;
+  }
+}
+
 // One unit (tile t, chunk) of a grid on NT consumer threads (kThreads, or
 // kHalfThreads for a half-CTA unit) plus a producer warp; tid: the thread's
 // index within the unit, bar: the unit's barrier; smem is the unit's shared
 // memory past its argument slot.  BGK: the grid has the electron-electron
-// collision term of Eq. 3 switched on.
-template <typename T, bool PADDED, bool BGK, int NT>
+// collision term of Eq. 3 switched on.  SA: a is in shared memory.
+template <typename T, bool PADDED, bool BGK, int NT, bool SA>
 __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, const int chunk,
                                             unsigned char* smem, const int tid, const int bar) {
   constexpr int NW = NT / 32;  // consumer warps
   constexpr int NS = unit_stages<NT>();  // stages of the ring
   constexpr int VEC = Vec<T>::N;
   constexpr int M = unit_vectors<NT, (int)sizeof(T)>();
+  // per-plane pointer reads from the shared-memory arguments at their use
+  // where the march runs out of registers (half units, the collision
+  // variant); elsewhere the pointers stay in registers (measured faster)
+  constexpr bool SAU = SA && (NT == kHalfThreads || BGK);
+  // compact index arithmetic (an item's plane in one multiply-add, 32-bit
+  // stage and plane sizes): faster in the half-unit, padded-row and
+  // collision variants, 1 % slower in the plain whole-CTA one (measured)
+  constexpr bool COMPACT = NT == kHalfThreads || PADDED || BGK;
+  using StageSz = std::conditional_t<COMPACT, unsigned, size_t>;  // < 227 KB
+  using PlaneSz = std::conditional_t<COMPACT, int, size_t>;
   const Geom& gm = a.geom;
-  const size_t sbytes = stage_bytes<T>(gm.stage_elems);
+  const StageSz sbytes = (StageSz)stage_bytes<T>(gm.stage_elems);
   unsigned char* stage_base = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * sbytes);
   uint64_t* empty = full + NS;
@@ -391,10 +421,17 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   const int k_up = k_first - dir;
   const bool prime = k_up >= 0 && k_up < nx;
   const int n_items = (s1 - s0) + (prime ? 1 : 0);
+  // item q visits plane k_first + dir (q - 1) after a prime item (q = 0:
+  // k_up), plane k_first + dir q without one
+  const int k_item0 = prime ? k_up : k_first;
   auto item_plane = [&](int q) -> int {
-    const int s = s0 + q - (prime ? 1 : 0);
-    if (s < s0) return k_up;
-    return dir > 0 ? s : nx - 1 - s;
+    if constexpr (COMPACT) {
+      return k_item0 + dir * q;
+    } else {
+      const int s = s0 + q - (prime ? 1 : 0);
+      if (s < s0) return k_up;
+      return dir > 0 ? s : nx - 1 - s;
+    }
   };
 
   if (sizeof(T) == 4) {  // source factors of this tile (FP32 grids)
@@ -427,7 +464,9 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
   const Params& p = *a.prm;
   const T* __restrict__ fin = static_cast<const T*>(a.f_in);
   T* __restrict__ fout = static_cast<T*>(a.f_out);
-  const size_t plane = (size_t)nv1 * pitch;
+  // cells of a plane (below 2^31, as a streamed row holds at most one
+  // unit's cells, 7168, and nv1 <= 65536)
+  const PlaneSz plane = (PlaneSz)nv1 * pitch;
   const int QV = pitch / VEC;  // vectors per row
   const int stage_n = gm.stage_elems;     // elements of a stage
   const size_t f_n = (size_t)nx * plane;  // elements of f
@@ -683,8 +722,9 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
     const int k = item_plane(q);
     // per-plane values and the source row (L2-resident table) are fetched
     // before waiting for the stage, so their latency overlaps the wait
-    const float c1f = a.c1_32[k];
-    const T a1 = c1f == 0.f ? (T)0 : (sizeof(T) == 8 ? (T)fabs(a.c1[k]) : (T)fabsf(c1f));
+    const float c1f = arg_at_use<SAU>(a.c1_32)[k];
+    const T a1 =
+        c1f == 0.f ? (T)0 : (sizeof(T) == 8 ? (T)fabs(arg_at_use<SAU>(a.c1)[k]) : (T)fabsf(c1f));
     const bool band = compute && k >= band_lo && k < band_hi;
     // source term: FP32 grids rebuild it from the separable factors in
     // shared memory, FP64 grids load the 2D table in the update loop
@@ -692,8 +732,9 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
     // grids take it from the producer's row tables)
     T bgk_a = (T)0, bgk_s = (T)0;
     if (BGK && sizeof(T) == 4) {
-      bgk_a = (T)a.bgk32[k];
-      bgk_s = (T)a.bgk32[nx + k];
+      const float* b32 = arg_at_use<SAU>(a.bgk32);
+      bgk_a = (T)b32[k];
+      bgk_s = (T)b32[nx + k];
     }
     const bool ok = mbar_wait(&full[st], (uint32_t)((q / NS) & 1), wlim);
     if (__any_sync(0xffffffffu, !ok)) {
@@ -721,7 +762,7 @@ __device__ __forceinline__ void stream_unit(const StepArgs& a, const int t, cons
       const double* dg = dgl + st * kMaxTileRows;
       T sum_n = (T)0;
       float sh_ = 0.f, sc_ = 0.f, sl_ = 0.f;  // FP64 grids: compensated FP32 sum
-      T* oplane = fout + (size_t)k * plane;
+      T* oplane = (SAU ? static_cast<T*>(arg_at_use<SAU>(a.f_out)) : fout) + (size_t)k * plane;
 #pragma unroll
       for (int m = 0; m < M; m++) {
         if (NT * m >= rows * QV) break;  // no thread of the unit has vector m (uniform)
@@ -867,7 +908,7 @@ template <typename T, bool PADDED, bool BGK>
 __global__ void __launch_bounds__(kBlock, 2) step_stream_kernel(const __grid_constant__ StepArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nt = a.geom.n_tiles;
-  stream_unit<T, PADDED, BGK, kThreads>(a, blockIdx.x % nt, blockIdx.x / nt, smem + kArgsBytes,
+  stream_unit<T, PADDED, BGK, kThreads, false>(a, blockIdx.x % nt, blockIdx.x / nt, smem + kArgsBytes,
                                         threadIdx.x, 0);
 }
 
@@ -882,7 +923,7 @@ step_stream_half_kernel(const __grid_constant__ StepArgs a) {
   const int u = 2 * blockIdx.x + h;
   if (u >= nt * a.geom.n_chunks) return;
   unsigned char* region = smem + h * half_region_bytes<T>(a.geom.stage_elems, a.pitch);
-  stream_unit<T, PADDED, BGK, kHalfThreads>(a, u % nt, u / nt, region + kArgsBytes,
+  stream_unit<T, PADDED, BGK, kHalfThreads, false>(a, u % nt, u / nt, region + kArgsBytes,
                                             threadIdx.x - h * kHalfBlock, 1 + h);
 }
 
@@ -900,7 +941,7 @@ step_stream_batch_kernel(const BatchInst* __restrict__ inst, const int2* __restr
   __syncthreads();
   const StepArgs& a = *reinterpret_cast<const StepArgs*>(smem);
   const int nt = a.geom.n_tiles;
-  stream_unit<T, PADDED, BGK, kThreads>(a, u.y % nt, u.y / nt, smem + kArgsBytes, threadIdx.x, 0);
+  stream_unit<T, PADDED, BGK, kThreads, true>(a, u.y % nt, u.y / nt, smem + kArgsBytes, threadIdx.x, 0);
 }
 
 // Many grids in one launch, half units: CTA b runs unit pairs[b].y of grid
@@ -925,7 +966,7 @@ step_stream_batch_half_kernel(const BatchInst* __restrict__ inst, const int4* __
   if (g < 0) return;  // the idle half of a CTA with one unit
   const StepArgs& a = *reinterpret_cast<const StepArgs*>(region);
   const int nt = a.geom.n_tiles;
-  stream_unit<T, PADDED, BGK, kHalfThreads>(a, u % nt, u / nt, region + kArgsBytes, ht, 1 + h);
+  stream_unit<T, PADDED, BGK, kHalfThreads, true>(a, u % nt, u / nt, region + kArgsBytes, ht, 1 + h);
 }
 
 }  // namespace
