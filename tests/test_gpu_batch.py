@@ -78,6 +78,39 @@ def assert_same(ga, gb):
     assert np.array_equal(ha, hb)
 
 
+# either side of the batched finalize's seam: one warp per grid of at most
+# 128 planes (four to a CTA), a block per 128 planes above
+SEAM = [(2, 8, 8), (31, 16, 12), (32, 16, 16), (33, 12, 20), (127, 16, 16), (128, 24, 24),
+        (129, 16, 16), (300, 16, 16)]
+
+
+@pytest.mark.parametrize("prec", [fk.FK_F64, fk.FK_F32])
+def test_finalize_warp_and_block_paths_equal_stepping_alone(prec):
+    """Grids of 2 to 300 planes in one batch with the collision term on, so
+    that the finalize also writes each plane's collision rates: 40 batch
+    steps equal 40 steps of each grid alone (whose finalize is the block
+    path for every size) bit for bit."""
+    alone, batched = twins(prec, SEAM)
+    for ga, gb in zip(alone, batched):
+        info = ga.info()
+        n_max = ga.moments()[0].max()
+        lnL = 0.02 / (info["dt"] * oracle.nu_ee(n_max, 2.0, 1.0))
+        for g in (ga, gb):
+            g.set_collisions(2.0, lnL, True)
+    with fk.Batch(batched) as b:
+        # 3 + 2 blocks for the grids of 300 and 129 planes, 2 CTAs of warps
+        # for the six others
+        assert b.info()["finalize_ctas"] == 7
+        b.step(40)
+        for g in alone:
+            g.step(40)
+        assert b.sync() == [fk.FK_OK] * len(SEAM)
+        for ga, gb in zip(alone, batched):
+            assert_same(ga, gb)
+    for g in alone + batched:
+        g.close()
+
+
 @pytest.mark.parametrize("prec", [fk.FK_F64, fk.FK_F32])
 def test_batch_bitwise_equals_stepping_alone(prec):
     alone, batched = twins(prec)
