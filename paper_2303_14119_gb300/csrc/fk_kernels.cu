@@ -601,46 +601,65 @@ __device__ __forceinline__ void finalize_body(const StepArgs& a, const FinOut& o
   }
   __syncthreads();
   const double e_wall = bc[0] * p.ex_sigma;
-  // E_x at cell centres and the v1-Courant numbers
-  double cmax = 0.0;
-#pragma unroll 4
-  for (int kk = t; kk < nx; kk += kFinThreads) {
-    const double below = boff[kk / kFinThreads] + __ldcg(fs.pre + kk);
-    const double n_k = __ldcg(ne + kk);
-    const double e = p.self_consistent ? e_wall - p.ex_n * (below + 0.5 * n_k) : p.Ex_ext;
-    Ex[kk] = e;
-    const double c = p.c1_per_ex * e;
-    c1[kk] = c;
-    c1_32[kk] = (float)c;
-    double cfl = fabs(c);
-    if (p.collisions) {
-      // BGK coefficients of the new state (Eqs. 3-4): dt nu_k = bgk_c n_k
-      const double ak = n_k > 0.0 ? p.bgk_c * n_k : 0.0;
-      a.bgk[kk] = ak;
-      a.bgk[nx + kk] = ak * n_k;
-      a.bgk32[kk] = (float)ak;
-      a.bgk32[nx + kk] = (float)(ak * n_k);
-      cfl += ak;  // the collision term takes part in the positivity bound
+  // E_x at cell centres and the v1-Courant numbers.  The planes' prefix
+  // sums and densities (other blocks' results) are loaded kLd at a time, and
+  // the coefficients once, ahead of the stores, past which the compiler
+  // cannot move a load.
+  const bool self_cons = p.self_consistent, coll = p.collisions;
+  const double ex_n = p.ex_n, ex_ext = p.Ex_ext, c1_per_ex = p.c1_per_ex, bgk_c = p.bgk_c;
+  const double cx_max = p.cx_max, ac2 = fabs(p.c2), dt = p.dt, sat_tol = p.sat_tol;
+  const long long cap = p.hist_cap, window = p.sat_window;
+  double cmax = 0.0, ex0 = 0.0;
+  constexpr int kLd = 8;
+  for (int k0 = t; k0 < nx; k0 += kLd * kFinThreads) {
+    double pre_l[kLd], ne_l[kLd];
+#pragma unroll
+    for (int j = 0; j < kLd; j++) {
+      const int kk = k0 + j * kFinThreads;
+      pre_l[j] = kk < nx ? __ldcg(fs.pre + kk) : 0.0;
+      ne_l[j] = kk < nx ? __ldcg(ne + kk) : 0.0;
     }
-    cmax = fmax(cmax, cfl);
+#pragma unroll
+    for (int j = 0; j < kLd; j++) {
+      const int kk = k0 + j * kFinThreads;
+      if (kk >= nx) break;
+      const double below = boff[kk / kFinThreads] + pre_l[j];
+      const double n_k = ne_l[j];
+      const double e = self_cons ? e_wall - ex_n * (below + 0.5 * n_k) : ex_ext;
+      if (kk == 0) ex0 = e;
+      Ex[kk] = e;
+      const double c = c1_per_ex * e;
+      c1[kk] = c;
+      c1_32[kk] = (float)c;
+      double cfl = fabs(c);
+      if (coll) {
+        // BGK coefficients of the new state (Eqs. 3-4): dt nu_k = bgk_c n_k
+        const double ak = n_k > 0.0 ? bgk_c * n_k : 0.0;
+        a.bgk[kk] = ak;
+        a.bgk[nx + kk] = ak * n_k;
+        a.bgk32[kk] = (float)ak;
+        a.bgk32[nx + kk] = (float)(ak * n_k);
+        cfl += ak;  // the collision term takes part in the positivity bound
+      }
+      cmax = fmax(cmax, cfl);
+    }
   }
   cmax = block_max<kFinThreads>(cmax, sh);
   __syncthreads();
   if (t == 0) {
     DevState d = *st;
-    if (cmax + p.cx_max + fabs(p.c2) > 1.0 + 1e-12) d.flags |= kFlagCfl;
+    if (cmax + cx_max + ac2 > 1.0 + 1e-12) d.flags |= kFlagCfl;
     const long long row = d.step;
-    const long long cap = p.hist_cap;
-    double rr[FK_HISTORY_COLS] = {(double)row, (double)row * p.dt, d.sigma, d.g_pe,
-                                  d.g_see, d.g_vac, d.n_tot, Ex[0]};
+    double rr[FK_HISTORY_COLS] = {(double)row, (double)row * dt, d.sigma, d.g_pe,
+                                  d.g_see, d.g_vac, d.n_tot, ex0};
     double* r = hist + (size_t)(row % cap) * FK_HISTORY_COLS;
     for (int q = 0; q < FK_HISTORY_COLS; q++) r[q] = rr[q];
     if (row + 1 > d.hist_count) d.hist_count = row + 1;
-    if (stepping && d.sat_step < 0 && row >= p.sat_window && p.sat_window < cap) {
-      const double* o = hist + (size_t)((row - p.sat_window) % cap) * FK_HISTORY_COLS;
+    if (stepping && d.sat_step < 0 && row >= window && window < cap) {
+      const double* o = hist + (size_t)((row - window) % cap) * FK_HISTORY_COLS;
       bool ok = true;
       for (int q = 2; q <= 4; q++)
-        if (!(fabs(rr[q] - o[q]) <= p.sat_tol * fabs(rr[q]))) ok = false;
+        if (!(fabs(rr[q] - o[q]) <= sat_tol * fabs(rr[q]))) ok = false;
       if (ok) d.sat_step = row;
     }
     st->flags = d.flags;
